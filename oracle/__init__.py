@@ -1,0 +1,383 @@
+"""FP64 CPU oracle for the Gaussian-RBF reconstruction path.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  It shares no code with ``paper_1305_5179_b300`` (neither imports the
+other); the seeded input generators in ``synth`` are the only common module.
+
+Each function states the passage of the paper it restates.  Heavy loops are in
+``rbf_oracle.c`` (plain C, double precision, compiled by ``build()``); the rest
+is numpy.  Library primitives used as single steps: ``numpy.argsort`` (stable
+sort), ``numpy`` elementwise arithmetic.  Parity is pinned in
+``tests/test_oracle_*.py`` against closed forms, brute force and library
+routines, see each function's docstring.
+
+Conventions shared with the library (these are *definitions*, stated in the
+library header as well, not shared code):
+  * centres are the extended set [X; X+; X-] (Section II.A.1), targets
+    0 / +t / -t with t = delta by default (t = 1 reproduces the paper's +-1);
+  * the kernel is exp(-r^2 / (2 sigma^2)) without the 1/(sqrt(2 pi) sigma)
+    prefactor of Eq. matrixEntries (it rescales c, leaves P_f unchanged);
+  * truncation keeps pairs with |x_i - x_j| < k sigma (strict), k = 0 keeps all;
+  * grid nodes are xi_i = lo + i (hi - lo)/(G - 1) (inclusive ends), x fastest.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sysconfig
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rbf_oracle.c")
+_LIB = os.path.join(_HERE, "librbf_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``rbf_oracle.c`` into ``librbf_oracle.so`` beside it (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", _SRC, "-o", _LIB, "-lm"]
+        subprocess.check_call(cmd)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        I64 = ctypes.c_int64
+        D = ctypes.c_double
+        lib.or_build_centers.argtypes = [P, P, I64, D, D, P, P]
+        lib.or_dense_matrix.argtypes = [P, I64, D, D, P]
+        lib.or_cholesky.argtypes = [P, I64]
+        lib.or_cholesky.restype = ctypes.c_int
+        lib.or_chol_solve.argtypes = [P, I64, P, P]
+        lib.or_kernel_rows.argtypes = [P, I64, D, D, P, P, I64, P, P]
+        lib.or_kernel_rows.restype = ctypes.c_int
+        lib.or_eval_points.argtypes = [P, I64, P, D, D, P, I64, P]
+        lib.or_eval_points.restype = ctypes.c_int
+        lib.or_num_threads.restype = ctypes.c_int
+        lib.or_set_threads.argtypes = [ctypes.c_int]
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads() -> int:
+    return int(_load().or_num_threads())
+
+
+def set_threads(t: int) -> None:
+    _load().or_set_threads(int(t))
+
+
+# --------------------------------------------------------------------------
+# Section II.A.1-2: extended data set
+# --------------------------------------------------------------------------
+def build_centers(points: np.ndarray, normals: np.ndarray, delta: float, tval: float | None = None):
+    """Extended set [X; X + delta n; X - delta n] and targets [0; +t; -t].
+
+    Section II.A.1 (off-surface points) and II.A.2 (targets).  ``tval`` defaults
+    to ``delta``.  Returns C (3N x 3 float64) and b (3N float64)."""
+    pts = np.ascontiguousarray(points, dtype=np.float32)
+    nrm = np.ascontiguousarray(normals, dtype=np.float32)
+    N = pts.shape[0]
+    C = np.empty((3 * N, 3))
+    b = np.empty(3 * N)
+    _load().or_build_centers(_p(pts), _p(nrm), N, float(delta),
+                             float(delta if tval is None else tval), _p(C), _p(b))
+    return C, b
+
+
+def default_delta(points: np.ndarray) -> float:
+    """Section II.A.1: delta = 1% of the bounding box (read: of its diagonal)."""
+    p = np.asarray(points, dtype=np.float64)
+    return 0.01 * float(np.linalg.norm(p.max(0) - p.min(0)))
+
+
+# --------------------------------------------------------------------------
+# Eq. matrixEntries / RBFsys: dense matrix, Cholesky, solve
+# --------------------------------------------------------------------------
+def dense_matrix(C: np.ndarray, sigma: float, k: float = 0.0) -> np.ndarray:
+    """A_ij = exp(-|c_i - c_j|^2/(2 sigma^2)), zero where |c_i - c_j| >= k sigma (k > 0)."""
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    n = C.shape[0]
+    A = np.empty((n, n))
+    _load().or_dense_matrix(_p(C), n, float(sigma), float(k), _p(A))
+    return A
+
+
+def cholesky(A: np.ndarray) -> np.ndarray:
+    """Unpivoted right-looking Cholesky A = L L^T (own code, Section II.B: A is SPD).
+
+    Raises ``np.linalg.LinAlgError`` when a pivot is not positive."""
+    L = np.array(A, dtype=np.float64, order="C", copy=True)
+    info = _load().or_cholesky(_p(L), L.shape[0])
+    if info != 0:
+        raise np.linalg.LinAlgError(f"non-positive pivot at column {info - 1}")
+    return L
+
+
+def chol_solve(L: np.ndarray, b: np.ndarray) -> np.ndarray:
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.empty_like(b)
+    _load().or_chol_solve(_p(np.ascontiguousarray(L)), L.shape[0], _p(b), _p(x))
+    return x
+
+
+def solve_dense(C: np.ndarray, b: np.ndarray, sigma: float, k: float = 0.0, refine_tol: float = 1e-12):
+    """Solve A c = b (Eq. RBFsys) by Cholesky, with one step of FP64 iterative
+    refinement when the relative residual exceeds ``refine_tol``.
+
+    Returns (c, relative residual)."""
+    A = dense_matrix(C, sigma, k)
+    L = cholesky(A)
+    x = chol_solve(L, b)
+    r = b - A @ x
+    nb = np.linalg.norm(b)
+    if nb > 0 and np.linalg.norm(r) / nb > refine_tol:
+        x = x + chol_solve(L, r)
+        r = b - A @ x
+    return x, (float(np.linalg.norm(r) / nb) if nb > 0 else 0.0)
+
+
+# --------------------------------------------------------------------------
+# Section III.A: truncated matrix-vector product on selected rows
+# --------------------------------------------------------------------------
+def kernel_rows(C: np.ndarray, z: np.ndarray, sigma: float, k: float, rows=None):
+    """y_r = sum_{j : |c_r - c_j| < k sigma} z_j exp(-|c_r - c_j|^2/(2 sigma^2)).
+
+    ``k <= 0`` keeps every pair.  Returns (y, number of pairs with i = j
+    included, summed over the rows)."""
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    n = C.shape[0]
+    rows = np.arange(n, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    y = np.empty(len(rows))
+    cnt = ctypes.c_int64(0)
+    rc = _load().or_kernel_rows(_p(C), n, float(sigma), float(k), _p(z), _p(rows), len(rows),
+                                _p(y), ctypes.byref(cnt))
+    if rc != 0:
+        raise MemoryError("oracle bucket list allocation failed")
+    return y, int(cnt.value)
+
+
+def residual_rows(C, b, x, sigma, k, rows=None):
+    """r_i = b_i - (A~ x)_i on ``rows`` (all rows by default)."""
+    y, _ = kernel_rows(C, x, sigma, k, rows)
+    bb = np.asarray(b, dtype=np.float64)
+    return (bb if rows is None else bb[np.asarray(rows)]) - y
+
+
+# --------------------------------------------------------------------------
+# Eq. matxvet: evaluation of P_f
+# --------------------------------------------------------------------------
+def eval_points(C: np.ndarray, w: np.ndarray, sigma: float, k: float, P: np.ndarray) -> np.ndarray:
+    """P_f(p) = sum_j w_j phi(|p - c_j|) at the rows of P (m x 3)."""
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    f = np.empty(P.shape[0])
+    rc = _load().or_eval_points(_p(C), C.shape[0], _p(w), float(sigma), float(k), _p(P), P.shape[0], _p(f))
+    if rc != 0:
+        raise MemoryError("oracle bucket list allocation failed")
+    return f
+
+
+def grid_nodes(lo, hi, dims, flat_index=None) -> np.ndarray:
+    """Nodes xi = lo + i (hi - lo)/(G - 1) per axis (G = 1 puts the node at lo),
+    ordered x fastest; ``flat_index`` selects nodes by their flat position."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    dims = np.asarray(dims, dtype=np.int64)
+    if flat_index is None:
+        flat_index = np.arange(int(np.prod(dims)), dtype=np.int64)
+    flat_index = np.asarray(flat_index, dtype=np.int64)
+    ix = flat_index % dims[0]
+    iy = (flat_index // dims[0]) % dims[1]
+    iz = flat_index // (dims[0] * dims[1])
+    step = np.where(dims > 1, (hi - lo) / np.maximum(dims - 1, 1), 0.0)
+    return np.stack([lo[0] + ix * step[0], lo[1] + iy * step[1], lo[2] + iz * step[2]], axis=1)
+
+
+# --------------------------------------------------------------------------
+# Cell binning (the "truncation area" of Algorithm 2 made concrete)
+# --------------------------------------------------------------------------
+def part1by2(v: np.ndarray) -> np.ndarray:
+    """Spread the low 10 bits of v so that bit b moves to bit 3b."""
+    v = np.asarray(v, dtype=np.uint64)
+    out = np.zeros_like(v)
+    for b in range(10):
+        out |= ((v >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b)
+    return out
+
+
+def morton3(qx, qy, qz) -> np.ndarray:
+    """Interleave three 10-bit integers: bit b of qx -> 3b, qy -> 3b+1, qz -> 3b+2."""
+    return (part1by2(qx) | (part1by2(qy) << np.uint64(1)) | (part1by2(qz) << np.uint64(2))).astype(np.uint32)
+
+
+def binning(C32: np.ndarray, sigma: float, k: float, cells_per_cutoff: int = 1, levels: int = 3):
+    """Cell binning of the centres in FP32, as a definition.
+
+    * lo = componentwise minimum of the centres; ext = hi - lo (FP32);
+    * cell edge hc = k sigma / s (k > 0) or max(ext)/8 (k = 0, or 1 if that is 0);
+    * fine edge hf = hc / 2^L, inv = float32(2^L / hc) computed in double;
+    * q_d = floor((c_d - lo_d) * inv) in float32 arithmetic;
+    * nbits = max(L, bit length of max_d floor(ext_d * inv)) (must be <= 10);
+    * key = Morton interleave of (q_x, q_y, q_z); cell = key >> 3L;
+    * stable sort of the centres by key.
+    Returns dict(perm, keys_sorted, cell_of_sorted, cell_start, cell_end (dense
+    tables over 2^(3(nbits-L)) cell codes), nbits, inv, lo).
+    """
+    c = np.ascontiguousarray(C32[:, :3], dtype=np.float32)
+    lo = c.min(0)
+    hi = c.max(0)
+    ext = (hi - lo).astype(np.float32)
+    L = int(levels)
+    if k > 0:
+        hc = float(np.float32(k)) * float(np.float32(sigma)) / float(cells_per_cutoff)
+    else:
+        m = float(ext.max())
+        hc = m / 8.0 if m > 0 else 1.0
+    inv = np.float32((2.0 ** L) / hc)
+    qmax = int(np.floor(ext * inv).max()) if len(c) else 0
+    nbits = max(L, int(qmax).bit_length())
+    if nbits > 10:
+        raise ValueError("domain spans more than 1024 fine cells per axis")
+    q = np.floor((c - lo).astype(np.float32) * inv).astype(np.int64)
+    q = np.clip(q, 0, (1 << nbits) - 1)
+    key = morton3(q[:, 0], q[:, 1], q[:, 2])
+    perm = np.argsort(key, kind="stable")
+    ks = key[perm]
+    cell = (ks >> np.uint32(3 * L)).astype(np.int64)
+    ncell = 1 << (3 * (nbits - L))
+    start = np.zeros(ncell, dtype=np.int64)
+    end = np.zeros(ncell, dtype=np.int64)
+    if len(cell):
+        first = np.ones(len(cell), dtype=bool)
+        first[1:] = cell[1:] != cell[:-1]
+        last = np.ones(len(cell), dtype=bool)
+        last[:-1] = cell[1:] != cell[:-1]
+        start[cell[first]] = np.nonzero(first)[0]
+        end[cell[last]] = np.nonzero(last)[0] + 1
+    return dict(perm=perm.astype(np.int64), keys_sorted=ks, cell_of_sorted=cell,
+                cell_start=start, cell_end=end, nbits=nbits, inv=inv, lo=lo)
+
+
+# --------------------------------------------------------------------------
+# Section III.A: restricted additive Schwarz preconditioner
+# --------------------------------------------------------------------------
+def schwarz_partition(n: int, core: int, block: int):
+    """Cores are consecutive runs of ``core`` positions of the binned order; the
+    overlapping subdomain Omega_i is the run of exactly min(block, n) positions
+    starting at clamp(s - (block - core)//2, 0, n - block).
+
+    Returns a list of (dom_start, dom_len, core_start, core_len) in binned order."""
+    out = []
+    o = block - core
+    for s in range(0, n, core):
+        e = min(s + core, n)
+        if n >= block:
+            d0 = min(max(s - o // 2, 0), n - block)
+            dl = block
+        else:
+            d0, dl = 0, n
+        out.append((d0, dl, s, e - s))
+    return out
+
+
+def schwarz_apply(Cs: np.ndarray, v: np.ndarray, sigma: float, parts, shift: float,
+                  restricted: bool = True) -> np.ndarray:
+    """z = sum_i Rt_i^T (A_i + shift I)^{-1} R_i v  (restricted, the paper's RASM)
+    or sum_i R_i^T (A_i + shift I)^{-1} R_i v (additive), Section III.A.
+
+    ``Cs`` are the centres in binned order, A_i is the untruncated Gaussian
+    matrix of subdomain i (a principal submatrix of the SPD matrix A), each block
+    solved with the own Cholesky of this module."""
+    z = np.zeros(len(v))
+    for d0, dl, c0, cl in parts:
+        idx = slice(d0, d0 + dl)
+        Ai = dense_matrix(Cs[idx], sigma, 0.0) + shift * np.eye(dl)
+        si = chol_solve(cholesky(Ai), v[idx])
+        if restricted:
+            z[c0:c0 + cl] = si[c0 - d0:c0 - d0 + cl]
+        else:
+            z[idx] += si
+    return z
+
+
+# --------------------------------------------------------------------------
+# Section III.A: GMRES (flexible, right-preconditioned) as the Krylov method
+# --------------------------------------------------------------------------
+def fgmres(matvec, b: np.ndarray, precond=None, m: int = 50, tol: float = 1e-6, max_it: int = 500,
+           x0: np.ndarray | None = None):
+    """Flexible GMRES(m) (Saad 1993) with classical Gram-Schmidt applied twice
+    and Givens rotations, all in FP64.  Stops when the rotated residual estimate
+    |g_{j+1}| <= tol * |b| or after ``max_it`` inner iterations; each restart
+    recomputes the true residual b - A x.  Returns (x, iterations, history of
+    the residual estimate relative to |b|)."""
+    b = np.asarray(b, dtype=np.float64)
+    n = len(b)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
+    M = (lambda v: v.copy()) if precond is None else precond
+    nb = np.linalg.norm(b)
+    hist = []
+    it = 0
+    if nb == 0:
+        return x, 0, hist
+    while it < max_it:
+        r = b - matvec(x)
+        beta = np.linalg.norm(r)
+        if beta <= tol * nb:
+            break
+        V = np.zeros((m + 1, n))
+        Z = np.zeros((m, n))
+        H = np.zeros((m + 1, m))
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        g = np.zeros(m + 1)
+        V[0] = r / beta
+        g[0] = beta
+        j = -1
+        for j in range(m):
+            Z[j] = M(V[j])
+            w = matvec(Z[j])
+            for _ in range(2):
+                h = V[:j + 1] @ w
+                w = w - V[:j + 1].T @ h
+                H[:j + 1, j] += h
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] > 0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            rho = np.hypot(H[j, j], H[j + 1, j])
+            cs[j] = H[j, j] / rho
+            sn[j] = H[j + 1, j] / rho
+            H[j, j] = rho
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            it += 1
+            hist.append(abs(g[j + 1]) / nb)
+            if abs(g[j + 1]) <= tol * nb or it >= max_it or H[j + 1, j] == 0 and rho == 0:
+                break
+        k = j + 1
+        y = np.zeros(k)
+        for i in range(k - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
+        x = x + Z[:k].T @ y
+        if hist and hist[-1] <= tol:
+            break
+    return x, it, hist

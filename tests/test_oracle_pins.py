@@ -1,0 +1,353 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these re-derive a value with the oracle's own formula: each compares
+against a closed form, a library routine, a geometric invariant or brute force
+organised differently, chosen so that a dropped term, a wrong sign or index, a
+transposed operand or a wrong constant in the oracle fails at least one test.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+# ---------------------------------------------------------------- Section II.A.1
+def test_offsurface_points_on_parallel_spheres():
+    """On the unit sphere with n = x, the points x +- delta n lie on the spheres
+    of radius 1 +- delta (a geometric invariant of Section II.A.1)."""
+    cl = synth.sphere(300, seed=3)
+    d = 0.07
+    C, b = oracle.build_centers(cl.points, cl.normals, d)
+    N = 300
+    r = np.linalg.norm(C, axis=1)
+    assert np.allclose(r[:N], 1.0, atol=1e-6)
+    assert np.allclose(r[N:2 * N], 1.0 + d, atol=1e-6)
+    assert np.allclose(r[2 * N:], 1.0 - d, atol=1e-6)
+    assert np.all(b[:N] == 0) and np.all(b[N:2 * N] == d) and np.all(b[2 * N:] == -d)
+    C1, b1 = oracle.build_centers(cl.points, cl.normals, d, tval=1.0)
+    assert np.all(b1[N:2 * N] == 1.0) and np.all(b1[2 * N:] == -1.0)
+
+
+def test_default_delta_is_one_percent_of_bbox_diagonal():
+    p = np.array([[0, 0, 0], [3, 4, 12]], dtype=np.float32)
+    assert oracle.default_delta(p) == pytest.approx(0.13)
+
+
+# ------------------------------------------------------- Eq. matrixEntries, RBFsys
+def test_entry_half_value_distance():
+    """exp(-r^2/(2 sigma^2)) = 1/2 exactly at r = sigma sqrt(2 ln 2)."""
+    s = 0.37
+    r = s * math.sqrt(2 * math.log(2.0))
+    C = np.array([[0.1, 0.2, 0.3], [0.1 + r, 0.2, 0.3]])
+    A = oracle.dense_matrix(C, s)
+    assert A[0, 0] == 1.0 and A[1, 1] == 1.0
+    assert A[0, 1] == pytest.approx(0.5, rel=1e-14)
+    assert A[1, 0] == pytest.approx(0.5, rel=1e-14)
+    # same distance split over the three axes
+    C2 = np.array([[0, 0, 0], [r / math.sqrt(3)] * 3])
+    assert oracle.dense_matrix(C2, s)[0, 1] == pytest.approx(0.5, rel=1e-14)
+
+
+def test_lattice_row_sum_is_separable():
+    """On an m^3 lattice of spacing h with z = 1 the untruncated row sum at node
+    (a, b, c) is the product of three 1-D sums of exp(-(i-a)^2 h^2/(2 sigma^2))."""
+    m, h, s = 7, 0.13, 0.21
+    P = synth.lattice(m, h, origin=(0.4, -0.2, 1.0))
+    z = np.ones(len(P))
+    row = (2 * m + 4) * m + 1          # node (x=1, y=4, z=2)
+    y, cnt = oracle.kernel_rows(P, z, s, 0.0, rows=[row])
+    one_d = [sum(math.exp(-((i - a) * h) ** 2 / (2 * s * s)) for i in range(m)) for a in (1, 4, 2)]
+    assert cnt == m ** 3
+    assert y[0] == pytest.approx(one_d[0] * one_d[1] * one_d[2], rel=1e-13)
+
+
+def test_lattice_row_sum_truncated_counts_ball_nodes():
+    """With cut-off k sigma, the row keeps exactly the lattice nodes strictly inside
+    the ball of radius k sigma (counted by integer arithmetic)."""
+    m, h, s, k = 13, 0.1, 0.1, 3.5
+    P = synth.lattice(m, h)
+    c = (6, 6, 6)
+    row = (c[2] * m + c[1]) * m + c[0]
+    y, cnt = oracle.kernel_rows(P, np.ones(len(P)), s, k, rows=[row])
+    # |d|^2 < (k sigma / h)^2 = 12.25 in lattice units
+    inside = [(i, j, l) for i in range(-6, 7) for j in range(-6, 7) for l in range(-6, 7)
+              if i * i + j * j + l * l < 12.25]
+    assert cnt == len(inside)
+    expect = sum(math.exp(-(i * i + j * j + l * l) * h * h / (2 * s * s)) for i, j, l in inside)
+    assert y[0] == pytest.approx(expect, rel=1e-13)
+
+
+def test_matrix_symmetric_positive_definite(sphere_c1):
+    """Section II.B: the Gaussian gives a symmetric positive definite matrix
+    (checked with LAPACK's symmetric eigensolver, a library routine)."""
+    cl = synth.sphere(60, seed=1)
+    C, _ = oracle.build_centers(cl.points, cl.normals, 0.05)
+    A = oracle.dense_matrix(C, 0.3)
+    assert np.array_equal(A, A.T)
+    lam = np.linalg.eigvalsh(A)
+    assert lam[0] > 0
+
+
+def test_truncation_bound():
+    """|(A~ z - A z)_i| <= exp(-k^2/2) * sum_{|c_i - c_j| >= k sigma} |z_j|."""
+    rng = np.random.default_rng(7)
+    C = rng.uniform(-1, 1, (400, 3))
+    z = rng.standard_normal(400)
+    s, k = 0.25, 2.5
+    yt, _ = oracle.kernel_rows(C, z, s, k)
+    yf, _ = oracle.kernel_rows(C, z, s, 0.0)
+    D = np.sqrt(((C[:, None, :] - C[None, :, :]) ** 2).sum(-1))
+    far = D >= k * s
+    bound = math.exp(-k * k / 2) * (far * np.abs(z)[None, :]).sum(1)
+    assert np.all(np.abs(yt - yf) <= bound * (1 + 1e-12) + 1e-300)
+    assert np.any(far)
+
+
+def test_kernel_rows_match_brute_force_loops():
+    """The bucket list only skips far pairs: compare with plain Python loops."""
+    rng = np.random.default_rng(11)
+    C = rng.uniform(0, 1, (50, 3))
+    z = rng.standard_normal(50)
+    s, k = 0.1, 3.0
+    y, cnt = oracle.kernel_rows(C, z, s, k)
+    ref = np.zeros(50)
+    ref_cnt = 0
+    for i in range(50):
+        for j in range(50):
+            d2 = sum((C[i, t] - C[j, t]) ** 2 for t in range(3))
+            if math.sqrt(d2) < k * s:
+                ref[i] += z[j] * math.exp(-d2 / (2 * s * s))
+                ref_cnt += 1
+    assert cnt == ref_cnt
+    assert np.allclose(y, ref, rtol=1e-13, atol=1e-15)
+
+
+# --------------------------------------------------------------- Cholesky / solve
+def test_cholesky_reconstructs_and_matches_lapack():
+    cl = synth.sphere(80, seed=2)
+    C, _ = oracle.build_centers(cl.points, cl.normals, 0.05)
+    A = oracle.dense_matrix(C, 0.04)      # well conditioned, so the factors compare
+    assert np.linalg.cond(A) < 1e4
+    L = oracle.cholesky(A)
+    assert np.all(np.triu(L, 1) == 0)
+    assert np.abs(L @ L.T - A).max() <= 1e-14 * np.abs(A).max() * 10
+    assert np.allclose(L, np.linalg.cholesky(A), rtol=1e-10, atol=1e-12)
+
+
+def test_cholesky_rejects_indefinite():
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.cholesky(np.array([[1.0, 2.0], [2.0, 1.0]]))
+
+
+def test_solve_one_and_two_points():
+    """n = 1: c = b.  n = 2: [[1, g], [g, 1]] c = b with g = exp(-r^2/(2 s^2))."""
+    c, res = oracle.solve_dense(np.array([[0.3, 0.1, -0.2]]), np.array([0.7]), 0.2)
+    assert c[0] == pytest.approx(0.7, rel=1e-15)
+    r, s = 0.15, 0.2
+    C = np.array([[0, 0, 0], [0, r, 0]])
+    b = np.array([0.3, -0.9])
+    g = math.exp(-r * r / (2 * s * s))
+    c, _ = oracle.solve_dense(C, b, s)
+    det = 1 - g * g
+    assert c[0] == pytest.approx((b[0] - g * b[1]) / det, rel=1e-12)
+    assert c[1] == pytest.approx((b[1] - g * b[0]) / det, rel=1e-12)
+
+
+@pytest.fixture(scope="module")
+def c1_solution(sphere_c1):
+    C, b = oracle.build_centers(sphere_c1.points, sphere_c1.normals, 0.05)
+    x, res = oracle.solve_dense(C, b, 0.1)
+    return C, b, x, res
+
+
+@pytest.mark.slow
+def test_c1_interpolation_residual(c1_solution):
+    """Interpolation conditions hold at every centre to 1e-12 (absolute, b ~ 0.05)."""
+    C, b, x, res = c1_solution
+    y, _ = oracle.kernel_rows(C, x, 0.1, 0.0)
+    assert np.abs(y - b).max() <= 1e-12
+    assert res <= 1e-12
+
+
+@pytest.mark.slow
+def test_c1_zero_set_near_unit_sphere(c1_solution):
+    """The zero set of P_f along 2,000 seeded rays lies within delta/2 of the unit
+    sphere (mean within delta/10); f < 0 just inside and f > 0 just outside."""
+    C, b, x, _ = c1_solution
+    rng = np.random.default_rng(123)
+    g = rng.standard_normal((2000, 3))
+    u = g / np.linalg.norm(g, axis=1, keepdims=True)
+    lo = np.full(2000, 0.9)
+    hi = np.full(2000, 1.1)
+    flo = oracle.eval_points(C, x, 0.1, 0.0, lo[:, None] * u)
+    fhi = oracle.eval_points(C, x, 0.1, 0.0, hi[:, None] * u)
+    assert np.all(flo < 0) and np.all(fhi > 0)
+    for _ in range(30):
+        mid = 0.5 * (lo + hi)
+        fm = oracle.eval_points(C, x, 0.1, 0.0, mid[:, None] * u)
+        neg = fm < 0
+        lo = np.where(neg, mid, lo)
+        hi = np.where(neg, hi, mid)
+    rstar = 0.5 * (lo + hi)
+    assert np.abs(rstar - 1).max() <= 0.025
+    assert np.abs(rstar - 1).mean() <= 0.005
+
+
+# ----------------------------------------------------------------- Eq. matxvet
+def test_eval_single_centre_closed_form():
+    s = 0.2
+    r = s * math.sqrt(2 * math.log(2.0))
+    C = np.array([[1.0, -1.0, 0.5]])
+    P = np.array([[1.0 + r, -1.0, 0.5], [1.0, -1.0, 0.5], [1.0, -1.0 + 3 * s, 0.5]])
+    f = oracle.eval_points(C, np.array([2.0]), s, 0.0, P)
+    assert f[0] == pytest.approx(1.0, rel=1e-14)
+    assert f[1] == pytest.approx(2.0, rel=1e-15)
+    assert f[2] == pytest.approx(2.0 * math.exp(-4.5), rel=1e-14)
+    ft = oracle.eval_points(C, np.array([2.0]), s, 2.0, P)   # cut-off 2 sigma drops the third
+    assert ft[2] == 0.0 and ft[0] == pytest.approx(1.0, rel=1e-14)
+
+
+def test_eval_far_points_are_zero_when_truncated():
+    rng = np.random.default_rng(1)
+    C = rng.uniform(0, 1, (100, 3))
+    P = np.array([[5.0, 5.0, 5.0], [-3.0, 0.5, 0.5], [0.5, 0.5, 1.0 + 0.31]])
+    f = oracle.eval_points(C, np.ones(100), 0.05, 6.0, P)
+    assert f[0] == 0.0 and f[1] == 0.0 and f[2] == 0.0
+
+
+def test_grid_nodes_inclusive_x_fastest():
+    P = oracle.grid_nodes((-1, 0, 2), (1, 1, 2), (3, 2, 1))
+    assert P.shape == (6, 3)
+    assert np.allclose(P[:, 0], [-1, 0, 1, -1, 0, 1])
+    assert np.allclose(P[:, 1], [0, 0, 0, 1, 1, 1])
+    assert np.allclose(P[:, 2], 2)
+    Q = oracle.grid_nodes((-1.2,) * 3, (1.2,) * 3, (64,) * 3, flat_index=[64 ** 3 - 1, 0])
+    assert np.allclose(Q[0], 1.2) and np.allclose(Q[1], -1.2)
+
+
+# ------------------------------------------------------------------- binning
+def test_morton_known_codes():
+    m = oracle.morton3(np.array([1, 0, 0, 7, 1023, 5]), np.array([0, 1, 0, 7, 0, 3]),
+                       np.array([0, 0, 1, 7, 0, 6]))
+    # (5,3,6): x=101 y=011 z=110 -> bits z2y2x2 z1y1x1 z0y0x0 = 101 110 011
+    assert list(m) == [1, 2, 4, 511, int("001" * 10, 2), int("101110011", 2)]
+
+
+def test_binning_permutation_sorted_stable():
+    rng = np.random.default_rng(4)
+    C = rng.uniform(-1, 2, (5000, 3)).astype(np.float32)
+    C[100:110] = C[7]                          # duplicates: equal keys
+    B = oracle.binning(C, 0.05, 3.0)
+    perm = B["perm"]
+    assert np.array_equal(np.sort(perm), np.arange(5000))
+    ks = B["keys_sorted"].astype(np.int64)
+    assert np.all(np.diff(ks) >= 0)
+    eq = np.diff(ks) == 0
+    assert np.all(np.diff(perm)[eq] > 0)       # stable: equal keys keep input order
+    # every centre lies in the fine cell its key names
+    inv, lo = B["inv"], B["lo"]
+    q = np.floor((C[perm] - lo).astype(np.float32) * inv)
+    hf = 1.0 / float(inv)
+    assert np.all(q >= 0)
+    assert np.all((C[perm] - lo) >= q * hf * (1 - 1e-6) - 1e-7)
+    # cell table covers every sorted position exactly once
+    st, en = B["cell_start"], B["cell_end"]
+    covered = np.zeros(5000, dtype=int)
+    for s, e in zip(st, en):
+        covered[s:e] += 1
+    assert np.all(covered == 1)
+
+
+def test_binning_cell_edge():
+    """Fine cells are hc/2^L with hc = k sigma / s; cells are 2^L fine cells."""
+    C = np.array([[0, 0, 0], [0.299, 0, 0], [0.301, 0, 0], [0.61, 0.0, 0.0]], dtype=np.float32)
+    B = oracle.binning(C, 0.1, 3.0, cells_per_cutoff=1, levels=3)   # hc = 0.3
+    cell = B["cell_of_sorted"][np.argsort(B["perm"])]
+    assert cell[0] == cell[1] and cell[2] != cell[1]
+    assert cell[2] == 1 and cell[3] == 8   # Morton codes of cell x = 1 and x = 2
+
+
+# ------------------------------------------------------------ Schwarz / FGMRES
+def test_schwarz_partition_covers_and_contains_cores():
+    for n, core, block in [(1000, 96, 128), (130, 96, 128), (100, 96, 128), (500, 128, 128), (7, 3, 5)]:
+        parts = oracle.schwarz_partition(n, core, block)
+        cov = np.zeros(n, dtype=int)
+        for d0, dl, c0, cl in parts:
+            assert dl == min(block, n)
+            assert d0 <= c0 and c0 + cl <= d0 + dl and 0 <= d0 and d0 + dl <= n
+            cov[c0:c0 + cl] += 1
+        assert np.all(cov == 1)
+
+
+def test_schwarz_single_block_is_exact_inverse():
+    cl = synth.sphere(40, seed=5)
+    C, b = oracle.build_centers(cl.points, cl.normals, 0.05)
+    s = 0.3
+    parts = oracle.schwarz_partition(len(C), len(C), len(C))
+    z = oracle.schwarz_apply(C, b, s, parts, 0.0)
+    A = oracle.dense_matrix(C, s)
+    assert np.allclose(z, np.linalg.solve(A, b), rtol=1e-8, atol=1e-10)
+    x, it, hist = oracle.fgmres(lambda v: A @ v, b, lambda v: oracle.schwarz_apply(C, v, s, parts, 0.0))
+    assert it == 1 and hist[-1] < 1e-8
+
+
+def test_schwarz_block_jacobi_and_additive():
+    """Zero overlap: restricted == additive == block-diagonal solve (LAPACK)."""
+    rng = np.random.default_rng(9)
+    C = rng.uniform(0, 1, (90, 3))
+    v = rng.standard_normal(90)
+    s, lam = 0.2, 1e-3
+    parts = oracle.schwarz_partition(90, 30, 30)
+    zr = oracle.schwarz_apply(C, v, s, parts, lam, restricted=True)
+    za = oracle.schwarz_apply(C, v, s, parts, lam, restricted=False)
+    ref = np.concatenate([np.linalg.solve(oracle.dense_matrix(C[i:i + 30], s) + lam * np.eye(30), v[i:i + 30])
+                          for i in (0, 30, 60)])
+    assert np.allclose(zr, ref, rtol=1e-9, atol=1e-12)
+    assert np.allclose(za, ref, rtol=1e-9, atol=1e-12)
+    # with overlap the two differ, and restricted only writes cores
+    parts = oracle.schwarz_partition(90, 30, 40)
+    zr = oracle.schwarz_apply(C, v, s, parts, lam, restricted=True)
+    za = oracle.schwarz_apply(C, v, s, parts, lam, restricted=False)
+    assert not np.allclose(zr, za)
+
+
+def test_fgmres_distinct_eigenvalues():
+    """GMRES on a diagonal matrix with k distinct eigenvalues converges in <= k steps."""
+    d = np.repeat([1.0, 2.0, 5.0, 9.0], 25)
+    b = np.random.default_rng(2).standard_normal(100)
+    x, it, hist = oracle.fgmres(lambda v: d * v, b, m=20, tol=1e-12)
+    assert it <= 4
+    assert np.allclose(x, b / d, rtol=1e-10)
+
+
+def test_fgmres_matches_scipy_gmres_history():
+    """Unrestarted residual history equals SciPy's GMRES (library) on an SPD system."""
+    from scipy.sparse.linalg import gmres
+    cl = synth.sphere(60, seed=8)
+    C, b = oracle.build_centers(cl.points, cl.normals, 0.05)
+    A = oracle.dense_matrix(C, 0.2)
+    x, it, hist = oracle.fgmres(lambda v: A @ v, b, m=30, tol=1e-30, max_it=30)
+    ref = []
+    gmres(A, b, rtol=1e-30, restart=30, maxiter=1, callback=lambda r: ref.append(r), callback_type="pr_norm")
+    assert it == 30
+    assert np.allclose(hist[:20], ref[:20], rtol=1e-6)
+    y = A @ x
+    assert np.linalg.norm(b - y) / np.linalg.norm(b) == pytest.approx(hist[-1], rel=1e-4)
+
+
+def test_fgmres_flexible_preconditioner_changes_nothing_at_convergence():
+    """A variable (flexible) preconditioner still gives the solution of A x = b."""
+    rng = np.random.default_rng(3)
+    Q = rng.standard_normal((40, 40))
+    A = Q @ Q.T + 40 * np.eye(40)
+    b = rng.standard_normal(40)
+    cnt = [0]
+
+    def prec(v):
+        cnt[0] += 1
+        return v / np.diag(A) * (1.0 + 0.1 * (cnt[0] % 3))
+    x, it, hist = oracle.fgmres(lambda v: A @ v, b, prec, m=40, tol=1e-12)
+    assert np.allclose(A @ x, b, rtol=1e-9, atol=1e-9)
