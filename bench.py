@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Benchmark of the Gaussian-RBF reconstruction hot path on synthetic scans.
+
+One step = one pass of the whole path on one cloud (Algorithm 1, steps 1-3):
+  a1 off-surface centres (x +- delta n) and targets;
+  a2 cell binning (Morton radix sort), source blocks, tiles, pair list;
+  a5 restricted additive Schwarz set-up (128-centre subdomains, float32 Cholesky);
+  a6/a7 flexible GMRES, 50 iterations (the fixed count of the paper's Table II),
+     float32 truncated products, float64 CGS2 Arnoldi;
+  a8 float64 true residual b - A~ x;
+  a9 P_f on the 256^3 grid over the data box padded by delta + 3 sigma.
+Workload: 1,000,000 points on the noisy torus (R = 1, r = 0.35, noise 1e-3),
+delta = 0.01 -> 3,000,000 centres, sigma = 0.02, cut-off 6 sigma.
+
+value = algorithmic pair evaluations of the step's Gaussian products (50 float32
+products + 1 float64 residual product + the grid evaluation) / step time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RBF pair-evals/s in matvec (whole step: centres, binning, RAS set-up, 50 FGMRES iterations, " \
+         "float64 residual, 256^3 grid)"
+UNIT = "pair-evals/s"
+
+WORKLOADS = {
+    "torus1m": dict(desc="torus R=1 r=0.35 noise 1e-3, N=1,000,000 points -> 3,000,000 centres",
+                    N=1_000_000, delta=0.01, sigma=0.02, k=6.0, grid=256, core=96, block=128, shift=1e-4,
+                    iters=50, m=50, precond="schwarz"),
+    "sphere1500": dict(desc="unit sphere N=1,500 -> 4,500 centres, untruncated", N=1500, delta=0.05, sigma=0.1,
+                       k=0.0, grid=64, core=96, block=128, shift=1e-4, iters=50, m=50, precond="none"),
+}
+
+
+def make_cloud(wl):
+    import synth
+    if wl["N"] == 1500:
+        return synth.sphere(1500, seed=0)
+    return synth.torus(wl["N"], noise=1e-3, seed=0)
+
+
+def grid_box(points, wl):
+    import numpy as np
+    pad = wl["delta"] + 3 * wl["sigma"]
+    if wl["N"] == 1500:
+        return (-1.2,) * 3, (1.2,) * 3
+    lo = points.min(0).astype(np.float64) - pad
+    hi = points.max(0).astype(np.float64) + pad
+    return tuple(lo), tuple(hi)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- oracle arm
+def oracle_rate(C64, wl, nrows, seed=0):
+    """Pair evaluations per second of the FP64 oracle on `nrows` sampled rows."""
+    import numpy as np
+    import oracle
+    rows = np.random.default_rng(seed).choice(len(C64), nrows, replace=False)
+    z = np.random.default_rng(seed + 1).standard_normal(len(C64))
+    t0 = time.perf_counter()
+    _, cnt = oracle.kernel_rows(C64, z, float(np.float32(wl["sigma"])), float(np.float32(wl["k"])), rows)
+    dt = time.perf_counter() - t0
+    return cnt / dt, cnt, dt
+
+
+def run_reference(args, wl):
+    import numpy as np
+    import oracle
+    rank, world, _ = dist_setup()
+    if rank != 0:
+        return 0
+    cl = make_cloud(wl)
+    C64, _ = oracle.build_centers(cl.points, cl.normals, wl["delta"])
+    C64 = C64.astype(np.float32).astype(np.float64)
+    nrows = args.ref_rows
+    for _ in range(args.warmup):
+        oracle_rate(C64, wl, max(100, nrows // 10))
+    tot_pairs, tot_t = 0, 0.0
+    for k in range(args.steps):
+        _, cnt, dt = oracle_rate(C64, wl, nrows, seed=k)
+        tot_pairs += cnt
+        tot_t += dt
+    v = tot_pairs / tot_t
+    cores = oracle.num_threads()
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl["desc"], "sample": f"{nrows} sampled rows per step", "sigma": wl["sigma"],
+                      "k": wl["k"]},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{nrows} sampled rows of the {len(C64):,}-centre operator per step, "
+                                      f"float64 row sums over a bucket list"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, wl):
+    import numpy as np
+    import torch
+    import paper_1305_5179_b300 as rbf
+
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    ctx = rbf.Context(local)
+    stream = torch.cuda.current_stream()
+
+    cl = make_cloud(wl)
+    lo, hi = grid_box(cl.points, wl)
+    G = wl["grid"]
+    dims = (G, G, G)
+    pts_h = torch.from_numpy(cl.points).pin_memory()
+    nrm_h = torch.from_numpy(cl.normals).pin_memory()
+    pts = pts_h.to(dev)
+    nrm = nrm_h.to(dev)
+    f_h = torch.empty((G, G, G), dtype=torch.float32).pin_memory()
+    solve_kw = dict(m=wl["m"], max_it=wl["iters"], fixed_iterations=True, precond=wl["precond"], core=wl["core"],
+                    block=wl["block"], shift=wl["shift"], escalate=True)
+
+    def step(p, q, fout=None):
+        C, b, _ = rbf.build_centers(ctx, p, q, delta=wl["delta"])
+        plan = rbf.Plan(ctx, C, sigma=wl["sigma"], k=wl["k"])
+        x, rep = plan.solve(b, **solve_kw)
+        f = plan.eval_grid(x, lo, hi, dims, out=fout)
+        return plan, x, f, rep
+
+    # untimed: pair counts of the products and of the grid evaluation
+    plan0, x0, f0, rep0 = step(pts, nrm)
+    pairs_mv = plan0.count_pairs()
+    pairs_grid = grid_pairs(plan0, wl, lo, hi, dims)
+    n = plan0.n
+    info = plan0.info()
+    del plan0
+    pairs_step = pairs_mv * (rep0["matvec_launches"] + rep0["residual_launches"]) + pairs_grid
+
+    for _ in range(max(0, args.warmup - 1)):
+        step(pts, nrm)
+    torch.cuda.synchronize()
+    barrier(world)
+    l0 = rbf.launch_count()
+    reps = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan, x, f, rep = step(pts, nrm)
+            reps.append(rep)
+            del plan
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        barrier(world)
+    launches = rbf.launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, world)
+    value = world * pairs_step / (ms * 1e-3)
+    clocks = clk.summary()
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    torch.cuda.synchronize()
+    barrier(world)
+    t0e = time.perf_counter()
+    for _ in range(args.steps):
+        p = pts_h.to(dev, non_blocking=True)
+        q = nrm_h.to(dev, non_blocking=True)
+        plan, x, f, rep = step(p, q)
+        f_h.copy_(f, non_blocking=True)
+        torch.cuda.synchronize()
+        del plan
+    t1e = time.perf_counter()
+    ms_e2e = max_over_ranks(1e3 * (t1e - t0e) / args.steps, world)
+    h2d = pts_h.numel() * 4 + nrm_h.numel() * 4
+    d2h = f_h.numel() * 4
+
+    # dominant kernel: float32 product, average launch time measured with CUDA events in the timed steps
+    mv_ms = statistics.mean(r["ms_matvec"] / max(1, r["matvec_launches"]) for r in reps)
+    probe = rbf.probe_peaks(local)
+    f_mhz = clocks.get("sm_mhz") or probe["sm_mhz"]
+    peak = probe["num_sms"] * f_mhz * 1e6 * probe["ex2_per_clk_sm"]   # one ex2 per pair
+    achieved = pairs_mv / (mv_ms * 1e-3)
+    roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "k_matvec_f32 (float32 truncated product)",
+            "peak_basis": f"{probe['num_sms']} SMs x {f_mhz:.0f} MHz (median SM clock in the timed region) x "
+                          f"{probe['ex2_per_clk_sm']:.2f} ex2/clk/SM (measured by rbf_probe_peaks): "
+                          f"one MUFU.EX2 per pair",
+            "probe": probe}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle as orc
+        Cc, _ = orc.build_centers(cl.points, cl.normals, wl["delta"])
+        Cc = Cc.astype(np.float32).astype(np.float64)
+        rate, cnt, dt = oracle_rate(Cc, wl, args.cpu_rows)
+        cpu = {"value": rate, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+               "sample": f"{args.cpu_rows} sampled rows of the {len(Cc):,}-centre truncated operator "
+                         f"({cnt:,} pairs, {dt:.1f} s), float64 row sums over a bucket list"}
+
+    if rank == 0:
+        rep = reps[-1]
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "sigma": wl["sigma"], "k": wl["k"], "delta": wl["delta"],
+                       "centres": n, "grid": list(dims), "fgmres_iterations": wl["iters"], "restart": wl["m"],
+                       "precond": f"{wl['precond']} core {wl['core']} block {wl['block']} shift {wl['shift']}",
+                       "pairs_per_matvec": pairs_mv, "pairs_grid": pairs_grid, "pairs_per_step": pairs_step,
+                       "l2": "working set > L2 (FGMRES basis alone is "
+                             f"{(wl['m'] + 1) * n * 8 / 1e9:.2f} GB)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "pairlist_len": info["pairlist_len"], "blocks": info["nblocks"],
+                       "tiles": info["nchunks"]},
+            "solve": {"iterations": rep["iterations"], "residual_true": rep["residual_true"],
+                      "residual_estimate": rep["residual_estimate"], "ms_setup": rep["ms_setup"],
+                      "ms_solve": rep["ms_solve"], "ms_matvec_total": rep["ms_matvec"],
+                      "ms_residual_f64": rep["ms_residual"], "ms_precond_total": rep["ms_precond"],
+                      "failed_blocks": rep["precond_failed_blocks"]},
+            "matvec": {"ms_per_launch": mv_ms, "pairs_per_s": achieved},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * pairs_step / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches // max(1, args.steps) * args.steps,
+            "gpu_launches_per_step": launches / max(1, args.steps),
+            "clocks": clocks,
+            "host_wall_ms_per_step": 1e3 * (t1 - t0) / args.steps,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def grid_pairs(plan, wl, lo, hi, dims):
+    """Algorithmic (node, centre) pairs of the grid evaluation (within the cut-off)."""
+    return plan.count_grid_pairs(lo, hi, dims)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="torus1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-rows", type=int, default=20000)
+    ap.add_argument("--ref-rows", type=int, default=20000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

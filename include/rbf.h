@@ -1,0 +1,284 @@
+/*
+ * rbf.h - C ABI of the B300 (sm_103a) Gaussian-RBF implicit-surface library.
+ *
+ * The library implements the computational core of Cuomo, Galletti, Giunta,
+ * Starace, "Surface Reconstruction from Scattered Point via RBF Interpolation on
+ * GPU" (Algorithm 1, steps 1-3):
+ *   step 1  extend the cloud X with off-surface points X+ and X- (Sec. II.A.1)
+ *   step 2  find the interpolant: solve A c = b (Eq. RBFsys) with the Gaussian
+ *           entries of Eq. matrixEntries, truncated at a cut-off so that the
+ *           product A z is local (Sec. III.A), by GMRES with a restricted
+ *           additive Schwarz preconditioner (Sec. III.A), matrix-free
+ *           ("MatShell", Sec. III.B)
+ *   step 3  evaluate P_f on a grid (Eq. matxvet; Algorithm 3 is the paper's
+ *           evaluation kernel)
+ *
+ * Conventions (fixed for every entry point):
+ *   - Kernel.  phi(r) = exp(-r^2 / (2 sigma^2)).  The paper's factor
+ *     1/(sqrt(2 pi) sigma) (Table I, Eq. matrixEntries) is left out: it
+ *     multiplies every weight by the same constant and leaves P_f unchanged.
+ *   - Truncation.  With cut-off factor k > 0 the operator keeps the pairs with
+ *     |c_i - c_j| < k sigma (strict); every dropped entry is below exp(-k^2/2).
+ *     k = 0 means untruncated (dense).  0 <= k <= 12.
+ *   - Centres.  float4 per centre (x, y, z, unused), 16-byte aligned, in the
+ *     order [X; X+; X-] that rbf_build_centers writes (Sec. II.A.1).
+ *   - Memory.  Every array argument is DEVICE memory owned by the caller unless
+ *     a comment says "host".  The library never frees or retains a caller
+ *     pointer beyond the call, except that a plan keeps its own copies of the
+ *     centres it was built from.
+ *   - Streams.  `stream` is a cudaStream_t passed as void*; NULL is the legacy
+ *     default stream.  Work is enqueued on it; calls that return host values
+ *     (reports, counts, info) synchronise that stream before returning.
+ *   - Errors.  Functions return rbf_status and never abort or print.  A
+ *     human-readable reason for the last failure on a context is returned by
+ *     rbf_last_error.  On error, outputs are unspecified.
+ *   - Threads.  A context and the plans made from it may be used by one host
+ *     thread at a time.
+ */
+#ifndef RBF_H
+#define RBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RBF_VERSION 1
+
+typedef enum {
+    RBF_OK = 0,
+    RBF_ERR_INVALID = 1,        /* bad argument: null pointer, size, sigma <= 0, k out of range, non-finite */
+    RBF_ERR_OOM = 2,            /* a device allocation failed */
+    RBF_ERR_CUDA = 3,           /* a CUDA runtime call or kernel launch failed */
+    RBF_ERR_NOT_CONVERGED = 4,  /* solver stopped at its iteration cap above tolerance (weights still valid) */
+    RBF_ERR_BREAKDOWN = 5,      /* Arnoldi produced a non-finite value */
+    RBF_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired */
+    RBF_ERR_NOT_SPD = 7,        /* a block factorisation failed even after the shift escalation */
+    RBF_ERR_UNSUPPORTED = 8     /* configuration outside the implemented range (message says which) */
+} rbf_status;
+
+typedef struct rbf_ctx rbf_ctx;
+typedef struct rbf_plan rbf_plan;
+
+/* Library version (RBF_VERSION of the build). */
+int rbf_version(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all contexts and threads).  Host-only, no device work. */
+int64_t rbf_launch_count(void);
+
+/* Static string naming a status code. */
+const char *rbf_status_string(rbf_status s);
+
+/* Create a context on CUDA device `device` (made current for every call on the
+ * context).  *ctx receives a host-owned handle; destroy it with rbf_ctx_destroy. */
+rbf_status rbf_ctx_create(rbf_ctx **ctx, int device);
+rbf_status rbf_ctx_destroy(rbf_ctx *ctx);
+
+/* Reason for the last failure on this context (empty string if none).  The
+ * pointer stays valid until the next call on the context. */
+const char *rbf_last_error(const rbf_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Step 1 (Sec. II.A.1-2): extended data set.
+ *   pts, nrm : N x 3 float, row-major (x, y, z per point); normals oriented
+ *              outward and of unit length (used as given).
+ *   delta    : offset along the normal; delta <= 0 selects 1% of the diagonal of
+ *              the bounding box of pts (the paper's default, Sec. II.A.1).
+ *   target   : value assigned on X+ (and -target on X-); target <= 0 selects
+ *              `delta` (signed-distance targets).  The paper's +-1 is target = 1.
+ *   centers  : out, 3N float4 (x, y, z, 0): [X; X + delta n; X - delta n].
+ *   targets  : out, 3N float: [0...; +target...; -target...].
+ *   delta_out: host, optional (may be NULL): the delta used.
+ * Errors: RBF_ERR_INVALID for N <= 0, null or misaligned pointers, or a
+ * non-finite coordinate (checked on the device; one stream synchronisation). */
+rbf_status rbf_build_centers(rbf_ctx *ctx, const float *pts, const float *nrm, int64_t N,
+                             float delta, float target, float *centers, float *targets,
+                             float *delta_out, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Plan: the matrix-free operator A~ over a fixed set of centres (the paper's
+ * MatShell, Sec. III.B), i.e. cell binning (Sec. III.A "truncation area",
+ * Algorithm 2) plus the block/tile structure the kernels walk.
+ *
+ * Binning is a definition shared with the tests:
+ *   lo = componentwise minimum of the centres, ext = hi - lo (float32);
+ *   cell edge hc = k sigma / cells_per_cutoff (k > 0), or max(ext)/8 (k = 0;
+ *   1 if ext is 0); fine cells hf = hc / 2^levels; inv = (float)(2^levels / hc)
+ *   computed in double; q_d = floor((c_d - lo_d) * inv) in float32;
+ *   key = Morton interleave (x in bit 0) of q; cell = key >> (3 levels);
+ *   centres are ordered by a stable sort on key.  At most 1024 fine cells per
+ *   axis (RBF_ERR_UNSUPPORTED otherwise).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    float sigma;            /* Gaussian width, > 0 */
+    float k;                /* cut-off factor: pairs with |d| < k sigma; 0 = untruncated */
+    int cells_per_cutoff;   /* s in hc = k sigma / s; 0 selects 1 */
+    int levels;             /* fine levels per cell (0..7); -1 selects 3 */
+} rbf_plan_params;
+
+typedef struct {
+    int64_t n;              /* centres */
+    int64_t ncells;         /* entries of the dense cell table (2^(3(nbits-levels))) */
+    int64_t nblocks;        /* source blocks (runs of <= 32 centres inside one cell) */
+    int64_t nchunks;        /* target tiles (runs of 256 consecutive binned centres) */
+    int64_t pairlist_len;   /* (tile, block) entries that survive the box test */
+    int64_t nsegments;      /* work items of the product kernels */
+    int nbits;              /* Morton bits per axis */
+    int levels;
+    float lo[3];
+    float inv;              /* fine cells per unit length (float32) */
+    float sigma, k;
+} rbf_plan_info;
+
+/* Build a plan over n centres (device float4 array, caller order).  The plan
+ * copies what it needs; `centers` may be freed after the call returns.
+ * Synchronises `stream` once (to size the cell table).
+ * Errors: RBF_ERR_INVALID (n <= 0, sigma <= 0 or non-finite, k < 0 or > 12,
+ * non-finite centre), RBF_ERR_UNSUPPORTED (domain too large for the cell grid),
+ * RBF_ERR_OOM, RBF_ERR_CUDA. */
+rbf_status rbf_plan_create(rbf_ctx *ctx, const float *centers, int64_t n, const rbf_plan_params *p,
+                           rbf_plan **plan, void *stream);
+rbf_status rbf_plan_destroy(rbf_plan *plan);
+
+/* Host-side summary of the plan (no device work). */
+rbf_status rbf_plan_get_info(const rbf_plan *plan, rbf_plan_info *info);
+
+/* Copy the binning out (device pointers, any may be NULL):
+ *   perm       : n int32, perm[p] = caller index of the centre at binned position p
+ *   keys       : n uint32, Morton key of binned position p (sorted, stable)
+ *   cell_start : ncells int32, first binned position of each cell code
+ *   cell_end   : ncells int32, one past the last (start == end == 0 when empty) */
+rbf_status rbf_plan_export_binning(rbf_plan *plan, int32_t *perm, uint32_t *keys, int32_t *cell_start,
+                                   int32_t *cell_end, void *stream);
+
+/* ------------------------------------------------------------------------
+ * The truncated product y = A~ z (Sec. III.A, Eq. matrixEntries), float32
+ * arithmetic with exp2 on the special-function unit, caller order.
+ *   z, y : n float each (may not alias).
+ * Per-pair error: relative ~1e-6 of the term; the cut-off decision is taken in
+ * float32 and can differ from an exact one only for pairs within rounding of
+ * the cut-off radius, whose entries are <= exp(-k^2/2). */
+rbf_status rbf_matvec(rbf_plan *plan, const float *z, float *y, void *stream);
+
+/* Number of algorithmic pairs (i, j) with |c_i - c_j| < k sigma, i = j included
+ * (all n^2 when k = 0), decided in double precision.  `count` is host memory.
+ * Costs about one double-precision product. */
+rbf_status rbf_count_pairs(rbf_plan *plan, int64_t *count, void *stream);
+
+/* True residual in double precision (difference, square distance, exp and
+ * accumulation all float64): r = b - A~ x, caller order.
+ *   b : n float (targets), x : n double, r : n double (out).
+ *   norms : host, optional, [|r|_2, |b|_2]. */
+rbf_status rbf_residual(rbf_plan *plan, const float *b, const double *x, double *r, double *norms,
+                        void *stream);
+
+/* ------------------------------------------------------------------------
+ * Restricted additive Schwarz preconditioner (Sec. III.A, RASM).
+ * Subdomains are defined on the binned order: cores are consecutive runs of
+ * `core` positions; subdomain i is the run of exactly min(block, n) positions
+ * starting at clamp(s_i - (block - core)/2, 0, n - block), s_i = i*core.  A_i is
+ * the untruncated Gaussian matrix of subdomain i, factorised in float32 as
+ * A_i + shift*I = L_i L_i^T.  With restricted = 1 the apply writes only the core
+ * entries of each local solve (RASM); with restricted = 0 it adds whole local
+ * solves (additive Schwarz, float atomics: not bitwise reproducible).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int core;               /* positions per core, 1 <= core <= block */
+    int block;              /* subdomain size, 1 <= block <= 128 */
+    float shift;            /* diagonal shift (absolute; diag(A) = 1), >= 0 */
+    int restricted;         /* 1 = RASM (default), 0 = additive */
+    int escalate;           /* if non-zero, a failed block retries with shift*10 up to 4 times */
+} rbf_schwarz_params;
+
+/* Assemble and factorise all blocks.  `failed` (host, optional) receives the
+ * number of blocks whose factorisation still failed; such blocks act as the
+ * identity.  Returns RBF_ERR_NOT_SPD if failed > 0 (the preconditioner is still
+ * usable). */
+rbf_status rbf_schwarz_setup(rbf_plan *plan, const rbf_schwarz_params *p, int64_t *failed, void *stream);
+
+/* z = M^-1 v with the factorised blocks, caller order, float in and out. */
+rbf_status rbf_schwarz_apply(rbf_plan *plan, const float *v, float *z, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Step 2: flexible GMRES(m) with right preconditioning (Sec. III.A: GMRES with
+ * RASM).  Precision: product and preconditioner in float32; Arnoldi basis,
+ * classical Gram-Schmidt applied twice, Hessenberg least squares and the
+ * solution vector in float64.  Each restart recomputes the true residual with
+ * rbf_residual's float64 kernel (iterative refinement: x += GMRES(b - A~ x)).
+ * ------------------------------------------------------------------------ */
+enum { RBF_PRECOND_NONE = 0, RBF_PRECOND_SCHWARZ = 1 };
+
+typedef struct {
+    int m;                  /* restart length, 1..512 (default 50 when 0) */
+    int max_it;             /* cap on inner iterations in total (default 500 when 0) */
+    double tol;             /* stop when |b - A~ x|_2 <= tol |b|_2 (default 1e-6 when 0) */
+    int precond;            /* RBF_PRECOND_* */
+    rbf_schwarz_params schwarz;
+    int fixed_iterations;   /* non-zero: run exactly max_it iterations, ignoring tol */
+    int true_residual_each_restart; /* non-zero (default): float64 residual at every restart;
+                                       zero: only at the end, the restart uses the estimate */
+} rbf_solve_params;
+
+typedef struct {
+    int iterations;         /* inner iterations (products) performed */
+    int restarts;           /* completed cycles */
+    int converged;          /* 1 if the true residual met tol */
+    int precond_failed_blocks;
+    double residual_estimate;   /* last |g_{j+1}| / |b| from the Givens recursion */
+    double residual_true;       /* final |b - A~ x| / |b| in float64 */
+    double ms_setup;            /* preconditioner set-up, milliseconds (CUDA events) */
+    double ms_solve;            /* iterations incl. true residuals, milliseconds */
+    int64_t matvec_pairs;       /* float32 product pair evaluations (algorithmic pairs x products),
+                                   0 if the plan has not counted its pairs */
+    int matvec_launches;        /* float32 products inside the solve */
+    int residual_launches;      /* float64 true-residual products inside the solve */
+    double ms_matvec;           /* summed CUDA-event time of the float32 products */
+    double ms_residual;         /* summed CUDA-event time of the float64 residual products */
+    double ms_precond;          /* summed CUDA-event time of the preconditioner applications */
+} rbf_report;
+
+/* Solve A~ x = b on a plan.  b: n float (caller order); x: n double (out,
+ * caller order).  `report` (host) may be NULL.  Returns RBF_ERR_NOT_CONVERGED
+ * when the cap is reached above tol (x holds the last iterate; with
+ * fixed_iterations this is RBF_OK). */
+rbf_status rbf_plan_solve(rbf_plan *plan, const float *b, const rbf_solve_params *p, double *x,
+                          rbf_report *report, void *stream);
+
+/* One-shot form of the paper's step 2: builds a plan, solves, frees the plan. */
+rbf_status rbf_solve(rbf_ctx *ctx, const float *centers, const float *targets, int64_t n,
+                     const rbf_plan_params *pp, const rbf_solve_params *sp, double *weights,
+                     rbf_report *report, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Step 3 (Eq. matxvet): P_f at the nodes of a structured grid,
+ * xi = lo + i (hi - lo)/(dims - 1) per axis (dims = 1 puts the node at lo),
+ * written x fastest: f[(iz * dims[1] + iy) * dims[0] + ix].  The sum uses the
+ * plan's cut-off (k sigma, or untruncated when k = 0); float32 arithmetic.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    float lo[3];
+    float hi[3];
+    int64_t dims[3];        /* each >= 1; product < 2^31 */
+} rbf_grid;
+
+/* weights: n double (caller order); f: dims product float (out). */
+rbf_status rbf_plan_eval_grid(rbf_plan *plan, const double *weights, const rbf_grid *g, float *f,
+                              void *stream);
+
+/* Number of (node, centre) pairs within the cut-off for this grid (nodes x n
+ * when k = 0), decided in double precision on the float32 node coordinates the
+ * evaluation uses.  `count` is host memory. */
+rbf_status rbf_count_grid_pairs(rbf_plan *plan, const rbf_grid *g, int64_t *count, void *stream);
+
+/* One-shot form: plan from (centers, n, pp), evaluate, free. */
+rbf_status rbf_eval_grid(rbf_ctx *ctx, const float *centers, const double *weights, int64_t n,
+                         const rbf_plan_params *pp, const rbf_grid *g, float *f, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBF_H */

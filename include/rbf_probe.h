@@ -1,0 +1,35 @@
+/*
+ * rbf_probe.h - measurement helper of librbf.so (not part of the paper's method).
+ *
+ * Measures the per-SM issue rates that bound the Gaussian product kernels:
+ * ex2.approx.f32 (the special-function unit), scalar FP32 FMA and packed
+ * f32x2 FMA, each as operations per SM per clock, with the SM clock derived
+ * from the cycle counter and the global nanosecond timer of the probe run.
+ * These are the denominators of the product kernels' roofline.
+ */
+#ifndef RBF_PROBE_H
+#define RBF_PROBE_H
+
+#include "rbf.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int num_sms;
+    double sm_mhz;                  /* SM clock during the probe (cycles / ns * 1000) */
+    double ex2_per_clk_sm;          /* MUFU.EX2 results per SM per clock */
+    double ffma_per_clk_sm;         /* scalar FP32 FMA per SM per clock */
+    double ffma2_lanes_per_clk_sm;  /* packed f32x2 FMA, FP32 lanes per SM per clock */
+} rbf_probe_result;
+
+/* Runs three short kernels (about 10 ms each) on `device` (default stream) and
+ * fills *r.  Errors: RBF_ERR_INVALID (null r), RBF_ERR_CUDA. */
+rbf_status rbf_probe_peaks(int device, rbf_probe_result *r);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBF_PROBE_H */

@@ -1,0 +1,377 @@
+"""Python binding of ``librbf.so`` (the C ABI in ``include/rbf.h``).
+
+Argument marshalling only: torch supplies device memory and the current CUDA
+stream; every step of the computation runs in the library's CUDA kernels.
+There is no fallback: if the shared library is missing or no CUDA device is
+present, calls raise.
+
+Typical use (Algorithm 1 of the paper, steps 1-3)::
+
+    import torch, paper_1305_5179_b300 as rbf
+    ctx = rbf.Context(0)
+    C, b, delta = rbf.build_centers(ctx, pts, nrm, delta=0.01)     # step 1
+    plan = rbf.Plan(ctx, C, sigma=0.02, k=6.0)                     # binning
+    x, rep = plan.solve(b, precond="schwarz", core=96, block=128)  # step 2
+    f = plan.eval_grid(x, lo, hi, dims)                            # step 3
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "librbf.so")
+
+RBF_OK = 0
+STATUS = {0: "RBF_OK", 1: "RBF_ERR_INVALID", 2: "RBF_ERR_OOM", 3: "RBF_ERR_CUDA", 4: "RBF_ERR_NOT_CONVERGED",
+          5: "RBF_ERR_BREAKDOWN", 6: "RBF_ERR_TIMEOUT", 7: "RBF_ERR_NOT_SPD", 8: "RBF_ERR_UNSUPPORTED"}
+PRECOND = {"none": 0, "schwarz": 1}
+
+# every entry point declared in include/rbf.h
+EXPORTS = (
+    "rbf_version", "rbf_launch_count", "rbf_probe_peaks", "rbf_status_string", "rbf_ctx_create", "rbf_ctx_destroy", "rbf_last_error",
+    "rbf_build_centers", "rbf_plan_create", "rbf_plan_destroy", "rbf_plan_get_info", "rbf_plan_export_binning",
+    "rbf_matvec", "rbf_count_pairs", "rbf_residual", "rbf_schwarz_setup", "rbf_schwarz_apply",
+    "rbf_plan_solve", "rbf_solve", "rbf_plan_eval_grid", "rbf_count_grid_pairs", "rbf_eval_grid",
+)
+
+
+class RbfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class PlanParams(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_float), ("k", ctypes.c_float), ("cells_per_cutoff", ctypes.c_int),
+                ("levels", ctypes.c_int)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("ncells", ctypes.c_int64), ("nblocks", ctypes.c_int64),
+                ("nchunks", ctypes.c_int64), ("pairlist_len", ctypes.c_int64), ("nsegments", ctypes.c_int64),
+                ("nbits", ctypes.c_int), ("levels", ctypes.c_int), ("lo", ctypes.c_float * 3),
+                ("inv", ctypes.c_float), ("sigma", ctypes.c_float), ("k", ctypes.c_float)]
+
+
+class SchwarzParams(ctypes.Structure):
+    _fields_ = [("core", ctypes.c_int), ("block", ctypes.c_int), ("shift", ctypes.c_float),
+                ("restricted", ctypes.c_int), ("escalate", ctypes.c_int)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("max_it", ctypes.c_int), ("tol", ctypes.c_double), ("precond", ctypes.c_int),
+                ("schwarz", SchwarzParams), ("fixed_iterations", ctypes.c_int),
+                ("true_residual_each_restart", ctypes.c_int)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("converged", ctypes.c_int),
+                ("precond_failed_blocks", ctypes.c_int), ("residual_estimate", ctypes.c_double),
+                ("residual_true", ctypes.c_double), ("ms_setup", ctypes.c_double), ("ms_solve", ctypes.c_double),
+                ("matvec_pairs", ctypes.c_int64), ("matvec_launches", ctypes.c_int),
+                ("residual_launches", ctypes.c_int), ("ms_matvec", ctypes.c_double), ("ms_residual", ctypes.c_double),
+                ("ms_precond", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ProbeResult(ctypes.Structure):
+    _fields_ = [("num_sms", ctypes.c_int), ("sm_mhz", ctypes.c_double), ("ex2_per_clk_sm", ctypes.c_double),
+                ("ffma_per_clk_sm", ctypes.c_double), ("ffma2_lanes_per_clk_sm", ctypes.c_double)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3), ("dims", ctypes.c_int64 * 3)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``librbf.so`` (built by ``paper_1305_5179_b300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIBPATH):
+        raise ImportError(f"{LIBPATH} is missing: run `python -m paper_1305_5179_b300.build`")
+    L = ctypes.CDLL(LIBPATH)
+    P, I64, I, F, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_double
+    sig = {
+        "rbf_version": ([], I),
+        "rbf_launch_count": ([], I64),
+        "rbf_probe_peaks": ([I, ctypes.POINTER(ProbeResult)], I),
+        "rbf_status_string": ([I], ctypes.c_char_p),
+        "rbf_ctx_create": ([ctypes.POINTER(P), I], I),
+        "rbf_ctx_destroy": ([P], I),
+        "rbf_last_error": ([P], ctypes.c_char_p),
+        "rbf_build_centers": ([P, P, P, I64, F, F, P, P, ctypes.POINTER(F), P], I),
+        "rbf_plan_create": ([P, P, I64, ctypes.POINTER(PlanParams), ctypes.POINTER(P), P], I),
+        "rbf_plan_destroy": ([P], I),
+        "rbf_plan_get_info": ([P, ctypes.POINTER(PlanInfo)], I),
+        "rbf_plan_export_binning": ([P, P, P, P, P, P], I),
+        "rbf_matvec": ([P, P, P, P], I),
+        "rbf_count_pairs": ([P, ctypes.POINTER(I64), P], I),
+        "rbf_residual": ([P, P, P, P, ctypes.POINTER(D), P], I),
+        "rbf_schwarz_setup": ([P, ctypes.POINTER(SchwarzParams), ctypes.POINTER(I64), P], I),
+        "rbf_schwarz_apply": ([P, P, P, P], I),
+        "rbf_plan_solve": ([P, P, ctypes.POINTER(SolveParams), P, ctypes.POINTER(Report), P], I),
+        "rbf_solve": ([P, P, P, I64, ctypes.POINTER(PlanParams), ctypes.POINTER(SolveParams), P,
+                       ctypes.POINTER(Report), P], I),
+        "rbf_plan_eval_grid": ([P, P, ctypes.POINTER(Grid), P, P], I),
+        "rbf_count_grid_pairs": ([P, ctypes.POINTER(Grid), ctypes.POINTER(I64), P], I),
+        "rbf_eval_grid": ([P, P, P, I64, ctypes.POINTER(PlanParams), ctypes.POINTER(Grid), P, P], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _req(t, dtype, name, n=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+    return t
+
+
+class Context:
+    """A library context bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._h = ctypes.c_void_p()
+        st = lib().rbf_ctx_create(ctypes.byref(self._h), int(device))
+        if st != RBF_OK:
+            raise RbfError(st, f"rbf_ctx_create(device={device}) failed")
+        self.device = int(device)
+
+    def check(self, st: int, what: str, allow=()):
+        if st != RBF_OK and st not in allow:
+            msg = lib().rbf_last_error(self._h)
+            raise RbfError(st, f"{what}: {msg.decode() if msg else ''}")
+        return st
+
+    def close(self):
+        if self._h:
+            lib().rbf_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(lib().rbf_launch_count())
+
+
+def probe_peaks(device: int = 0) -> dict:
+    """Measured MUFU.EX2 / FFMA / FFMA2 rates per SM per clock and the SM clock."""
+    r = ProbeResult()
+    st = lib().rbf_probe_peaks(int(device), ctypes.byref(r))
+    if st != RBF_OK:
+        raise RbfError(st, "rbf_probe_peaks")
+    return {f: getattr(r, f) for f, _ in r._fields_}
+
+
+def build_centers(ctx: Context, pts, nrm, delta: float = 0.0, target: float = 0.0, stream=None):
+    """Step 1: extended set [X; X + delta n; X - delta n] (float4) and targets."""
+    import torch
+    _req(pts, torch.float32, "pts")
+    _req(nrm, torch.float32, "nrm", pts.numel())
+    N = pts.numel() // 3
+    C = torch.empty((3 * N, 4), dtype=torch.float32, device=pts.device)
+    b = torch.empty(3 * N, dtype=torch.float32, device=pts.device)
+    d = ctypes.c_float(0)
+    ctx.check(lib().rbf_build_centers(ctx._h, _ptr(pts), _ptr(nrm), N, float(delta), float(target), _ptr(C), _ptr(b),
+                                      ctypes.byref(d), _stream(stream)), "rbf_build_centers")
+    return C, b, float(d.value)
+
+
+def _grid(lo, hi, dims) -> Grid:
+    g = Grid()
+    for i in range(3):
+        g.lo[i] = float(lo[i])
+        g.hi[i] = float(hi[i])
+        g.dims[i] = int(dims[i])
+    return g
+
+
+def _solve_params(m=50, max_it=500, tol=1e-6, precond="none", core=96, block=128, shift=1e-4, restricted=True,
+                  escalate=True, fixed_iterations=False, true_residual_each_restart=True) -> SolveParams:
+    sp = SolveParams()
+    sp.m, sp.max_it, sp.tol = int(m), int(max_it), float(tol)
+    sp.precond = PRECOND[precond] if isinstance(precond, str) else int(precond)
+    sp.schwarz = SchwarzParams(int(core), int(block), float(shift), int(bool(restricted)), int(bool(escalate)))
+    sp.fixed_iterations = int(bool(fixed_iterations))
+    sp.true_residual_each_restart = int(bool(true_residual_each_restart))
+    return sp
+
+
+class Plan:
+    """The matrix-free truncated Gaussian operator over a fixed set of centres."""
+
+    def __init__(self, ctx: Context, centers, sigma: float, k: float = 0.0, cells_per_cutoff: int = 1,
+                 levels: int = 3, stream=None):
+        import torch
+        _req(centers, torch.float32, "centers")
+        if centers.dim() != 2 or centers.shape[1] != 4:
+            raise ValueError("centers must be (n, 4) float32")
+        self.ctx = ctx
+        self.n = int(centers.shape[0])
+        self.device = centers.device
+        self.params = PlanParams(float(sigma), float(k), int(cells_per_cutoff), int(levels))
+        self._h = ctypes.c_void_p()
+        ctx.check(lib().rbf_plan_create(ctx._h, _ptr(centers), self.n, ctypes.byref(self.params),
+                                        ctypes.byref(self._h), _stream(stream)), "rbf_plan_create")
+
+    def close(self):
+        if self._h:
+            lib().rbf_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        pi = PlanInfo()
+        self.ctx.check(lib().rbf_plan_get_info(self._h, ctypes.byref(pi)), "rbf_plan_get_info")
+        d = {f: getattr(pi, f) for f, _ in pi._fields_}
+        d["lo"] = [pi.lo[i] for i in range(3)]
+        return d
+
+    def export_binning(self, stream=None):
+        import torch
+        info = self.info()
+        perm = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        keys = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        cs = torch.empty(info["ncells"], dtype=torch.int32, device=self.device)
+        ce = torch.empty(info["ncells"], dtype=torch.int32, device=self.device)
+        self.ctx.check(lib().rbf_plan_export_binning(self._h, _ptr(perm), _ptr(keys), _ptr(cs), _ptr(ce),
+                                                     _stream(stream)), "rbf_plan_export_binning")
+        return perm, keys, cs, ce
+
+    def matvec(self, z, out=None, stream=None):
+        import torch
+        _req(z, torch.float32, "z", self.n)
+        y = torch.empty_like(z) if out is None else _req(out, torch.float32, "out", self.n)
+        self.ctx.check(lib().rbf_matvec(self._h, _ptr(z), _ptr(y), _stream(stream)), "rbf_matvec")
+        return y
+
+    def count_pairs(self, stream=None) -> int:
+        c = ctypes.c_int64(0)
+        self.ctx.check(lib().rbf_count_pairs(self._h, ctypes.byref(c), _stream(stream)), "rbf_count_pairs")
+        return int(c.value)
+
+    def residual(self, b, x, stream=None):
+        import torch
+        _req(b, torch.float32, "b", self.n)
+        _req(x, torch.float64, "x", self.n)
+        r = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        norms = (ctypes.c_double * 2)()
+        self.ctx.check(lib().rbf_residual(self._h, _ptr(b), _ptr(x), _ptr(r), norms, _stream(stream)), "rbf_residual")
+        return r, (norms[0], norms[1])
+
+    def schwarz_setup(self, core=96, block=128, shift=1e-4, restricted=True, escalate=False, stream=None) -> int:
+        p = SchwarzParams(int(core), int(block), float(shift), int(bool(restricted)), int(bool(escalate)))
+        f = ctypes.c_int64(0)
+        self.ctx.check(lib().rbf_schwarz_setup(self._h, ctypes.byref(p), ctypes.byref(f), _stream(stream)),
+                       "rbf_schwarz_setup", allow=(7,))
+        return int(f.value)
+
+    def schwarz_apply(self, v, stream=None):
+        import torch
+        _req(v, torch.float32, "v", self.n)
+        z = torch.empty_like(v)
+        self.ctx.check(lib().rbf_schwarz_apply(self._h, _ptr(v), _ptr(z), _stream(stream)), "rbf_schwarz_apply")
+        return z
+
+    def solve(self, b, x=None, stream=None, **kw):
+        """Step 2: FGMRES on A~ x = b.  Keyword arguments as ``_solve_params``.
+        Returns (x float64, report dict); does not raise on NOT_CONVERGED."""
+        import torch
+        _req(b, torch.float32, "b", self.n)
+        x = torch.empty(self.n, dtype=torch.float64, device=self.device) if x is None else x
+        rep = Report()
+        sp = _solve_params(**kw)
+        st = lib().rbf_plan_solve(self._h, _ptr(b), ctypes.byref(sp), _ptr(x), ctypes.byref(rep), _stream(stream))
+        self.ctx.check(st, "rbf_plan_solve", allow=(4,))
+        d = rep.as_dict()
+        d["status"] = STATUS[st]
+        return x, d
+
+    def count_grid_pairs(self, lo, hi, dims, stream=None) -> int:
+        g = _grid(lo, hi, dims)
+        c = ctypes.c_int64(0)
+        self.ctx.check(lib().rbf_count_grid_pairs(self._h, ctypes.byref(g), ctypes.byref(c), _stream(stream)),
+                       "rbf_count_grid_pairs")
+        return int(c.value)
+
+    def eval_grid(self, weights, lo, hi, dims, out=None, stream=None):
+        """Step 3: P_f on the grid, shape (dims[2], dims[1], dims[0]) float32."""
+        import torch
+        _req(weights, torch.float64, "weights", self.n)
+        f = torch.empty((int(dims[2]), int(dims[1]), int(dims[0])), dtype=torch.float32,
+                        device=self.device) if out is None else out
+        g = _grid(lo, hi, dims)
+        self.ctx.check(lib().rbf_plan_eval_grid(self._h, _ptr(weights), ctypes.byref(g), _ptr(f), _stream(stream)),
+                       "rbf_plan_eval_grid")
+        return f
+
+
+def solve(ctx: Context, centers, targets, sigma: float, k: float = 0.0, stream=None, **kw):
+    """One-shot step 2 (plan + FGMRES + free)."""
+    import torch
+    _req(centers, torch.float32, "centers")
+    n = centers.shape[0]
+    _req(targets, torch.float32, "targets", n)
+    pp = PlanParams(float(sigma), float(k), 1, 3)
+    x = torch.empty(n, dtype=torch.float64, device=centers.device)
+    rep = Report()
+    sp = _solve_params(**kw)
+    st = lib().rbf_solve(ctx._h, _ptr(centers), _ptr(targets), n, ctypes.byref(pp), ctypes.byref(sp), _ptr(x),
+                         ctypes.byref(rep), _stream(stream))
+    ctx.check(st, "rbf_solve", allow=(4,))
+    d = rep.as_dict()
+    d["status"] = STATUS[st]
+    return x, d
+
+
+def eval_grid(ctx: Context, centers, weights, sigma: float, k: float, lo, hi, dims, stream=None):
+    """One-shot step 3."""
+    import torch
+    _req(centers, torch.float32, "centers")
+    n = centers.shape[0]
+    _req(weights, torch.float64, "weights", n)
+    pp = PlanParams(float(sigma), float(k), 1, 3)
+    f = torch.empty((int(dims[2]), int(dims[1]), int(dims[0])), dtype=torch.float32, device=centers.device)
+    g = _grid(lo, hi, dims)
+    ctx.check(lib().rbf_eval_grid(ctx._h, _ptr(centers), _ptr(weights), n, ctypes.byref(pp), ctypes.byref(g), _ptr(f),
+                                  _stream(stream)), "rbf_eval_grid")
+    return f

@@ -1,0 +1,329 @@
+// extern "C" entry points (include/rbf.h): argument checks, device selection,
+// error translation.  No arithmetic of the method lives here.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "centers.cuh"
+#include "plan.cuh"
+
+static std::atomic<long long> g_launches{0};
+void rbf_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+template <typename F>
+rbf_status guarded(rbf_ctx *ctx, F &&f) {
+    if (!ctx) return RBF_ERR_INVALID;
+    try {
+        ctx->last_error.clear();
+        cudaError_t e = cudaSetDevice(ctx->device);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            ctx->last_error = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+            return RBF_ERR_CUDA;
+        }
+        return f();
+    } catch (const RbfError &err) {
+        ctx->last_error = err.msg;
+        return err.status;
+    } catch (const std::bad_alloc &) {
+        ctx->last_error = "host allocation failed";
+        return RBF_ERR_OOM;
+    } catch (...) {
+        ctx->last_error = "unknown exception";
+        return RBF_ERR_CUDA;
+    }
+}
+
+inline cudaStream_t S(void *s) { return (cudaStream_t)s; }
+
+inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+void check_plan_params(const rbf_plan_params *p) {
+    RBF_CHECK(p, RBF_ERR_INVALID, "null plan parameters");
+    RBF_CHECK(std::isfinite(p->sigma) && p->sigma > 0.f, RBF_ERR_INVALID, "sigma must be finite and > 0");
+    RBF_CHECK(std::isfinite(p->k) && p->k >= 0.f && p->k <= 12.f, RBF_ERR_INVALID, "k must be in [0, 12]");
+    RBF_CHECK(p->cells_per_cutoff >= 0 && p->cells_per_cutoff <= 4, RBF_ERR_INVALID, "cells_per_cutoff in 0..4");
+    RBF_CHECK(p->levels >= -1 && p->levels <= 7, RBF_ERR_INVALID, "levels in -1..7");
+}
+
+rbf_plan *make_plan(rbf_ctx *ctx, const float *centers, int64_t n, const rbf_plan_params *p, cudaStream_t s) {
+    check_plan_params(p);
+    RBF_CHECK(centers && aligned16(centers), RBF_ERR_INVALID, "centers must be a 16-byte aligned device pointer");
+    RBF_CHECK(n > 0 && n < (1LL << 31) - 1, RBF_ERR_INVALID, "n = %lld out of range", (long long)n);
+    rbf_plan *P = new rbf_plan();
+    try {
+        P->ctx = ctx;
+        P->n = n;
+        P->sigma = p->sigma;
+        P->k = p->k;
+        P->cells_per_cutoff = p->cells_per_cutoff > 0 ? p->cells_per_cutoff : 1;
+        P->levels = p->levels >= 0 ? p->levels : 3;
+        plan_build(P, (const float4 *)centers, s);
+    } catch (...) {
+        delete P;
+        throw;
+    }
+    return P;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rbf_version(void) { return RBF_VERSION; }
+
+int64_t rbf_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+const char *rbf_status_string(rbf_status s) {
+    switch (s) {
+        case RBF_OK: return "RBF_OK";
+        case RBF_ERR_INVALID: return "RBF_ERR_INVALID";
+        case RBF_ERR_OOM: return "RBF_ERR_OOM";
+        case RBF_ERR_CUDA: return "RBF_ERR_CUDA";
+        case RBF_ERR_NOT_CONVERGED: return "RBF_ERR_NOT_CONVERGED";
+        case RBF_ERR_BREAKDOWN: return "RBF_ERR_BREAKDOWN";
+        case RBF_ERR_TIMEOUT: return "RBF_ERR_TIMEOUT";
+        case RBF_ERR_NOT_SPD: return "RBF_ERR_NOT_SPD";
+        case RBF_ERR_UNSUPPORTED: return "RBF_ERR_UNSUPPORTED";
+    }
+    return "RBF_UNKNOWN_STATUS";
+}
+
+rbf_status rbf_ctx_create(rbf_ctx **ctx, int device) {
+    if (!ctx) return RBF_ERR_INVALID;
+    *ctx = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        (void)cudaGetLastError();
+        return RBF_ERR_CUDA;
+    }
+    rbf_ctx *c = new (std::nothrow) rbf_ctx();
+    if (!c) return RBF_ERR_OOM;
+    c->device = device;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete c;
+        return RBF_ERR_CUDA;
+    }
+    *ctx = c;
+    return RBF_OK;
+}
+
+rbf_status rbf_ctx_destroy(rbf_ctx *ctx) {
+    delete ctx;
+    return RBF_OK;
+}
+
+const char *rbf_last_error(const rbf_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+rbf_status rbf_build_centers(rbf_ctx *ctx, const float *pts, const float *nrm, int64_t N, float delta, float target,
+                             float *centers, float *targets, float *delta_out, void *stream) {
+    return guarded(ctx, [&]() {
+        RBF_CHECK(pts && nrm && centers && targets, RBF_ERR_INVALID, "null pointer argument");
+        RBF_CHECK(aligned16(centers), RBF_ERR_INVALID, "centers must be 16-byte aligned");
+        RBF_CHECK(N > 0 && 3 * N < (1LL << 31) - 1, RBF_ERR_INVALID, "N = %lld out of range", (long long)N);
+        RBF_CHECK(std::isfinite(delta) && std::isfinite(target), RBF_ERR_INVALID, "non-finite delta or target");
+        float d = build_centers(pts, nrm, N, delta, target, centers, targets, S(stream));
+        if (delta_out) *delta_out = d;
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_plan_create(rbf_ctx *ctx, const float *centers, int64_t n, const rbf_plan_params *p, rbf_plan **plan,
+                           void *stream) {
+    if (plan) *plan = nullptr;
+    return guarded(ctx, [&]() {
+        RBF_CHECK(plan, RBF_ERR_INVALID, "null plan output");
+        *plan = make_plan(ctx, centers, n, p, S(stream));
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_plan_destroy(rbf_plan *plan) {
+    if (!plan) return RBF_OK;
+    cudaSetDevice(plan->ctx->device);
+    delete plan;
+    return RBF_OK;
+}
+
+rbf_status rbf_plan_get_info(const rbf_plan *P, rbf_plan_info *info) {
+    if (!P || !info) return RBF_ERR_INVALID;
+    std::memset(info, 0, sizeof(*info));
+    info->n = P->n;
+    info->ncells = P->ncells;
+    info->nblocks = P->nblk;
+    info->nchunks = P->nchk;
+    info->pairlist_len = P->pl.len;
+    info->nsegments = P->pl.nseg;
+    info->nbits = P->nbits;
+    info->levels = P->levels;
+    for (int d = 0; d < 3; ++d) info->lo[d] = P->lo[d];
+    info->inv = P->inv;
+    info->sigma = P->sigma;
+    info->k = P->k;
+    return RBF_OK;
+}
+
+rbf_status rbf_plan_export_binning(rbf_plan *P, int32_t *perm, uint32_t *keys, int32_t *cell_start, int32_t *cell_end,
+                                   void *stream) {
+    if (!P) return RBF_ERR_INVALID;
+    return guarded(P->ctx, [&]() {
+        cudaStream_t s = S(stream);
+        if (perm) RBF_CUDA(cudaMemcpyAsync(perm, P->perm.p, P->n * 4, cudaMemcpyDeviceToDevice, s));
+        if (keys) RBF_CUDA(cudaMemcpyAsync(keys, P->keys.p, P->n * 4, cudaMemcpyDeviceToDevice, s));
+        if (cell_start) RBF_CUDA(cudaMemcpyAsync(cell_start, P->cell_start.p, P->ncells * 4, cudaMemcpyDeviceToDevice, s));
+        if (cell_end) RBF_CUDA(cudaMemcpyAsync(cell_end, P->cell_end.p, P->ncells * 4, cudaMemcpyDeviceToDevice, s));
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_matvec(rbf_plan *P, const float *z, float *y, void *stream) {
+    if (!P) return RBF_ERR_INVALID;
+    return guarded(P->ctx, [&]() {
+        RBF_CHECK(z && y && z != y, RBF_ERR_INVALID, "z and y must be distinct device pointers");
+        cudaStream_t s = S(stream);
+        P->zs.ensure(P->n, s);
+        P->ys.ensure(P->n, s);
+        permute_to_binned_f32(P, z, P->zs.p, s);
+        matvec_binned(P, P->zs.p, P->ys.p, s);
+        permute_from_binned_f32(P, P->ys.p, y, s);
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_count_pairs(rbf_plan *P, int64_t *count, void *stream) {
+    if (!P) return RBF_ERR_INVALID;
+    return guarded(P->ctx, [&]() {
+        RBF_CHECK(count, RBF_ERR_INVALID, "null count");
+        *count = count_pairs(P, S(stream));
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_residual(rbf_plan *P, const float *b, const double *x, double *r, double *norms, void *stream) {
+    if (!P) return RBF_ERR_INVALID;
+    return guarded(P->ctx, [&]() {
+        RBF_CHECK(b && x && r, RBF_ERR_INVALID, "null pointer argument");
+        cudaStream_t s = S(stream);
+        DevBuf<float> bs;
+        DevBuf<double> xs, rs;
+        bs.alloc(P->n, s);
+        xs.alloc(P->n, s);
+        rs.alloc(P->n, s);
+        permute_to_binned_f32(P, b, bs.p, s);
+        permute_to_binned_f64(P, x, xs.p, s);
+        residual_binned_f64(P, bs.p, xs.p, rs.p, nullptr, s);
+        permute_from_binned_f64(P, rs.p, r, s);
+        if (norms) {
+            std::vector<double> hr(P->n);
+            std::vector<float> hb(P->n);
+            RBF_CUDA(cudaMemcpyAsync(hr.data(), rs.p, P->n * 8, cudaMemcpyDeviceToHost, s));
+            RBF_CUDA(cudaMemcpyAsync(hb.data(), bs.p, P->n * 4, cudaMemcpyDeviceToHost, s));
+            RBF_CUDA(cudaStreamSynchronize(s));
+            double a = 0, c = 0;
+            for (int64_t i = 0; i < P->n; ++i) {
+                a += hr[i] * hr[i];
+                c += (double)hb[i] * (double)hb[i];
+            }
+            norms[0] = std::sqrt(a);
+            norms[1] = std::sqrt(c);
+        }
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_schwarz_setup(rbf_plan *P, const rbf_schwarz_params *p, int64_t *failed, void *stream) {
+    if (!P) return RBF_ERR_INVALID;
+    return guarded(P->ctx, [&]() {
+        RBF_CHECK(p, RBF_ERR_INVALID, "null schwarz parameters");
+        int64_t f = 0;
+        schwarz_setup(P, *p, &f, S(stream));
+        if (failed) *failed = f;
+        return f > 0 ? RBF_ERR_NOT_SPD : RBF_OK;
+    });
+}
+
+rbf_status rbf_schwarz_apply(rbf_plan *P, const float *v, float *z, void *stream) {
+    if (!P) return RBF_ERR_INVALID;
+    return guarded(P->ctx, [&]() {
+        RBF_CHECK(v && z && v != z, RBF_ERR_INVALID, "v and z must be distinct device pointers");
+        cudaStream_t s = S(stream);
+        P->zs.ensure(P->n, s);
+        P->ys.ensure(P->n, s);
+        permute_to_binned_f32(P, v, P->zs.p, s);
+        schwarz_apply_binned(P, nullptr, P->zs.p, P->ys.p, s);
+        permute_from_binned_f32(P, P->ys.p, z, s);
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_plan_solve(rbf_plan *P, const float *b, const rbf_solve_params *p, double *x, rbf_report *report,
+                          void *stream) {
+    if (!P) return RBF_ERR_INVALID;
+    return guarded(P->ctx, [&]() {
+        RBF_CHECK(b && p && x, RBF_ERR_INVALID, "null pointer argument");
+        RBF_CHECK(p->precond == RBF_PRECOND_NONE || p->precond == RBF_PRECOND_SCHWARZ, RBF_ERR_INVALID,
+                  "unknown preconditioner %d", p->precond);
+        RBF_CHECK(std::isfinite(p->tol) && p->tol >= 0, RBF_ERR_INVALID, "tol must be finite and >= 0");
+        return fgmres_solve(P, b, *p, x, report, S(stream));
+    });
+}
+
+rbf_status rbf_solve(rbf_ctx *ctx, const float *centers, const float *targets, int64_t n, const rbf_plan_params *pp,
+                     const rbf_solve_params *sp, double *weights, rbf_report *report, void *stream) {
+    return guarded(ctx, [&]() {
+        RBF_CHECK(targets && sp && weights, RBF_ERR_INVALID, "null pointer argument");
+        rbf_plan *P = make_plan(ctx, centers, n, pp, S(stream));
+        rbf_status st;
+        try {
+            st = fgmres_solve(P, targets, *sp, weights, report, S(stream));
+        } catch (...) {
+            delete P;
+            throw;
+        }
+        cudaStreamSynchronize(S(stream));
+        delete P;
+        return st;
+    });
+}
+
+rbf_status rbf_plan_eval_grid(rbf_plan *P, const double *weights, const rbf_grid *g, float *f, void *stream) {
+    if (!P) return RBF_ERR_INVALID;
+    return guarded(P->ctx, [&]() {
+        RBF_CHECK(weights && g && f, RBF_ERR_INVALID, "null pointer argument");
+        eval_grid(P, weights, *g, f, S(stream));
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_count_grid_pairs(rbf_plan *P, const rbf_grid *g, int64_t *count, void *stream) {
+    if (!P) return RBF_ERR_INVALID;
+    return guarded(P->ctx, [&]() {
+        RBF_CHECK(g && count, RBF_ERR_INVALID, "null pointer argument");
+        *count = count_grid_pairs(P, *g, S(stream));
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_eval_grid(rbf_ctx *ctx, const float *centers, const double *weights, int64_t n,
+                         const rbf_plan_params *pp, const rbf_grid *g, float *f, void *stream) {
+    return guarded(ctx, [&]() {
+        RBF_CHECK(weights && g && f, RBF_ERR_INVALID, "null pointer argument");
+        rbf_plan *P = make_plan(ctx, centers, n, pp, S(stream));
+        try {
+            eval_grid(P, weights, *g, f, S(stream));
+        } catch (...) {
+            delete P;
+            throw;
+        }
+        cudaStreamSynchronize(S(stream));
+        delete P;
+        return RBF_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,452 @@
+// The truncated Gaussian product y_i = sum_{|c_i - c_j| < k sigma} z_j exp(-|c_i - c_j|^2 / (2 sigma^2))
+// (Sec. III.A, Eq. matrixEntries): the operation GMRES repeats (the paper's MatShell).
+//
+// float32 kernel.  One CTA = one segment of a tile's pair list, 4 warps.  Every
+// warp holds all 256 targets of the tile (8 per lane) and walks every 4th block
+// of the segment.  For a block with centre c_B and scaled source offsets
+// s_j = (x_j - c_B) * scl (precomputed as (2 s_j, -|s_j|^2)), and a target with
+// d = (x_i - c_B) * scl:
+//      |x_i - x_j|^2 scl^2 = |d|^2 - 2 d.s_j + |s_j|^2,
+//      phi_ij = 2^(-|d|^2) * 2^(d.(2 s_j) - |s_j|^2)
+// so each pair costs 3 FFMA + 1 MUFU.EX2 + 1 FFMA (accumulate), and the per
+// (target, block) factor 2^(-|d|^2) is applied once per block.  Blocks that are
+// not entirely inside the cut-off compare d.(2 s_j) - |s_j|^2 against the
+// per-target threshold |d|^2 - R (R = scaled squared cut-off) before adding.
+// The 4 warps' partial sums are added in a fixed order (deterministic).
+//
+// float64 kernel (true residual): one thread per target, all arithmetic in
+// double precision, cut-off decided as |x_i - x_j|^2 < (k sigma)^2 in double.
+#include <cmath>
+
+#include "plan.cuh"
+
+namespace {
+
+constexpr int kWarps = 4;
+constexpr int kPer = kChunk / 32;   // targets per lane
+
+struct MvArgs {
+    const float4 *pos;   // binned positions (targets, sorted mode)
+    const float4 *src;
+    const float *w;      // binned weights
+    const int2 *blk;
+    const float4 *blk_c;
+    const int32_t *ent;
+    const int4 *seg;
+    int64_t n;
+    float scl, R;
+    float *out;          // direct: y (binned) / grid f; else partial [seg][256]
+    int direct;
+    // grid targets
+    float glo[3], gstep[3];
+    int gdim[3];
+    int bdim[3];
+};
+
+// Target slot q = lane + 32 r of tile t: coordinates and validity.
+template <bool kGrid>
+__device__ __forceinline__ bool target_xyz(const MvArgs &a, int64_t t, int q, float &x, float &y, float &z,
+                                           int64_t &outidx) {
+    if (!kGrid) {
+        int64_t i = t * kChunk + q;
+        if (i < a.n) {
+            float4 p = a.pos[i];
+            x = p.x; y = p.y; z = p.z;
+            outidx = i;
+            return true;
+        }
+        x = y = z = 0.f;
+        outidx = -1;
+        return false;
+    } else {
+        int64_t bx = t % a.bdim[0], by = (t / a.bdim[0]) % a.bdim[1], bz = t / ((int64_t)a.bdim[0] * a.bdim[1]);
+        int ix = (int)bx * 8 + (q & 7), iy = (int)by * 8 + ((q >> 3) & 7), iz = (int)bz * 4 + (q >> 6);
+        bool v = ix < a.gdim[0] && iy < a.gdim[1] && iz < a.gdim[2];
+        x = fmaf((float)ix, a.gstep[0], a.glo[0]);
+        y = fmaf((float)iy, a.gstep[1], a.glo[1]);
+        z = fmaf((float)iz, a.gstep[2], a.glo[2]);
+        outidx = v ? ((int64_t)iz * a.gdim[1] + iy) * a.gdim[0] + ix : -1;
+        return v;
+    }
+}
+
+template <bool kMasked>
+__device__ __forceinline__ void block_sum(const float4 *__restrict__ ss, const float *__restrict__ sw, int cnt,
+                                          const float (&dx)[kPer], const float (&dy)[kPer], const float (&dz)[kPer],
+                                          const float (&thr)[kPer], float (&p)[kPer]) {
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) p[r] = 0.f;
+#pragma unroll 4
+    for (int j = 0; j < cnt; ++j) {
+        float4 s = ss[j];
+        float wj = sw[j];
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            float arg = fmaf(dx[r], s.x, fmaf(dy[r], s.y, fmaf(dz[r], s.z, s.w)));
+            float e = ex2_approx(arg);
+            if (kMasked) e = arg > thr[r] ? e : 0.f;
+            p[r] = fmaf(wj, e, p[r]);
+        }
+    }
+}
+
+template <bool kGrid>
+__global__ void __launch_bounds__(kWarps * 32) k_matvec_f32(MvArgs a) {
+    __shared__ float4 s_src[kWarps][kBlk];
+    __shared__ float s_w[kWarps][kBlk];
+    __shared__ float s_red[kWarps][kChunk];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int4 sg = a.seg[blockIdx.x];
+    const int64_t t = sg.x;
+
+    float tx[kPer], ty[kPer], tz[kPer], acc[kPer];
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+        int64_t oi;
+        target_xyz<kGrid>(a, t, lane + 32 * r, tx[r], ty[r], tz[r], oi);
+        acc[r] = 0.f;
+    }
+    for (int e = sg.y + warp; e < sg.z; e += kWarps) {
+        int ent = a.ent[e];
+        bool masked = ent < 0;
+        int b = ent & 0x7fffffff;
+        int2 bi = a.blk[b];
+        float4 c = a.blk_c[b];
+        // stage the block (zero weight in the padding makes padded terms vanish)
+        float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
+        float wv = 0.f;
+        if (lane < bi.y) {
+            sv = a.src[bi.x + lane];
+            wv = a.w[bi.x + lane];
+        }
+        s_src[warp][lane] = sv;
+        s_w[warp][lane] = wv;
+        __syncwarp();
+        float dx[kPer], dy[kPer], dz[kPer], ea[kPer], thr[kPer], p[kPer];
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            dx[r] = (tx[r] - c.x) * a.scl;
+            dy[r] = (ty[r] - c.y) * a.scl;
+            dz[r] = (tz[r] - c.z) * a.scl;
+            float d2 = fmaf(dx[r], dx[r], fmaf(dy[r], dy[r], dz[r] * dz[r]));
+            ea[r] = ex2_approx(-d2);
+            thr[r] = d2 - a.R;
+        }
+        int cnt = (bi.y + 3) & ~3;
+        if (masked)
+            block_sum<true>(s_src[warp], s_w[warp], cnt, dx, dy, dz, thr, p);
+        else
+            block_sum<false>(s_src[warp], s_w[warp], cnt, dx, dy, dz, thr, p);
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) acc[r] = fmaf(ea[r], p[r], acc[r]);
+        __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) s_red[warp][lane + 32 * r] = acc[r];
+    __syncthreads();
+    for (int q = threadIdx.x; q < kChunk; q += kWarps * 32) {
+        float v = ((s_red[0][q] + s_red[1][q]) + s_red[2][q]) + s_red[3][q];
+        if (a.direct) {
+            float x, y, z;
+            int64_t oi;
+            if (target_xyz<kGrid>(a, t, q, x, y, z, oi)) a.out[oi] = v;
+        } else {
+            a.out[(int64_t)blockIdx.x * kChunk + q] = v;
+        }
+    }
+}
+
+// Sum the segments of each tile in order.
+template <bool kGrid>
+__global__ void k_reduce_segments(MvArgs a, const int32_t *__restrict__ tile_seg, const float *__restrict__ part) {
+    int64_t t = blockIdx.x;
+    int s0 = tile_seg[t], s1 = tile_seg[t + 1];
+    for (int q = threadIdx.x; q < kChunk; q += blockDim.x) {
+        float x, y, z;
+        int64_t oi;
+        if (!target_xyz<kGrid>(a, t, q, x, y, z, oi)) continue;
+        float v = 0.f;
+        for (int sidx = s0; sidx < s1; ++sidx) v += part[(int64_t)sidx * kChunk + q];
+        a.out[oi] = v;
+    }
+}
+
+// ---------------------------------------------------------------- float64
+constexpr int kT64 = kChunk;   // one thread per target
+
+__global__ void __launch_bounds__(kT64) k_resid_f64(const float4 *__restrict__ pos, const double *__restrict__ x,
+                                                   const int2 *__restrict__ blk, const int32_t *__restrict__ ent,
+                                                   const int4 *__restrict__ seg, int64_t n, double rc2, double inv2s2,
+                                                   const float *__restrict__ b, double *__restrict__ out, int direct,
+                                                   unsigned long long *__restrict__ cnt) {
+    __shared__ double s_x[kBlk], s_y[kBlk], s_z[kBlk], s_w[kBlk];
+    __shared__ unsigned long long s_cnt[kT64 / 32];
+    const int4 sg = seg[blockIdx.x];
+    const int64_t i = (int64_t)sg.x * kChunk + threadIdx.x;
+    const bool valid = i < n;
+    double px = 0, py = 0, pz = 0;
+    if (valid) {
+        float4 p = pos[i];
+        px = p.x; py = p.y; pz = p.z;
+    }
+    double acc = 0.0;
+    unsigned long long c = 0;
+    for (int e = sg.y; e < sg.z; ++e) {
+        int bidx = ent[e] & 0x7fffffff;
+        int2 bi = blk[bidx];
+        __syncthreads();
+        if (threadIdx.x < kBlk) {
+            if ((int)threadIdx.x < bi.y) {
+                float4 q = pos[bi.x + threadIdx.x];
+                s_x[threadIdx.x] = q.x; s_y[threadIdx.x] = q.y; s_z[threadIdx.x] = q.z;
+                s_w[threadIdx.x] = x[bi.x + threadIdx.x];
+            }
+        }
+        __syncthreads();
+        for (int j = 0; j < bi.y; ++j) {
+            double dx = px - s_x[j], dy = py - s_y[j], dz = pz - s_z[j];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (rc2 <= 0.0 || r2 < rc2) {
+                acc += s_w[j] * exp(-r2 * inv2s2);
+                ++c;
+            }
+        }
+    }
+    if (direct) {
+        if (valid) out[i] = (double)b[i] - acc;
+    } else {
+        out[(int64_t)blockIdx.x * kChunk + threadIdx.x] = acc;
+    }
+    if (cnt) {
+        if (!valid) c = 0;
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long t = 0;
+            for (int w = 0; w < kT64 / 32; ++w) t += s_cnt[w];
+            atomicAdd(cnt, t);
+        }
+    }
+}
+
+__global__ void k_reduce_resid(const int32_t *__restrict__ tile_seg, const double *__restrict__ part, int64_t n,
+                               const float *__restrict__ b, double *__restrict__ out) {
+    int64_t t = blockIdx.x;
+    int s0 = tile_seg[t], s1 = tile_seg[t + 1];
+    for (int q = threadIdx.x; q < kChunk; q += blockDim.x) {
+        int64_t i = t * kChunk + q;
+        if (i >= n) continue;
+        double v = 0.0;
+        for (int sidx = s0; sidx < s1; ++sidx) v += part[(int64_t)sidx * kChunk + q];
+        out[i] = (double)b[i] - v;
+    }
+}
+
+MvArgs base_args(const rbf_plan *P, const PairList &pl, const float *w, float *out, float *partial) {
+    MvArgs a{};
+    a.pos = P->pos.p;
+    a.src = P->src.p;
+    a.w = w;
+    a.blk = P->blk.p;
+    a.blk_c = P->blk_c.p;
+    a.ent = pl.ent.p;
+    a.seg = pl.seg.p;
+    a.n = P->n;
+    a.scl = P->scl;
+    a.R = P->R;
+    a.direct = pl.direct ? 1 : 0;
+    a.out = pl.direct ? out : partial;
+    return a;
+}
+
+}  // namespace
+
+void matvec_binned(rbf_plan *P, const float *zs, float *ys, cudaStream_t s) {
+    const PairList &pl = P->pl;
+    if (!pl.direct) P->partial.ensure((size_t)pl.nseg * kChunk, s);
+    MvArgs a = base_args(P, pl, zs, ys, P->partial.p);
+    if (pl.nseg > 0) {
+        k_matvec_f32<false><<<(unsigned)pl.nseg, kWarps * 32, 0, s>>>(a);
+        RBF_LAUNCHED();
+    }
+    if (!pl.direct) {
+        a.out = ys;
+        k_reduce_segments<false><<<(unsigned)pl.ntiles, 256, 0, s>>>(a, pl.tile_seg.p, P->partial.p);
+        RBF_LAUNCHED();
+    }
+}
+
+void residual_binned_f64(rbf_plan *P, const float *bs, const double *xs, double *rs, unsigned long long *cnt,
+                         cudaStream_t s) {
+    const PairList &pl = P->pl;
+    DevBuf<double> part;
+    if (!pl.direct) part.alloc((size_t)pl.nseg * kChunk, s);
+    if (pl.nseg > 0) {
+        k_resid_f64<<<(unsigned)pl.nseg, kT64, 0, s>>>(P->pos.p, xs, P->blk.p, pl.ent.p, pl.seg.p, P->n, P->rc2_64,
+                                                       P->inv2s2_64, bs, pl.direct ? rs : part.p, pl.direct ? 1 : 0,
+                                                       cnt);
+        RBF_LAUNCHED();
+    }
+    if (!pl.direct) {
+        k_reduce_resid<<<(unsigned)pl.ntiles, 256, 0, s>>>(pl.tile_seg.p, part.p, P->n, bs, rs);
+        RBF_LAUNCHED();
+    }
+}
+
+// Grid evaluation shares the float32 product kernel with grid-generated targets.
+void matvec_grid_launch(rbf_plan *P, const PairList &pl, const float *ws, const rbf_grid &g, const int64_t bricks[3],
+                        float *f, cudaStream_t s) {
+    if (!pl.direct) P->partial.ensure((size_t)pl.nseg * kChunk, s);
+    MvArgs a = base_args(P, pl, ws, f, P->partial.p);
+    for (int d = 0; d < 3; ++d) {
+        a.glo[d] = g.lo[d];
+        a.gstep[d] = g.dims[d] > 1 ? (float)(((double)g.hi[d] - (double)g.lo[d]) / (double)(g.dims[d] - 1)) : 0.f;
+        a.gdim[d] = (int)g.dims[d];
+        a.bdim[d] = (int)bricks[d];
+    }
+    if (pl.nseg > 0) {
+        k_matvec_f32<true><<<(unsigned)pl.nseg, kWarps * 32, 0, s>>>(a);
+        RBF_LAUNCHED();
+    }
+    if (!pl.direct) {
+        a.out = f;
+        k_reduce_segments<true><<<(unsigned)pl.ntiles, 256, 0, s>>>(a, pl.tile_seg.p, P->partial.p);
+        RBF_LAUNCHED();
+    }
+}
+
+// ---------------------------------------------------------------- pair count
+namespace {
+
+// Pairs with |x_i - x_j| < k sigma.  The test runs in float32 and is repeated in
+// float64 only within 1e-5 (relative) of the cut-off, where float32 rounding of
+// the squared distance (< 3e-7 relative) could flip it; so the count equals the
+// float64 decision.
+__global__ void __launch_bounds__(kT64) k_count_pairs(const float4 *__restrict__ pos, const int2 *__restrict__ blk,
+                                                     const int32_t *__restrict__ ent, const int4 *__restrict__ seg,
+                                                     int64_t n, double rc2, unsigned long long *__restrict__ cnt) {
+    __shared__ float4 s_p[kBlk];
+    __shared__ unsigned long long s_cnt[kT64 / 32];
+    const int4 sg = seg[blockIdx.x];
+    const int64_t i = (int64_t)sg.x * kChunk + threadIdx.x;
+    const bool valid = i < n;
+    float4 p = valid ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float rc2f = (float)rc2, lo = rc2f * (1.f - 1e-5f), hi = rc2f * (1.f + 1e-5f);
+    unsigned long long c = 0;
+    for (int e = sg.y; e < sg.z; ++e) {
+        int2 bi = blk[ent[e] & 0x7fffffff];
+        __syncthreads();
+        if ((int)threadIdx.x < bi.y) s_p[threadIdx.x] = pos[bi.x + threadIdx.x];
+        __syncthreads();
+        for (int j = 0; j < bi.y; ++j) {
+            float4 q = s_p[j];
+            float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            bool in;
+            if (r2 < lo) in = true;
+            else if (r2 >= hi) in = false;
+            else {
+                double ex = (double)p.x - (double)q.x, ey = (double)p.y - (double)q.y, ez = (double)p.z - (double)q.z;
+                in = ex * ex + ey * ey + ez * ez < rc2;
+            }
+            c += in ? 1 : 0;
+        }
+    }
+    if (!valid) c = 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kT64 / 32; ++w) t += s_cnt[w];
+        atomicAdd(cnt, t);
+    }
+}
+
+// Grid version: node coordinates as the float32 product kernel forms them.
+__global__ void __launch_bounds__(kT64) k_count_grid_pairs(MvArgs a, double rc2, unsigned long long *__restrict__ cnt) {
+    __shared__ float4 s_p[kBlk];
+    __shared__ unsigned long long s_cnt[kT64 / 32];
+    const int4 sg = a.seg[blockIdx.x];
+    float px, py, pz;
+    int64_t oi;
+    const bool valid = target_xyz<true>(a, sg.x, threadIdx.x, px, py, pz, oi);
+    const float rc2f = (float)rc2, lo = rc2f * (1.f - 1e-5f), hi = rc2f * (1.f + 1e-5f);
+    unsigned long long c = 0;
+    for (int e = sg.y; e < sg.z; ++e) {
+        int2 bi = a.blk[a.ent[e] & 0x7fffffff];
+        __syncthreads();
+        if ((int)threadIdx.x < bi.y) s_p[threadIdx.x] = a.pos[bi.x + threadIdx.x];
+        __syncthreads();
+        for (int j = 0; j < bi.y; ++j) {
+            float4 q = s_p[j];
+            float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            bool in;
+            if (r2 < lo) in = true;
+            else if (r2 >= hi) in = false;
+            else {
+                double ex = (double)px - (double)q.x, ey = (double)py - (double)q.y, ez = (double)pz - (double)q.z;
+                in = ex * ex + ey * ey + ez * ez < rc2;
+            }
+            c += in ? 1 : 0;
+        }
+    }
+    if (!valid) c = 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kT64 / 32; ++w) t += s_cnt[w];
+        atomicAdd(cnt, t);
+    }
+}
+
+}  // namespace
+
+int64_t count_grid_pairs_launch(rbf_plan *P, const PairList &pl, const rbf_grid &g, const int64_t bricks[3],
+                                cudaStream_t s) {
+    int64_t nodes = g.dims[0] * g.dims[1] * g.dims[2];
+    if (P->k <= 0.f) return nodes * P->n;
+    MvArgs a = base_args(P, pl, nullptr, nullptr, nullptr);
+    for (int d = 0; d < 3; ++d) {
+        a.glo[d] = g.lo[d];
+        a.gstep[d] = g.dims[d] > 1 ? (float)(((double)g.hi[d] - (double)g.lo[d]) / (double)(g.dims[d] - 1)) : 0.f;
+        a.gdim[d] = (int)g.dims[d];
+        a.bdim[d] = (int)bricks[d];
+    }
+    DevBuf<unsigned long long> c;
+    c.alloc(1, s);
+    c.zero(s);
+    if (pl.nseg > 0) {
+        k_count_grid_pairs<<<(unsigned)pl.nseg, kT64, 0, s>>>(a, P->rc2_64, c.p);
+        RBF_LAUNCHED();
+    }
+    unsigned long long h = 0;
+    RBF_CUDA(cudaMemcpyAsync(&h, c.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(cudaStreamSynchronize(s));
+    return (int64_t)h;
+}
+
+int64_t count_pairs(rbf_plan *P, cudaStream_t s) {
+    if (P->pairs >= 0) return P->pairs;
+    if (P->k <= 0.f) {
+        P->pairs = P->n * P->n;
+        return P->pairs;
+    }
+    DevBuf<unsigned long long> c;
+    c.alloc(1, s);
+    c.zero(s);
+    if (P->pl.nseg > 0) {
+        k_count_pairs<<<(unsigned)P->pl.nseg, kT64, 0, s>>>(P->pos.p, P->blk.p, P->pl.ent.p, P->pl.seg.p, P->n,
+                                                           P->rc2_64, c.p);
+        RBF_LAUNCHED();
+    }
+    unsigned long long h = 0;
+    RBF_CUDA(cudaMemcpyAsync(&h, c.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(cudaStreamSynchronize(s));
+    P->pairs = (int64_t)h;
+    return P->pairs;
+}

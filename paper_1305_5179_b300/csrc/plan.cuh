@@ -1,0 +1,105 @@
+// The matrix-free operator over a fixed set of centres (internal).
+#pragma once
+#include "common.cuh"
+
+constexpr int kBlk = 32;      // sources per block (one warp stages one block)
+constexpr int kChunk = 256;   // targets per tile (8 per lane of a warp)
+
+// A list of (target tile, source block) work: entries of a tile are contiguous,
+// split into segments (one CTA each) when there are too few tiles to fill the GPU.
+struct PairList {
+    int64_t ntiles = 0;
+    int64_t len = 0;
+    int64_t nseg = 0;
+    bool direct = true;            // one segment per tile: write outputs directly
+    PBuf<int32_t> off;           // ntiles + 1
+    PBuf<int32_t> ent;           // len; bit 31 set = pair-wise cut-off test needed
+    PBuf<int4> seg;              // (tile, e0, e1, unused)
+    PBuf<int32_t> tile_seg;      // ntiles + 1: segments of tile t are [tile_seg[t], tile_seg[t+1])
+};
+
+struct SchwarzData {
+    bool ready = false;
+    int core = 0, block = 0, restricted = 1;
+    float shift = 0.f;
+    int64_t nblocks = 0;
+    PBuf<float> L;               // nblocks x block x block, row-major lower factor
+    PBuf<float> shift_used;      // nblocks
+    PBuf<int32_t> failed;        // nblocks (1 = factorisation failed, block acts as identity)
+};
+
+struct GridCache {
+    bool valid = false;
+    rbf_grid g{};
+    int64_t bricks[3] = {0, 0, 0};
+    PairList pl;
+};
+
+struct rbf_plan {
+    rbf_ctx *ctx = nullptr;
+    int64_t n = 0;
+    float sigma = 0.f, k = 0.f;
+    int cells_per_cutoff = 1, levels = 3, nbits = 0;
+    float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    float inv = 0.f;          // fine cells per unit length
+    int cdim = 0;             // cells per axis in the cell table (2^(nbits - levels))
+    float rc = 0.f;           // cut-off radius used for box culling (k sigma, or the dense zero radius)
+    float scl = 0.f;          // sqrt(log2(e) / (2 sigma^2)): scaled units where phi = 2^(-|d|^2)
+    float R = 0.f;            // scaled squared cut-off (k^2 log2(e) / 2), +inf when untruncated
+    double rc2_64 = 0.0;      // (k sigma)^2 in double, 0 = untruncated
+    double inv2s2_64 = 0.0;   // 1 / (2 sigma^2) in double
+    int64_t ncells = 0, nblk = 0, nchk = 0;
+    int64_t pairs = -1;       // algorithmic pairs, once counted
+
+    PBuf<int32_t> perm;        // binned position -> caller index
+    PBuf<uint32_t> keys;       // sorted Morton keys
+    PBuf<int32_t> cell_start, cell_end;
+    PBuf<int32_t> cell_blk;    // ncells + 1: blocks of cell c are [cell_blk[c], cell_blk[c+1])
+    PBuf<float4> pos;          // binned positions (x, y, z, 0)
+    PBuf<int2> blk;            // (start, count)
+    PBuf<float4> blk_c;        // block centre (x, y, z, radius)
+    PBuf<float4> blk_lo, blk_hi;
+    PBuf<float4> src;          // per binned source: (2 s_x, 2 s_y, 2 s_z, -|s|^2), s = scaled offset to its block centre
+    PBuf<float4> chk_lo, chk_hi;
+    PairList pl;
+
+    // work vectors (binned order)
+    PBuf<float> zs, ys;
+    PBuf<float> partial;
+    PBuf<double> xd, rd;
+
+    SchwarzData sz;
+    GridCache grid;
+};
+
+// plan.cu
+void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s);
+// Pair list of target tiles given by boxes (lo, hi per tile) against the plan's source blocks.
+void build_pairlist(rbf_plan *P, const float4 *tlo, const float4 *thi, int64_t ntiles, PairList &pl,
+                    cudaStream_t s);
+void permute_to_binned_f32(const rbf_plan *P, const float *in, float *out, cudaStream_t s);
+void permute_to_binned_f64_to_f32(const rbf_plan *P, const double *in, float *out, cudaStream_t s);
+void permute_to_binned_f64(const rbf_plan *P, const double *in, double *out, cudaStream_t s);
+void permute_from_binned_f32(const rbf_plan *P, const float *in, float *out, cudaStream_t s);
+void permute_from_binned_f64(const rbf_plan *P, const double *in, double *out, cudaStream_t s);
+
+// matvec.cu
+void matvec_binned(rbf_plan *P, const float *zs, float *ys, cudaStream_t s);
+// Algorithmic pair count (cached on the plan).
+int64_t count_pairs(rbf_plan *P, cudaStream_t s);
+// r = b - A~ x in float64 (binned order); counts pairs when cnt != nullptr (device int64).
+void residual_binned_f64(rbf_plan *P, const float *bs, const double *xs, double *rs,
+                         unsigned long long *cnt, cudaStream_t s);
+
+// schwarz.cu
+void schwarz_setup(rbf_plan *P, const rbf_schwarz_params &p, int64_t *failed_host, cudaStream_t s);
+// z = M^-1 v, binned order; v given as float64 (vd) or float32 (vf), exactly one non-null.
+void schwarz_apply_binned(rbf_plan *P, const double *vd, const float *vf, float *z, cudaStream_t s);
+
+// grid.cu
+void eval_grid(rbf_plan *P, const double *weights, const rbf_grid &g, float *f, cudaStream_t s);
+int64_t count_grid_pairs(rbf_plan *P, const rbf_grid &g, cudaStream_t s);
+
+// fgmres.cu
+rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_params &p, double *x_caller,
+                        rbf_report *rep, cudaStream_t s);

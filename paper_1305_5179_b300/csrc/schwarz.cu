@@ -1,0 +1,205 @@
+// Restricted additive Schwarz preconditioner (Sec. III.A, RASM).
+//
+// Subdomain i of the binned order is the run [d0_i, d0_i + B) around the core
+// [s_i, s_i + core) (B = min(block, n), d0_i = clamp(s_i - (block - core)/2, 0,
+// n - B)).  Set-up: one CTA per subdomain assembles the untruncated Gaussian
+// block A_i + shift I in shared memory (float32, exp2 on the SFU) and factorises
+// it in place by a right-looking Cholesky (one thread per column); a failed
+// pivot retries with a 10x larger shift when escalation is on.  Apply: one warp
+// per subdomain gathers v, solves L y = v (row dots, warp reductions) and
+// L^T x = y (row updates), and writes the core entries (restricted) or adds
+// the whole local solution (additive).
+#include <cmath>
+
+#include "plan.cuh"
+
+namespace {
+
+constexpr int kMaxB = 128;
+constexpr int kSetupThreads = 128;
+
+__device__ __forceinline__ void dom_of(int64_t blkid, int core, int B, int64_t n, int64_t &d0, int64_t &c0,
+                                       int &cl) {
+    int64_t s = blkid * core;
+    int64_t e = s + core < n ? s + core : n;
+    int o = B - core;
+    int64_t st = s - o / 2;
+    if (st > n - B) st = n - B;
+    if (st < 0) st = 0;
+    d0 = st;
+    c0 = s;
+    cl = (int)(e - s);
+}
+
+__global__ void __launch_bounds__(kSetupThreads) k_schwarz_setup(const float4 *__restrict__ pos, int64_t n, int core,
+                                                                 int B, float scl, float shift, int escalate,
+                                                                 float *__restrict__ Lout, float *__restrict__ shift_used,
+                                                                 int32_t *__restrict__ failed) {
+    extern __shared__ float sm[];
+    const int ld = B + 1;
+    float *A = sm;                                  // B x (B + 1), padded rows
+    __shared__ int s_fail;
+    int64_t d0, c0;
+    int cl;
+    dom_of(blockIdx.x, core, B, n, d0, c0, cl);
+    float lam = shift;
+    int attempts = escalate ? 5 : 1;
+    int ok = 0;
+    for (int att = 0; att < attempts && !ok; ++att, lam *= 10.f) {
+        for (int idx = threadIdx.x; idx < B * B; idx += blockDim.x) {
+            int i = idx / B, j = idx % B;
+            if (j > i) continue;
+            float4 pi = pos[d0 + i], pj = pos[d0 + j];   // difference before scaling keeps it exact-ish
+            float dx = (pi.x - pj.x) * scl, dy = (pi.y - pj.y) * scl, dz = (pi.z - pj.z) * scl;
+            float v = ex2_approx(-(dx * dx + dy * dy + dz * dz));
+            A[i * ld + j] = (i == j) ? 1.f + lam : v;
+        }
+        if (threadIdx.x == 0) s_fail = 0;
+        __syncthreads();
+        for (int j = 0; j < B; ++j) {
+            if (threadIdx.x == 0) {
+                float d = A[j * ld + j];
+                if (!(d > 0.f) || !isfinite(d)) s_fail = 1;
+                A[j * ld + j] = sqrtf(fmaxf(d, 1e-30f));
+            }
+            __syncthreads();
+            if (s_fail) break;
+            float ljj = A[j * ld + j];
+            for (int i = j + 1 + threadIdx.x; i < B; i += blockDim.x) A[i * ld + j] /= ljj;
+            __syncthreads();
+            for (int c = j + 1 + threadIdx.x; c < B; c += blockDim.x) {
+                float lcj = A[c * ld + j];
+                for (int i = c; i < B; ++i) A[i * ld + c] = fmaf(-A[i * ld + j], lcj, A[i * ld + c]);
+            }
+            __syncthreads();
+        }
+        ok = !s_fail;
+        __syncthreads();
+    }
+    float *L = Lout + (int64_t)blockIdx.x * B * B;
+    for (int idx = threadIdx.x; idx < B * B; idx += blockDim.x) {
+        int i = idx / B, j = idx % B;
+        float v;
+        if (ok)
+            v = j <= i ? A[i * ld + j] : 0.f;
+        else
+            v = (i == j) ? 1.f : 0.f;
+        L[idx] = v;
+    }
+    if (threadIdx.x == 0) {
+        failed[blockIdx.x] = ok ? 0 : 1;
+        shift_used[blockIdx.x] = ok ? lam / 10.f : -1.f;
+    }
+}
+
+template <typename Tin>
+__global__ void k_schwarz_apply(const Tin *__restrict__ v, int64_t n, int core, int B, int64_t nblocks,
+                                const float *__restrict__ Lall, int restricted, float *__restrict__ z) {
+    int64_t blk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (blk >= nblocks) return;
+    int64_t d0, c0;
+    int cl;
+    dom_of(blk, core, B, n, d0, c0, cl);
+    const float *L = Lall + blk * (int64_t)B * B;
+    constexpr int Q = kMaxB / 32;
+    float y[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        int k = lane + 32 * q;
+        y[q] = k < B ? (float)v[d0 + k] : 0.f;
+    }
+    // forward: y_j = (v_j - sum_{k<j} L_jk y_k) / L_jj
+    for (int j = 0; j < B; ++j) {
+        const float *row = L + (int64_t)j * B;
+        float s = 0.f;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            int k = lane + 32 * q;
+            if (32 * q < j && k < j) s = fmaf(row[k], y[q], s);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        float ljj = row[j];
+        if (lane == (j & 31)) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+                if (q == (j >> 5)) y[q] = (y[q] - s) / ljj;
+        }
+    }
+    // backward: x_j = y_j / L_jj; y_k -= L_jk x_j for k < j
+    for (int j = B - 1; j >= 0; --j) {
+        const float *row = L + (int64_t)j * B;
+        float yj = 0.f;
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+            if (q == (j >> 5)) yj = y[q];
+        float xj = __shfl_sync(0xffffffffu, yj, j & 31) / row[j];
+        if (lane == (j & 31)) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+                if (q == (j >> 5)) y[q] = xj;
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            int k = lane + 32 * q;
+            if (32 * q < j && k < j) y[q] = fmaf(-row[k], xj, y[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        int k = lane + 32 * q;
+        if (k >= B) continue;
+        int64_t gi = d0 + k;
+        if (restricted) {
+            if (gi >= c0 && gi < c0 + cl) z[gi] = y[q];
+        } else {
+            atomicAdd(&z[gi], y[q]);
+        }
+    }
+}
+
+}  // namespace
+
+void schwarz_setup(rbf_plan *P, const rbf_schwarz_params &p, int64_t *failed_host, cudaStream_t s) {
+    RBF_CHECK(p.block >= 1 && p.block <= kMaxB, RBF_ERR_UNSUPPORTED, "schwarz block %d outside 1..%d", p.block, kMaxB);
+    RBF_CHECK(p.core >= 1 && p.core <= p.block, RBF_ERR_INVALID, "schwarz core %d outside 1..block", p.core);
+    RBF_CHECK(p.shift >= 0.f && std::isfinite(p.shift), RBF_ERR_INVALID, "schwarz shift must be finite and >= 0");
+    SchwarzData &S = P->sz;
+    S.ready = false;
+    S.core = p.core;
+    S.block = (int)std::min<int64_t>(p.block, P->n);
+    S.restricted = p.restricted ? 1 : 0;
+    S.shift = p.shift;
+    S.nblocks = ceil_div(P->n, p.core);
+    const int B = S.block;
+    S.L.alloc((size_t)S.nblocks * B * B, s);
+    S.shift_used.alloc(S.nblocks, s);
+    S.failed.alloc(S.nblocks, s);
+    size_t smem = (size_t)B * (B + 1) * sizeof(float);
+    RBF_CUDA(cudaFuncSetAttribute(k_schwarz_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_schwarz_setup<<<(unsigned)S.nblocks, kSetupThreads, smem, s>>>(P->pos.p, P->n, S.core, B, P->scl, p.shift,
+                                                                     p.escalate, S.L.p, S.shift_used.p, S.failed.p);
+    RBF_LAUNCHED();
+    if (failed_host) {
+        std::vector<int32_t> f(S.nblocks);
+        RBF_CUDA(cudaMemcpyAsync(f.data(), S.failed.p, S.nblocks * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        RBF_CUDA(cudaStreamSynchronize(s));
+        int64_t c = 0;
+        for (auto x : f) c += x;
+        *failed_host = c;
+    }
+    S.ready = true;
+}
+
+void schwarz_apply_binned(rbf_plan *P, const double *vd, const float *vf, float *z, cudaStream_t s) {
+    SchwarzData &S = P->sz;
+    RBF_CHECK(S.ready, RBF_ERR_INVALID, "schwarz preconditioner not set up");
+    if (!S.restricted) RBF_CUDA(cudaMemsetAsync(z, 0, P->n * sizeof(float), s));
+    unsigned grid = (unsigned)ceil_div(S.nblocks * 32, 256);
+    if (vd)
+        k_schwarz_apply<double><<<grid, 256, 0, s>>>(vd, P->n, S.core, S.block, S.nblocks, S.L.p, S.restricted, z);
+    else
+        k_schwarz_apply<float><<<grid, 256, 0, s>>>(vf, P->n, S.core, S.block, S.nblocks, S.L.p, S.restricted, z);
+    RBF_LAUNCHED();
+}

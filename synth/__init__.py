@@ -66,19 +66,20 @@ def sphere(n: int, seed: int = 0, radius: float = 1.0) -> Cloud:
 
 
 def torus(n: int, R: float = 1.0, r: float = 0.35, noise: float = 0.0,
-          seed: int = 0, center=(0.0, 0.0, 0.0)) -> Cloud:
+          seed: int = 0, center=(0.0, 0.0, 0.0), theta_max: float = 2 * math.pi) -> Cloud:
     """``n`` points uniform by area on the ring torus (major ``R``, minor ``r``).
 
     The area element is r (R + r cos(phi)) dtheta dphi, so phi is accepted with
     probability (R + r cos phi) / (R + r).  The normal is the analytic one at the
     clean point; isotropic Gaussian noise of std ``noise`` is then added to the
-    position only.
+    position only.  ``theta_max`` < 2 pi keeps the sector 0 <= theta < theta_max
+    (a patch with the density of n * 2 pi / theta_max points on the whole torus).
     """
     rng = np.random.default_rng(seed)
     th_out, ph_out, got = [], [], 0
     while got < n:
         m = max(1024, int(1.3 * (n - got)) + 16)
-        th = rng.uniform(0.0, 2 * math.pi, m)
+        th = rng.uniform(0.0, theta_max, m)
         ph = rng.uniform(0.0, 2 * math.pi, m)
         keep = rng.uniform(0.0, 1.0, m) < (R + r * np.cos(ph)) / (R + r)
         th_out.append(th[keep]); ph_out.append(ph[keep]); got += int(keep.sum())
@@ -92,7 +93,7 @@ def torus(n: int, R: float = 1.0, r: float = 0.35, noise: float = 0.0,
     p = p + np.asarray(center, dtype=np.float64)
     return Cloud(_f32(p), _f32(nrm),
                  dict(shape="torus", n=n, R=R, r=r, noise=noise, seed=seed,
-                      center=list(map(float, center))))
+                      center=list(map(float, center)), theta_max=theta_max))
 
 
 def ellipsoid(n: int, axes=(1.0, 1.0, 1.0), seed: int = 0,

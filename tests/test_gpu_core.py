@@ -1,0 +1,381 @@
+"""GPU parity of the hot path against the FP64 oracle, through the C ABI.
+
+Every input is seeded and synthetic; the oracle side sees the same float32
+centres (as float64) and the same float32 sigma and k.  Tolerances:
+  * centre build: within half an ulp of float32 (one rounding of x + delta n);
+  * binning: bit-exact (permutation, keys, cell table);
+  * truncated / dense product: |y - y64|_2 / |y64|_2 <= 1e-5;
+  * pair count: exact (the kernel decides in float64 near the cut-off);
+  * float64 residual: |r - r64|_inf <= 1e-11 * max_i sum_j |a_ij x_j|;
+  * grid evaluation: max |f - f64| <= 1e-4 (max f64 - min f64).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F32 = np.float32
+
+
+@pytest.fixture(scope="module")
+def rbf():
+    import paper_1305_5179_b300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(rbf):
+    return rbf.Context(0)
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def c4(C):
+    """float64 (n, 3) -> float32 (n, 4) device centres and the float32-exact float64 copy."""
+    C32 = np.zeros((len(C), 4), dtype=np.float32)
+    C32[:, :3] = C
+    return dev(C32), C32[:, :3].astype(np.float64)
+
+
+def rel2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def torus_patch(N_full=1_000_000, theta=0.3, seed=1, delta=0.01):
+    """A sector of the 1,000,000-point noisy torus (R = 1, r = 0.35) with its
+    full density: the neighbourhood sizes of the scan-scale workload."""
+    n_sector = int(N_full * theta / (2 * math.pi))
+    cl = synth.torus(n_sector, noise=1e-3, seed=seed, theta_max=theta)
+    C, b = oracle.build_centers(cl.points, cl.normals, delta)
+    return cl, C, b
+
+
+# ---------------------------------------------------------------------- step 1
+def test_build_centers_match_oracle(ctx, rbf, sphere_c1):
+    cl = sphere_c1
+    C, b, d = rbf.build_centers(ctx, dev(cl.points), dev(cl.normals), delta=0.05)
+    Co, bo = oracle.build_centers(cl.points, cl.normals, 0.05)
+    Cg = C.cpu().numpy().astype(np.float64)
+    assert d == pytest.approx(0.05)
+    ulp = np.spacing(np.abs(Co).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(Cg[:, :3] - Co) <= 0.5 * ulp + 1e-12)
+    assert np.all(Cg[:, 3] == 0)
+    assert np.array_equal(b.cpu().numpy().astype(np.float64), bo.astype(np.float32).astype(np.float64))
+
+
+def test_build_centers_default_delta_and_unit_targets(ctx, rbf):
+    cl = synth.torus(1000, seed=3)
+    C, b, d = rbf.build_centers(ctx, dev(cl.points), dev(cl.normals), delta=0.0, target=1.0)
+    assert d == pytest.approx(oracle.default_delta(cl.points), rel=1e-6)
+    bb = b.cpu().numpy()
+    assert np.all(bb[:1000] == 0) and np.all(bb[1000:2000] == 1) and np.all(bb[2000:] == -1)
+
+
+def test_build_centers_rejects_non_finite(ctx, rbf):
+    cl = synth.sphere(10)
+    p = cl.points.copy()
+    p[3, 1] = np.nan
+    with pytest.raises(rbf.RbfError) as e:
+        rbf.build_centers(ctx, dev(p), dev(cl.normals), delta=0.1)
+    assert e.value.status == 1
+
+
+# ---------------------------------------------------------------------- binning
+def _binning_case(ctx, rbf, C, sigma, k, s=1, L=3):
+    Cd, C64 = c4(C)
+    plan = rbf.Plan(ctx, Cd, sigma=sigma, k=k, cells_per_cutoff=s, levels=L)
+    perm, keys, cs, ce = plan.export_binning()
+    ref = oracle.binning(C64.astype(np.float32), F32(sigma), F32(k), s, L)
+    info = plan.info()
+    assert info["nbits"] == ref["nbits"]
+    assert np.float32(info["inv"]) == ref["inv"]
+    assert np.array_equal(perm.cpu().numpy(), ref["perm"])
+    assert np.array_equal(keys.cpu().numpy().view(np.uint32), ref["keys_sorted"])
+    assert np.array_equal(cs.cpu().numpy(), ref["cell_start"])
+    assert np.array_equal(ce.cpu().numpy(), ref["cell_end"])
+    return plan
+
+
+def test_binning_bit_exact_torus_patch(ctx, rbf):
+    _, C, _ = torus_patch(theta=0.2)
+    _binning_case(ctx, rbf, C, 0.02, 6.0)
+    _binning_case(ctx, rbf, C, 0.02, 6.0, s=2, L=2)
+
+
+def test_binning_bit_exact_dense_sphere(ctx, rbf, sphere_c1):
+    C, _ = oracle.build_centers(sphere_c1.points, sphere_c1.normals, 0.05)
+    _binning_case(ctx, rbf, C, 0.1, 0.0)
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 4097, 20000])
+def test_binning_bit_exact_ragged_and_duplicates(ctx, rbf, n):
+    rng = np.random.default_rng(n)
+    C = rng.uniform(-0.7, 1.3, (n, 3))
+    if n > 40:
+        C[10:30] = C[5]                                # equal keys keep input order
+    _binning_case(ctx, rbf, C, 0.05, 3.0)
+
+
+# ---------------------------------------------------------------------- product
+def _matvec_check(ctx, rbf, C, sigma, k, rows=None, seeds=(0, 1), tol=1e-5):
+    Cd, C64 = c4(C)
+    plan = rbf.Plan(ctx, Cd, sigma=sigma, k=k)
+    n = len(C)
+    for sd in seeds:
+        rng = np.random.default_rng(100 + sd)
+        z = (rng.standard_normal(n) if sd % 2 == 0 else rng.uniform(0, 1, n)).astype(np.float32)
+        y = plan.matvec(dev(z)).cpu().numpy().astype(np.float64)
+        y64, _ = oracle.kernel_rows(C64, z.astype(np.float64), float(F32(sigma)), float(F32(k)), rows)
+        yg = y if rows is None else y[rows]
+        assert rel2(yg, y64) <= tol, (sd, rel2(yg, y64))
+    return plan
+
+
+def test_matvec_dense_c1_all_rows(ctx, rbf, sphere_c1):
+    C, _ = oracle.build_centers(sphere_c1.points, sphere_c1.normals, 0.05)
+    _matvec_check(ctx, rbf, C, 0.1, 0.0)
+
+
+def test_matvec_truncated_torus_patch(ctx, rbf):
+    _, C, _ = torus_patch(theta=0.15)
+    rows = np.random.default_rng(5).choice(len(C), 3000, replace=False)
+    _matvec_check(ctx, rbf, C, 0.02, 6.0, rows=rows)
+
+
+@pytest.mark.parametrize("n,k", [(1, 3.0), (2, 0.0), (31, 3.0), (33, 0.0), (255, 3.0), (257, 6.0), (1000, 2.0),
+                                 (5000, 4.0)])
+def test_matvec_ragged(ctx, rbf, n, k):
+    rng = np.random.default_rng(n)
+    C = rng.uniform(0, 1, (n, 3))
+    _matvec_check(ctx, rbf, C, 0.08, k)
+
+
+def test_matvec_deterministic(ctx, rbf):
+    _, C, _ = torus_patch(theta=0.1)
+    Cd, _ = c4(C)
+    plan = rbf.Plan(ctx, Cd, sigma=0.02, k=6.0)
+    z = dev(np.random.default_rng(0).standard_normal(len(C)))
+    assert torch.equal(plan.matvec(z), plan.matvec(z))
+
+
+def test_pair_count_exact(ctx, rbf):
+    _, C, _ = torus_patch(theta=0.05)
+    Cd, C64 = c4(C)
+    plan = rbf.Plan(ctx, Cd, sigma=0.02, k=6.0)
+    _, cnt = oracle.kernel_rows(C64, np.zeros(len(C)), float(F32(0.02)), float(F32(6.0)))
+    assert plan.count_pairs() == cnt
+    rng = np.random.default_rng(2)
+    C2 = rng.uniform(0, 1, (3000, 3))
+    Cd2, C642 = c4(C2)
+    plan2 = rbf.Plan(ctx, Cd2, sigma=0.05, k=3.0)
+    _, cnt2 = oracle.kernel_rows(C642, np.zeros(3000), float(F32(0.05)), float(F32(3.0)))
+    assert plan2.count_pairs() == cnt2
+    plan3 = rbf.Plan(ctx, Cd2, sigma=0.05, k=0.0)
+    assert plan3.count_pairs() == 3000 * 3000
+
+
+def test_residual_float64(ctx, rbf):
+    _, C, b = torus_patch(theta=0.05)
+    Cd, C64 = c4(C)
+    plan = rbf.Plan(ctx, Cd, sigma=0.02, k=6.0)
+    x = np.random.default_rng(4).standard_normal(len(C))
+    b32 = b.astype(np.float32)
+    r, (rn, bn) = plan.residual(dev(b32), dev(x, torch.float64))
+    r64 = oracle.residual_rows(C64, b32.astype(np.float64), x, float(F32(0.02)), float(F32(6.0)))
+    scale, _ = oracle.kernel_rows(C64, np.abs(x), float(F32(0.02)), float(F32(6.0)))
+    assert np.abs(r.cpu().numpy() - r64).max() <= 1e-11 * scale.max()
+    assert rn == pytest.approx(np.linalg.norm(r64), rel=1e-10)
+    assert bn == pytest.approx(np.linalg.norm(b32.astype(np.float64)), rel=1e-12)
+
+
+# ---------------------------------------------------------------------- Schwarz
+def _schwarz_tol(Cs, sigma, parts, shift):
+    """4 sqrt(B) eps32 kappa_max: forward error of float32 Cholesky solves."""
+    kap = 0.0
+    for d0, dl, _, _ in parts[:: max(1, len(parts) // 8)]:
+        lam = np.linalg.eigvalsh(oracle.dense_matrix(Cs[d0:d0 + dl], sigma) + shift * np.eye(dl))
+        kap = max(kap, lam[-1] / lam[0])
+    return 4 * math.sqrt(parts[0][1]) * np.finfo(np.float32).eps * kap
+
+
+@pytest.mark.parametrize("core,block,restricted", [(96, 128, True), (64, 64, True), (48, 64, False)])
+def test_schwarz_apply_matches_oracle(ctx, rbf, core, block, restricted):
+    cl = synth.sphere(700, seed=9)
+    C, _ = oracle.build_centers(cl.points, cl.normals, 0.05)
+    Cd, C64 = c4(C)
+    sigma, shift = 0.1, 1e-2
+    plan = rbf.Plan(ctx, Cd, sigma=sigma, k=0.0)
+    failed = plan.schwarz_setup(core=core, block=block, shift=shift, restricted=restricted)
+    assert failed == 0
+    perm = plan.export_binning()[0].cpu().numpy()
+    Cs = C64[perm]
+    parts = oracle.schwarz_partition(len(C), core, block)
+    v = np.random.default_rng(1).standard_normal(len(C)).astype(np.float32)
+    z = plan.schwarz_apply(dev(v)).cpu().numpy().astype(np.float64)
+    zref_s = oracle.schwarz_apply(Cs, v[perm].astype(np.float64), float(F32(sigma)), parts, float(F32(shift)),
+                                  restricted)
+    zref = np.empty_like(zref_s)
+    zref[perm] = zref_s
+    tol = _schwarz_tol(Cs, float(F32(sigma)), parts, float(F32(shift)))
+    assert rel2(z, zref) <= tol, (rel2(z, zref), tol)
+
+
+def test_schwarz_ragged_tail_and_small_n(ctx, rbf):
+    rng = np.random.default_rng(3)
+    for n in (50, 129, 1000):
+        C = rng.uniform(0, 1, (n, 3))
+        Cd, C64 = c4(C)
+        plan = rbf.Plan(ctx, Cd, sigma=0.05, k=0.0)
+        assert plan.schwarz_setup(core=96, block=128, shift=0.05) == 0
+        perm = plan.export_binning()[0].cpu().numpy()
+        parts = oracle.schwarz_partition(n, 96, 128)
+        v = rng.standard_normal(n).astype(np.float32)
+        z = plan.schwarz_apply(dev(v)).cpu().numpy().astype(np.float64)
+        zs = oracle.schwarz_apply(C64[perm], v[perm].astype(np.float64), float(F32(0.05)), parts, float(F32(0.05)))
+        zr = np.empty_like(zs)
+        zr[perm] = zs
+        assert rel2(z, zr) <= _schwarz_tol(C64[perm], float(F32(0.05)), parts, float(F32(0.05)))
+
+
+# ---------------------------------------------------------------------- FGMRES
+def test_fgmres_first_iterations_match_oracle(ctx, rbf, sphere_c1):
+    """The first 8 FGMRES iterates (no preconditioner, x0 = 0) agree with the
+    FP64 oracle's textbook FGMRES: the float32 product only perturbs them."""
+    C, b = oracle.build_centers(sphere_c1.points, sphere_c1.normals, 0.05)
+    Cd, C64 = c4(C)
+    b32 = b.astype(np.float32)
+    plan = rbf.Plan(ctx, Cd, sigma=0.1, k=0.0)
+    x, rep = plan.solve(dev(b32), m=50, max_it=8, fixed_iterations=True)
+    A = oracle.dense_matrix(C64, float(F32(0.1)))
+    xo, it, hist = oracle.fgmres(lambda v: A @ v, b32.astype(np.float64), m=50, tol=1e-30, max_it=8)
+    assert rep["iterations"] == 8 and it == 8
+    assert rep["residual_estimate"] == pytest.approx(hist[-1], rel=1e-3)
+    assert rel2(A @ x.cpu().numpy(), A @ xo) <= 1e-4
+
+
+def test_fgmres_true_residual_report(ctx, rbf, sphere_c1):
+    C, b = oracle.build_centers(sphere_c1.points, sphere_c1.normals, 0.05)
+    Cd, C64 = c4(C)
+    b32 = b.astype(np.float32)
+    plan = rbf.Plan(ctx, Cd, sigma=0.1, k=0.0)
+    x, rep = plan.solve(dev(b32), m=30, max_it=90, tol=1e-12)
+    r = oracle.residual_rows(C64, b32.astype(np.float64), x.cpu().numpy(), float(F32(0.1)), 0.0)
+    assert rep["residual_true"] == pytest.approx(np.linalg.norm(r) / np.linalg.norm(b32), rel=1e-6)
+    assert rep["iterations"] == 90 and rep["restarts"] == 3
+    assert rep["residual_true"] < 1e-2
+
+
+def test_fgmres_converges_to_oracle_solution_well_conditioned(ctx, rbf):
+    """With sigma well below the spacing the system is well conditioned: mixed
+    precision FGMRES with float64 refinement reaches 1e-10 and the weights of the
+    oracle's dense Cholesky solve."""
+    cl = synth.sphere(400, seed=4)
+    C, b = oracle.build_centers(cl.points, cl.normals, 0.05)
+    Cd, C64 = c4(C)
+    b32 = b.astype(np.float32)
+    s = float(F32(0.04))
+    plan = rbf.Plan(ctx, Cd, sigma=0.04, k=0.0)
+    x, rep = plan.solve(dev(b32), m=40, max_it=400, tol=1e-10)
+    assert rep["converged"] == 1 and rep["residual_true"] <= 1e-10
+    xo, _ = oracle.solve_dense(C64, b32.astype(np.float64), s)
+    assert rel2(x.cpu().numpy(), xo) <= 1e-8
+
+
+def test_fgmres_schwarz_single_block_is_direct(ctx, rbf):
+    """One subdomain holding every centre: RAS is A^-1 (up to float32), so FGMRES
+    needs one or two iterations."""
+    cl = synth.sphere(40, seed=5)
+    C, b = oracle.build_centers(cl.points, cl.normals, 0.05)
+    Cd, _ = c4(C)
+    plan = rbf.Plan(ctx, Cd, sigma=0.08, k=0.0)
+    x, rep = plan.solve(dev(b.astype(np.float32)), precond="schwarz", core=120, block=120, shift=0.0, tol=1e-5,
+                        max_it=20)
+    assert rep["converged"] == 1 and rep["iterations"] <= 3
+
+
+def test_solve_schwarz_on_torus_patch(ctx, rbf):
+    _, C, b = torus_patch(theta=0.05)
+    Cd, C64 = c4(C)
+    b32 = b.astype(np.float32)
+    plan = rbf.Plan(ctx, Cd, sigma=0.02, k=6.0)
+    x, rep = plan.solve(dev(b32), precond="schwarz", core=96, block=128, shift=1e-4, escalate=True, m=20,
+                        max_it=40, fixed_iterations=True)
+    assert rep["iterations"] == 40 and rep["status"] == "RBF_OK"
+    r = oracle.residual_rows(C64, b32.astype(np.float64), x.cpu().numpy(), float(F32(0.02)), float(F32(6.0)))
+    assert rep["residual_true"] == pytest.approx(np.linalg.norm(r) / np.linalg.norm(b32), rel=1e-6)
+    assert rep["residual_true"] < 1.0
+
+
+# ---------------------------------------------------------------------- grid
+def _grid_check(plan, C64, w, sigma, k, lo, hi, dims, nsample=20000, seed=0):
+    f = plan.eval_grid(dev(w, torch.float64), lo, hi, dims).cpu().numpy().ravel().astype(np.float64)
+    total = int(np.prod(dims))
+    rng = np.random.default_rng(seed)
+    idx = np.unique(np.concatenate([rng.choice(total, min(nsample, total), replace=False),
+                                    [0, total - 1, dims[0] - 1, total - dims[0]]]))
+    P = oracle.grid_nodes(lo, hi, dims, idx)
+    f64 = oracle.eval_points(C64, w, float(F32(sigma)), float(F32(k)), P)
+    rng_f = f64.max() - f64.min()
+    assert np.abs(f[idx] - f64).max() <= 1e-4 * rng_f, (np.abs(f[idx] - f64).max(), rng_f)
+    return f
+
+
+def test_eval_grid_c1_with_oracle_weights(ctx, rbf, sphere_c1):
+    """The whole evaluation path on the 64^3 grid over [-1.2, 1.2]^3 with the
+    oracle's dense-Cholesky weights."""
+    C, b = oracle.build_centers(sphere_c1.points, sphere_c1.normals, 0.05)
+    Cd, C64 = c4(C)
+    xo, res = oracle.solve_dense(C64, b, float(F32(0.1)))
+    plan = rbf.Plan(ctx, Cd, sigma=0.1, k=0.0)
+    _grid_check(plan, C64, xo, 0.1, 0.0, (-1.2,) * 3, (1.2,) * 3, (64, 64, 64))
+
+
+def test_eval_grid_truncated_ragged(ctx, rbf):
+    _, C, _ = torus_patch(theta=0.1)
+    Cd, C64 = c4(C)
+    plan = rbf.Plan(ctx, Cd, sigma=0.02, k=6.0)
+    w = np.random.default_rng(7).standard_normal(len(C))
+    lo = C64.min(0) - 0.05
+    hi = C64.max(0) + 0.05
+    _grid_check(plan, C64, w, 0.02, 6.0, lo, hi, (37, 29, 23))
+    f1 = _grid_check(plan, C64, w, 0.02, 6.0, lo, hi, (61, 8, 5), seed=1)
+    f2 = plan.eval_grid(dev(w, torch.float64), lo, hi, (61, 8, 5)).cpu().numpy().ravel()
+    assert np.array_equal(f1.astype(np.float32), f2)        # cached pair list, same result
+
+
+def test_eval_grid_single_node_and_far_grid(ctx, rbf):
+    rng = np.random.default_rng(1)
+    C = rng.uniform(0, 1, (500, 3))
+    Cd, C64 = c4(C)
+    plan = rbf.Plan(ctx, Cd, sigma=0.05, k=4.0)
+    w = rng.standard_normal(500)
+    f = plan.eval_grid(dev(w, torch.float64), (0.5, 0.5, 0.5), (0.5, 0.5, 0.5), (1, 1, 1)).cpu().numpy()
+    f64 = oracle.eval_points(C64, w, float(F32(0.05)), float(F32(4.0)), np.array([[0.5, 0.5, 0.5]]))
+    assert abs(f.ravel()[0] - f64[0]) <= 1e-5 * np.abs(w).sum()
+    far = plan.eval_grid(dev(w, torch.float64), (5, 5, 5), (6, 6, 6), (9, 9, 9)).cpu().numpy()
+    assert np.all(far == 0)
+
+
+# ---------------------------------------------------------------------- errors
+def test_invalid_arguments(ctx, rbf):
+    C = dev(np.zeros((10, 4), dtype=np.float32))
+    for kw in (dict(sigma=0.0, k=1.0), dict(sigma=-1.0, k=1.0), dict(sigma=0.1, k=13.0), dict(sigma=float("nan"))):
+        with pytest.raises(rbf.RbfError) as e:
+            rbf.Plan(ctx, C, **kw)
+        assert e.value.status == 1
+    plan = rbf.Plan(ctx, dev(np.random.default_rng(0).uniform(0, 1, (100, 4)).astype(np.float32)), sigma=0.1, k=3.0)
+    with pytest.raises(rbf.RbfError):
+        plan.eval_grid(dev(np.zeros(100), torch.float64), (0, 0, 0), (1, 1, 1), (0, 4, 4))
+    with pytest.raises(rbf.RbfError) as e:
+        plan.schwarz_setup(core=64, block=256)
+    assert e.value.status == 8
+    with pytest.raises(rbf.RbfError):
+        plan.schwarz_apply(dev(np.zeros(100, dtype=np.float32)))
