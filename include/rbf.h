@@ -105,8 +105,8 @@ rbf_status rbf_build_centers(rbf_ctx *ctx, const float *pts, const float *nrm, i
  *
  * Binning is a definition shared with the tests:
  *   lo = componentwise minimum of the centres, ext = hi - lo (float32);
- *   cell edge hc = k sigma / cells_per_cutoff (k > 0), or max(ext)/8 (k = 0;
- *   1 if ext is 0); fine cells hf = hc / 2^levels; inv = (float)(2^levels / hc)
+ *   cell edge hc = k sigma / cells_per_cutoff (k > 0), or
+ *   max(min(max(ext)/8, 3 sigma), max(ext)/128) in double (k = 0; 1 if ext is 0); fine cells hf = hc / 2^levels; inv = (float)(2^levels / hc)
  *   computed in double; q_d = floor((c_d - lo_d) * inv) in float32;
  *   key = Morton interleave (x in bit 0) of q; cell = key >> (3 levels);
  *   centres are ordered by a stable sort on key.  At most 1024 fine cells per
@@ -168,11 +168,17 @@ rbf_status rbf_matvec(rbf_plan *plan, const float *z, float *y, void *stream);
  * Costs about one double-precision product. */
 rbf_status rbf_count_pairs(rbf_plan *plan, int64_t *count, void *stream);
 
-/* True residual in double precision (difference, square distance, exp and
- * accumulation all float64): r = b - A~ x, caller order.
+/* True residual r = b - A~ x with float64-class accuracy, caller order.
+ *   mode  : RBF_RESIDUAL_DF (default, 0): double-float arithmetic (pairs of
+ *           float32 with error-free transformations, table-driven exp2) on the
+ *           float32 pipes, per-term relative error ~1e-14;
+ *           RBF_RESIDUAL_F64 (1): native float64 difference, square distance,
+ *           exp and accumulation (B300's FP64 rate makes this ~25x slower).
+ *           The cut-off is decided on the float64-class squared distance.
  *   b : n float (targets), x : n double, r : n double (out).
  *   norms : host, optional, [|r|_2, |b|_2]. */
-rbf_status rbf_residual(rbf_plan *plan, const float *b, const double *x, double *r, double *norms,
+enum { RBF_RESIDUAL_DF = 0, RBF_RESIDUAL_F64 = 1 };
+rbf_status rbf_residual(rbf_plan *plan, const float *b, const double *x, double *r, double *norms, int mode,
                         void *stream);
 
 /* ------------------------------------------------------------------------
@@ -207,7 +213,8 @@ rbf_status rbf_schwarz_apply(rbf_plan *plan, const float *v, float *z, void *str
  * RASM).  Precision: product and preconditioner in float32; Arnoldi basis,
  * classical Gram-Schmidt applied twice, Hessenberg least squares and the
  * solution vector in float64.  Each restart recomputes the true residual with
- * rbf_residual's float64 kernel (iterative refinement: x += GMRES(b - A~ x)).
+ * rbf_residual's float64-accurate kernel (iterative refinement:
+ * x += GMRES(b - A~ x)).
  * ------------------------------------------------------------------------ */
 enum { RBF_PRECOND_NONE = 0, RBF_PRECOND_SCHWARZ = 1 };
 
@@ -219,7 +226,8 @@ typedef struct {
     rbf_schwarz_params schwarz;
     int fixed_iterations;   /* non-zero: run exactly max_it iterations, ignoring tol */
     int true_residual_each_restart; /* non-zero (default): float64 residual at every restart;
-                                       zero: only at the end, the restart uses the estimate */
+                                       zero: float32 product at restarts, float64 residual at the end */
+    int residual_mode;      /* RBF_RESIDUAL_DF (0) or RBF_RESIDUAL_F64 (1), see rbf_residual */
 } rbf_solve_params;
 
 typedef struct {

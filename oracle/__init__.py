@@ -229,7 +229,8 @@ def binning(C32: np.ndarray, sigma: float, k: float, cells_per_cutoff: int = 1, 
     """Cell binning of the centres in FP32, as a definition.
 
     * lo = componentwise minimum of the centres; ext = hi - lo (FP32);
-    * cell edge hc = k sigma / s (k > 0) or max(ext)/8 (k = 0, or 1 if that is 0);
+    * cell edge hc = k sigma / s (k > 0), or max(min(max(ext)/8, 3 sigma), max(ext)/128)
+      (k = 0; 1 if ext is 0);
     * fine edge hf = hc / 2^L, inv = float32(2^L / hc) computed in double;
     * q_d = floor((c_d - lo_d) * inv) in float32 arithmetic;
     * nbits = max(L, bit length of max_d floor(ext_d * inv)) (must be <= 10);
@@ -247,7 +248,7 @@ def binning(C32: np.ndarray, sigma: float, k: float, cells_per_cutoff: int = 1, 
         hc = float(np.float32(k)) * float(np.float32(sigma)) / float(cells_per_cutoff)
     else:
         m = float(ext.max())
-        hc = m / 8.0 if m > 0 else 1.0
+        hc = max(min(m / 8.0, 3.0 * float(np.float32(sigma))), m / 128.0) if m > 0 else 1.0
     inv = np.float32((2.0 ** L) / hc)
     qmax = int(np.floor(ext * inv).max()) if len(c) else 0
     nbits = max(L, int(qmax).bit_length())

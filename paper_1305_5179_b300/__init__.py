@@ -27,6 +27,7 @@ RBF_OK = 0
 STATUS = {0: "RBF_OK", 1: "RBF_ERR_INVALID", 2: "RBF_ERR_OOM", 3: "RBF_ERR_CUDA", 4: "RBF_ERR_NOT_CONVERGED",
           5: "RBF_ERR_BREAKDOWN", 6: "RBF_ERR_TIMEOUT", 7: "RBF_ERR_NOT_SPD", 8: "RBF_ERR_UNSUPPORTED"}
 PRECOND = {"none": 0, "schwarz": 1}
+RESIDUAL = {"df": 0, "f64": 1}
 
 # every entry point declared in include/rbf.h
 EXPORTS = (
@@ -63,7 +64,7 @@ class SchwarzParams(ctypes.Structure):
 class SolveParams(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("max_it", ctypes.c_int), ("tol", ctypes.c_double), ("precond", ctypes.c_int),
                 ("schwarz", SchwarzParams), ("fixed_iterations", ctypes.c_int),
-                ("true_residual_each_restart", ctypes.c_int)]
+                ("true_residual_each_restart", ctypes.c_int), ("residual_mode", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -114,7 +115,7 @@ def lib() -> ctypes.CDLL:
         "rbf_plan_export_binning": ([P, P, P, P, P, P], I),
         "rbf_matvec": ([P, P, P, P], I),
         "rbf_count_pairs": ([P, ctypes.POINTER(I64), P], I),
-        "rbf_residual": ([P, P, P, P, ctypes.POINTER(D), P], I),
+        "rbf_residual": ([P, P, P, P, ctypes.POINTER(D), I, P], I),
         "rbf_schwarz_setup": ([P, ctypes.POINTER(SchwarzParams), ctypes.POINTER(I64), P], I),
         "rbf_schwarz_apply": ([P, P, P, P], I),
         "rbf_plan_solve": ([P, P, ctypes.POINTER(SolveParams), P, ctypes.POINTER(Report), P], I),
@@ -221,13 +222,15 @@ def _grid(lo, hi, dims) -> Grid:
 
 
 def _solve_params(m=50, max_it=500, tol=1e-6, precond="none", core=96, block=128, shift=1e-4, restricted=True,
-                  escalate=True, fixed_iterations=False, true_residual_each_restart=True) -> SolveParams:
+                  escalate=True, fixed_iterations=False, true_residual_each_restart=True,
+                  residual="df") -> SolveParams:
     sp = SolveParams()
     sp.m, sp.max_it, sp.tol = int(m), int(max_it), float(tol)
     sp.precond = PRECOND[precond] if isinstance(precond, str) else int(precond)
     sp.schwarz = SchwarzParams(int(core), int(block), float(shift), int(bool(restricted)), int(bool(escalate)))
     sp.fixed_iterations = int(bool(fixed_iterations))
     sp.true_residual_each_restart = int(bool(true_residual_each_restart))
+    sp.residual_mode = RESIDUAL[residual]
     return sp
 
 
@@ -289,13 +292,15 @@ class Plan:
         self.ctx.check(lib().rbf_count_pairs(self._h, ctypes.byref(c), _stream(stream)), "rbf_count_pairs")
         return int(c.value)
 
-    def residual(self, b, x, stream=None):
+    def residual(self, b, x, mode="df", stream=None):
+        """True residual b - A~ x (float64); mode "df" (double-float) or "f64" (native)."""
         import torch
         _req(b, torch.float32, "b", self.n)
         _req(x, torch.float64, "x", self.n)
         r = torch.empty(self.n, dtype=torch.float64, device=self.device)
         norms = (ctypes.c_double * 2)()
-        self.ctx.check(lib().rbf_residual(self._h, _ptr(b), _ptr(x), _ptr(r), norms, _stream(stream)), "rbf_residual")
+        self.ctx.check(lib().rbf_residual(self._h, _ptr(b), _ptr(x), _ptr(r), norms, RESIDUAL[mode],
+                                          _stream(stream)), "rbf_residual")
         return r, (norms[0], norms[1])
 
     def schwarz_setup(self, core=96, block=128, shift=1e-4, restricted=True, escalate=False, stream=None) -> int:

@@ -204,7 +204,8 @@ rbf_status rbf_count_pairs(rbf_plan *P, int64_t *count, void *stream) {
     });
 }
 
-rbf_status rbf_residual(rbf_plan *P, const float *b, const double *x, double *r, double *norms, void *stream) {
+rbf_status rbf_residual(rbf_plan *P, const float *b, const double *x, double *r, double *norms, int mode,
+                        void *stream) {
     if (!P) return RBF_ERR_INVALID;
     return guarded(P->ctx, [&]() {
         RBF_CHECK(b && x && r, RBF_ERR_INVALID, "null pointer argument");
@@ -216,7 +217,9 @@ rbf_status rbf_residual(rbf_plan *P, const float *b, const double *x, double *r,
         rs.alloc(P->n, s);
         permute_to_binned_f32(P, b, bs.p, s);
         permute_to_binned_f64(P, x, xs.p, s);
-        residual_binned_f64(P, bs.p, xs.p, rs.p, nullptr, s);
+        RBF_CHECK(mode == RBF_RESIDUAL_DF || mode == RBF_RESIDUAL_F64, RBF_ERR_INVALID, "unknown residual mode %d",
+                  mode);
+        residual_binned(P, mode, bs.p, xs.p, rs.p, s);
         permute_from_binned_f64(P, rs.p, r, s);
         if (norms) {
             std::vector<double> hr(P->n);
@@ -269,6 +272,8 @@ rbf_status rbf_plan_solve(rbf_plan *P, const float *b, const rbf_solve_params *p
         RBF_CHECK(p->precond == RBF_PRECOND_NONE || p->precond == RBF_PRECOND_SCHWARZ, RBF_ERR_INVALID,
                   "unknown preconditioner %d", p->precond);
         RBF_CHECK(std::isfinite(p->tol) && p->tol >= 0, RBF_ERR_INVALID, "tol must be finite and >= 0");
+        RBF_CHECK(p->residual_mode == RBF_RESIDUAL_DF || p->residual_mode == RBF_RESIDUAL_F64, RBF_ERR_INVALID,
+                  "unknown residual mode %d", p->residual_mode);
         return fgmres_solve(P, b, *p, x, report, S(stream));
     });
 }

@@ -5,7 +5,8 @@
 // Arnoldi basis V (float64), classical Gram-Schmidt applied twice, the
 // Hessenberg matrix, its Givens rotations and least-squares solve, and the
 // iterate x are float64.  Every restart recomputes the true residual
-// r = b - A~ x with the float64 product kernel, so the outer loop is iterative
+// r = b - A~ x with a float64-accurate product (double-float on the float32
+// pipes by default, or native float64), so the outer loop is iterative
 // refinement x <- x + FGMRES(r).
 //
 // Per inner step j: Z_j = M^-1 V_j; w = A~ Z_j; two passes of h = V^T w,
@@ -238,7 +239,7 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
         if (!have_true) {
             if (each_restart) {
                 t_res.begin(s);
-                residual_binned_f64(P, bs.p, x.p, r.p, nullptr, s);
+                residual_binned(P, p.residual_mode, bs.p, x.p, r.p, s);
                 t_res.end(s);
             } else {
                 // float32 product for the restart vector; the float64 residual runs once at the end
@@ -352,7 +353,7 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
     // final true residual (float64)
     if (!have_true || !each_restart) {
         t_res.begin(s);
-        residual_binned_f64(P, bs.p, x.p, r.p, nullptr, s);
+        residual_binned(P, p.residual_mode, bs.p, x.p, r.p, s);
         t_res.end(s);
         norm2_dev(r.p, n, G, part.p, scal.p, s);
         double r2 = 0;

@@ -1,6 +1,6 @@
 // Step 3 of Algorithm 1 (Eq. matxvet): P_f on the nodes of a structured grid.
 //
-// The grid is cut into bricks of 8 x 8 x 4 nodes (256 targets, one tile of the
+// The grid is cut into bricks of 8 x 4 x 4 nodes (128 targets, one tile of the
 // product kernel); each brick gets a box and a pair list against the source
 // blocks exactly like the tiles of centres, so bricks far from every centre
 // cost nothing.  The pair list is cached on the plan for repeated grids.
@@ -20,8 +20,8 @@ __global__ void k_brick_boxes(int64_t nb, int bx, int by, int gx, int gy, int gz
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nb) return;
     int ix = (int)(t % bx), iy = (int)((t / bx) % by), iz = (int)(t / ((int64_t)bx * by));
-    int x0 = ix * 8, y0 = iy * 8, z0 = iz * 4;
-    int x1 = min(x0 + 7, gx - 1), y1 = min(y0 + 7, gy - 1), z1 = min(z0 + 3, gz - 1);
+    int x0 = ix * 8, y0 = iy * 4, z0 = iz * 4;
+    int x1 = min(x0 + 7, gx - 1), y1 = min(y0 + 3, gy - 1), z1 = min(z0 + 3, gz - 1);
     lo[t] = make_float4(fmaf((float)x0, sx, lox), fmaf((float)y0, sy, loy), fmaf((float)z0, sz, loz), 0.f);
     hi[t] = make_float4(fmaf((float)x1, sx, lox), fmaf((float)y1, sy, loy), fmaf((float)z1, sz, loz), 0.f);
 }
@@ -65,7 +65,7 @@ static int64_t grid_prepare(rbf_plan *P, const rbf_grid &g, cudaStream_t s) {
         gc.valid = false;
         gc.g = g;
         gc.bricks[0] = ceil_div(g.dims[0], 8);
-        gc.bricks[1] = ceil_div(g.dims[1], 8);
+        gc.bricks[1] = ceil_div(g.dims[1], 4);
         gc.bricks[2] = ceil_div(g.dims[2], 4);
         int64_t nb = gc.bricks[0] * gc.bricks[1] * gc.bricks[2];
         float st[3];

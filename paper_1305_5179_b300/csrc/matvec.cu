@@ -2,17 +2,21 @@
 // (Sec. III.A, Eq. matrixEntries): the operation GMRES repeats (the paper's MatShell).
 //
 // float32 kernel.  One CTA = one segment of a tile's pair list, 4 warps.  Every
-// warp holds all 256 targets of the tile (8 per lane) and walks every 4th block
-// of the segment.  For a block with centre c_B and scaled source offsets
-// s_j = (x_j - c_B) * scl (precomputed as (2 s_j, -|s_j|^2)), and a target with
-// d = (x_i - c_B) * scl:
+// warp holds all 128 targets of the tile (4 per lane, as 2 packed pairs for the
+// f32x2 FMA unit) and walks every 4th block of the segment.  For a block with
+// centre c_B and scaled source offsets s_j = (x_j - c_B) * scl (precomputed as
+// (2 s_j, -|s_j|^2)), and a target with d = (x_i - c_B) * scl:
 //      |x_i - x_j|^2 scl^2 = |d|^2 - 2 d.s_j + |s_j|^2,
 //      phi_ij = 2^(-|d|^2) * 2^(d.(2 s_j) - |s_j|^2)
-// so each pair costs 3 FFMA + 1 MUFU.EX2 + 1 FFMA (accumulate), and the per
-// (target, block) factor 2^(-|d|^2) is applied once per block.  Blocks that are
-// not entirely inside the cut-off compare d.(2 s_j) - |s_j|^2 against the
+// so a pair of targets costs 3 FFMA2 + 2 MUFU.EX2 + 1 FFMA2 per source, and the
+// per (target, block) factor 2^(-|d|^2) is applied once per block.  Blocks that
+// are not entirely inside the cut-off compare d.(2 s_j) - |s_j|^2 against the
 // per-target threshold |d|^2 - R (R = scaled squared cut-off) before adding.
-// The 4 warps' partial sums are added in a fixed order (deterministic).
+// When 2 |d| r_B (r_B the scaled block radius) could exceed 64 for some target,
+// the block takes a shifted form 2^(-|d|^2 + c) * 2^(d.(2 s_j) - |s_j|^2 - c),
+// c = 2 |d| r_B, whose inner exponent is never positive (no overflow).
+// Sources of the next block are prefetched into registers while the current
+// block is computed.  The 4 warps' partial sums are added in a fixed order.
 //
 // float64 kernel (true residual): one thread per target, all arithmetic in
 // double precision, cut-off decided as |x_i - x_j|^2 < (k sigma)^2 in double.
@@ -23,27 +27,51 @@
 namespace {
 
 constexpr int kWarps = 4;
-constexpr int kPer = kChunk / 32;   // targets per lane
+constexpr int kPacks = kChunk / 64;   // packed target pairs per lane
+
+typedef unsigned long long f2;      // two float32 in one 64-bit register pair
+
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1,%2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &a, float &b) { asm("mov.b64 {%0,%1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 
 struct MvArgs {
     const float4 *pos;   // binned positions (targets, sorted mode)
     const float4 *src;
     const float *w;      // binned weights
     const int2 *blk;
-    const float4 *blk_c;
+    const float4 *blk_c; // (centre, overflow guard U_B = (32 / r_B)^2 in scaled units)
     const int32_t *ent;
     const int4 *seg;
     int64_t n;
     float scl, R;
-    float *out;          // direct: y (binned) / grid f; else partial [seg][256]
+    float *out;          // direct: y (binned) / grid f; else partial [seg][kChunk]
     int direct;
-    // grid targets
+    // grid targets: bricks of 8 x 4 x 4 nodes
     float glo[3], gstep[3];
     int gdim[3];
     int bdim[3];
 };
 
-// Target slot q = lane + 32 r of tile t: coordinates and validity.
+// Target slot q (0..kChunk-1) of tile t: coordinates and validity.
 template <bool kGrid>
 __device__ __forceinline__ bool target_xyz(const MvArgs &a, int64_t t, int q, float &x, float &y, float &z,
                                            int64_t &outidx) {
@@ -60,7 +88,7 @@ __device__ __forceinline__ bool target_xyz(const MvArgs &a, int64_t t, int q, fl
         return false;
     } else {
         int64_t bx = t % a.bdim[0], by = (t / a.bdim[0]) % a.bdim[1], bz = t / ((int64_t)a.bdim[0] * a.bdim[1]);
-        int ix = (int)bx * 8 + (q & 7), iy = (int)by * 8 + ((q >> 3) & 7), iz = (int)bz * 4 + (q >> 6);
+        int ix = (int)bx * 8 + (q & 7), iy = (int)by * 4 + ((q >> 3) & 3), iz = (int)bz * 4 + (q >> 5);
         bool v = ix < a.gdim[0] && iy < a.gdim[1] && iz < a.gdim[2];
         x = fmaf((float)ix, a.gstep[0], a.glo[0]);
         y = fmaf((float)iy, a.gstep[1], a.glo[1]);
@@ -70,79 +98,151 @@ __device__ __forceinline__ bool target_xyz(const MvArgs &a, int64_t t, int q, fl
     }
 }
 
-template <bool kMasked>
-__device__ __forceinline__ void block_sum(const float4 *__restrict__ ss, const float *__restrict__ sw, int cnt,
-                                          const float (&dx)[kPer], const float (&dy)[kPer], const float (&dz)[kPer],
-                                          const float (&thr)[kPer], float (&p)[kPer]) {
+struct Stage {           // one block of sources, duplicated for the f32x2 operands
+    ulonglong2 A[kBlk];  // (2 s_x, 2 s_x), (2 s_y, 2 s_y)
+    ulonglong2 B[kBlk];  // (2 s_z, 2 s_z), (b, b)
+    f2 W[kBlk];          // (w, w)
+};
+
+// p[k] = sum_j w_j 2^(arg_kj), arg = d.(2 s_j) - |s_j|^2 (- shift); masked: only arg > thr.
+template <bool kMasked, bool kShift>
+__device__ __forceinline__ void block_sum(const Stage &st, int cnt, const f2 (&dx)[kPacks], const f2 (&dy)[kPacks],
+                                          const f2 (&dz)[kPacks], const f2 (&thr)[kPacks], const f2 (&sh)[kPacks],
+                                          f2 (&p)[kPacks]) {
 #pragma unroll
-    for (int r = 0; r < kPer; ++r) p[r] = 0.f;
+    for (int k = 0; k < kPacks; ++k) p[k] = 0ull;
 #pragma unroll 4
     for (int j = 0; j < cnt; ++j) {
-        float4 s = ss[j];
-        float wj = sw[j];
+        const ulonglong2 A = st.A[j];
+        const ulonglong2 B = st.B[j];
+        const f2 W = st.W[j];
 #pragma unroll
-        for (int r = 0; r < kPer; ++r) {
-            float arg = fmaf(dx[r], s.x, fmaf(dy[r], s.y, fmaf(dz[r], s.z, s.w)));
-            float e = ex2_approx(arg);
-            if (kMasked) e = arg > thr[r] ? e : 0.f;
-            p[r] = fmaf(wj, e, p[r]);
+        for (int k = 0; k < kPacks; ++k) {
+            f2 c0 = kShift ? sub2(B.y, sh[k]) : B.y;
+            f2 arg = fma2(dx[k], A.x, fma2(dy[k], A.y, fma2(dz[k], B.x, c0)));
+            float a0, a1;
+            upk(arg, a0, a1);
+            float e0 = ex2_approx(a0), e1 = ex2_approx(a1);
+            if (kMasked) {
+                float t0, t1;
+                upk(thr[k], t0, t1);
+                e0 = a0 > t0 ? e0 : 0.f;
+                e1 = a1 > t1 ? e1 : 0.f;
+            }
+            p[k] = fma2(W, pk(e0, e1), p[k]);
         }
     }
 }
 
 template <bool kGrid>
 __global__ void __launch_bounds__(kWarps * 32) k_matvec_f32(MvArgs a) {
-    __shared__ float4 s_src[kWarps][kBlk];
-    __shared__ float s_w[kWarps][kBlk];
+    __shared__ Stage s_st[kWarps];
     __shared__ float s_red[kWarps][kChunk];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int4 sg = a.seg[blockIdx.x];
     const int64_t t = sg.x;
+    const f2 scl2 = pk(a.scl, a.scl);
 
-    float tx[kPer], ty[kPer], tz[kPer], acc[kPer];
+    f2 tx[kPacks], ty[kPacks], tz[kPacks], acc[kPacks];
 #pragma unroll
-    for (int r = 0; r < kPer; ++r) {
+    for (int k = 0; k < kPacks; ++k) {
+        float x0, y0, z0, x1, y1, z1;
         int64_t oi;
-        target_xyz<kGrid>(a, t, lane + 32 * r, tx[r], ty[r], tz[r], oi);
-        acc[r] = 0.f;
+        target_xyz<kGrid>(a, t, 64 * k + 2 * lane, x0, y0, z0, oi);
+        target_xyz<kGrid>(a, t, 64 * k + 2 * lane + 1, x1, y1, z1, oi);
+        tx[k] = pk(x0, x1);
+        ty[k] = pk(y0, y1);
+        tz[k] = pk(z0, z1);
+        acc[k] = 0ull;
     }
-    for (int e = sg.y + warp; e < sg.z; e += kWarps) {
-        int ent = a.ent[e];
-        bool masked = ent < 0;
-        int b = ent & 0x7fffffff;
-        int2 bi = a.blk[b];
-        float4 c = a.blk_c[b];
-        // stage the block (zero weight in the padding makes padded terms vanish)
-        float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
-        float wv = 0.f;
+    Stage &st = s_st[warp];
+    // prefetch the first block
+    int e = sg.y + warp;
+    int ent = 0;
+    int2 bi = make_int2(0, 0);
+    float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
+    float wv = 0.f;
+    if (e < sg.z) {
+        ent = a.ent[e];
+        bi = a.blk[ent & 0x7fffffff];
         if (lane < bi.y) {
             sv = a.src[bi.x + lane];
             wv = a.w[bi.x + lane];
         }
-        s_src[warp][lane] = sv;
-        s_w[warp][lane] = wv;
+    }
+    for (; e < sg.z; e += kWarps) {
+        const bool masked = ent < 0;
+        const int b = ent & 0x7fffffff;
+        const int cnt = (bi.y + 3) & ~3;
+        const float4 c = a.blk_c[b];
+        st.A[lane] = make_ulonglong2(pk(sv.x, sv.x), pk(sv.y, sv.y));
+        st.B[lane] = make_ulonglong2(pk(sv.z, sv.z), pk(sv.w, sv.w));
+        st.W[lane] = pk(wv, wv);
         __syncwarp();
-        float dx[kPer], dy[kPer], dz[kPer], ea[kPer], thr[kPer], p[kPer];
-#pragma unroll
-        for (int r = 0; r < kPer; ++r) {
-            dx[r] = (tx[r] - c.x) * a.scl;
-            dy[r] = (ty[r] - c.y) * a.scl;
-            dz[r] = (tz[r] - c.z) * a.scl;
-            float d2 = fmaf(dx[r], dx[r], fmaf(dy[r], dy[r], dz[r] * dz[r]));
-            ea[r] = ex2_approx(-d2);
-            thr[r] = d2 - a.R;
+        // prefetch the next block while this one is computed
+        const int en = e + kWarps;
+        if (en < sg.z) {
+            ent = a.ent[en];
+            bi = a.blk[ent & 0x7fffffff];
+            sv = make_float4(0.f, 0.f, 0.f, 0.f);
+            wv = 0.f;
+            if (lane < bi.y) {
+                sv = a.src[bi.x + lane];
+                wv = a.w[bi.x + lane];
+            }
         }
-        int cnt = (bi.y + 3) & ~3;
-        if (masked)
-            block_sum<true>(s_src[warp], s_w[warp], cnt, dx, dy, dz, thr, p);
-        else
-            block_sum<false>(s_src[warp], s_w[warp], cnt, dx, dy, dz, thr, p);
+        f2 dx[kPacks], dy[kPacks], dz[kPacks], d2[kPacks], thr[kPacks], sh[kPacks], ea[kPacks], p[kPacks];
+        bool unsafe = false;
+        const f2 cx = pk(c.x, c.x), cy = pk(c.y, c.y), cz = pk(c.z, c.z), R2 = pk(a.R, a.R);
 #pragma unroll
-        for (int r = 0; r < kPer; ++r) acc[r] = fmaf(ea[r], p[r], acc[r]);
+        for (int k = 0; k < kPacks; ++k) {
+            dx[k] = mul2(sub2(tx[k], cx), scl2);
+            dy[k] = mul2(sub2(ty[k], cy), scl2);
+            dz[k] = mul2(sub2(tz[k], cz), scl2);
+            d2[k] = fma2(dx[k], dx[k], fma2(dy[k], dy[k], mul2(dz[k], dz[k])));
+            thr[k] = sub2(d2[k], R2);
+            float q0, q1;
+            upk(d2[k], q0, q1);
+            unsafe |= (q0 > c.w) | (q1 > c.w);
+        }
+        unsafe = __any_sync(0xffffffffu, unsafe);
+        if (!unsafe) {
+#pragma unroll
+            for (int k = 0; k < kPacks; ++k) {
+                float q0, q1;
+                upk(d2[k], q0, q1);
+                ea[k] = pk(ex2_approx(-q0), ex2_approx(-q1));
+            }
+            if (masked)
+                block_sum<true, false>(st, cnt, dx, dy, dz, thr, sh, p);
+            else
+                block_sum<false, false>(st, cnt, dx, dy, dz, thr, sh, p);
+        } else {
+            // shift c = 2 |d| r_B with r_B = 32 / sqrt(U_B)
+            const float rB = c.w < INFINITY ? 32.f * rsqrtf(c.w) : 0.f;
+#pragma unroll
+            for (int k = 0; k < kPacks; ++k) {
+                float q0, q1, t0, t1;
+                upk(d2[k], q0, q1);
+                upk(thr[k], t0, t1);
+                float c0 = 2.f * sqrtf(q0) * rB, c1 = 2.f * sqrtf(q1) * rB;
+                sh[k] = pk(c0, c1);
+                ea[k] = pk(ex2_approx(c0 - q0), ex2_approx(c1 - q1));
+                thr[k] = pk(t0 - c0, t1 - c1);
+            }
+            block_sum<true, true>(st, cnt, dx, dy, dz, thr, sh, p);
+        }
+#pragma unroll
+        for (int k = 0; k < kPacks; ++k) acc[k] = fma2(ea[k], p[k], acc[k]);
         __syncwarp();
     }
 #pragma unroll
-    for (int r = 0; r < kPer; ++r) s_red[warp][lane + 32 * r] = acc[r];
+    for (int k = 0; k < kPacks; ++k) {
+        float a0, a1;
+        upk(acc[k], a0, a1);
+        s_red[warp][64 * k + 2 * lane] = a0;
+        s_red[warp][64 * k + 2 * lane + 1] = a1;
+    }
     __syncthreads();
     for (int q = threadIdx.x; q < kChunk; q += kWarps * 32) {
         float v = ((s_red[0][q] + s_red[1][q]) + s_red[2][q]) + s_red[3][q];

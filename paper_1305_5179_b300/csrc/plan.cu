@@ -71,7 +71,7 @@ __global__ void k_fill_blocks(const int32_t *__restrict__ start, const int32_t *
     for (int k = 0; k * kBlk < m; ++k) blk[b0 + k] = make_int2(s + k * kBlk, min(kBlk, m - k * kBlk));
 }
 
-// One warp per block: box, centre, radius, and the scaled source offsets.
+// One warp per block: box, centre, overflow guard, and the scaled source offsets.
 __global__ void k_block_geom(const float4 *__restrict__ pos, const int2 *__restrict__ blk, int64_t nblk, float scl,
                              float4 *__restrict__ bc, float4 *__restrict__ blo, float4 *__restrict__ bhi,
                              float4 *__restrict__ src) {
@@ -91,7 +91,9 @@ __global__ void k_block_geom(const float4 *__restrict__ pos, const int2 *__restr
     float cx = 0.5f * (mn[0] + mx[0]), cy = 0.5f * (mn[1] + mx[1]), cz = 0.5f * (mn[2] + mx[2]);
     if (lane == 0) {
         float hx = mx[0] - mn[0], hy = mx[1] - mn[1], hz = mx[2] - mn[2];
-        bc[b] = make_float4(cx, cy, cz, 0.5f * sqrtf(hx * hx + hy * hy + hz * hz));
+        // w: overflow guard U = (32 / r)^2, r the block radius in scaled units (see the product kernel)
+        float r = 0.5f * sqrtf(hx * hx + hy * hy + hz * hz) * scl;
+        bc[b] = make_float4(cx, cy, cz, r > 0.f ? (32.f / r) * (32.f / r) : INFINITY);
         blo[b] = make_float4(mn[0], mn[1], mn[2], 0.f);
         bhi[b] = make_float4(mx[0], mx[1], mx[2], 0.f);
     }
@@ -332,8 +334,10 @@ void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s) {
     if (P->k > 0.f) {
         hc = (double)P->k * (double)P->sigma / (double)P->cells_per_cutoff;
     } else {
+        // untruncated: cells of at most 3 sigma keep blocks compact in scaled units, at least
+        // max(ext)/128 keeps the fine grid within 1024 cells per axis
         double m = std::max({(double)ext[0], (double)ext[1], (double)ext[2]});
-        hc = m > 0 ? m / 8.0 : 1.0;
+        hc = m > 0 ? std::max(std::min(m / 8.0, 3.0 * (double)P->sigma), m / 128.0) : 1.0;
     }
     P->inv = (float)(std::ldexp(1.0, P->levels) / hc);
     float qmaxf = 0.f;

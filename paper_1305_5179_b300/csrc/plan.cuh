@@ -3,7 +3,7 @@
 #include "common.cuh"
 
 constexpr int kBlk = 32;      // sources per block (one warp stages one block)
-constexpr int kChunk = 256;   // targets per tile (8 per lane of a warp)
+constexpr int kChunk = 128;   // targets per tile (4 per lane of a warp, as 2 packed pairs)
 
 // A list of (target tile, source block) work: entries of a tile are contiguous,
 // split into segments (one CTA each) when there are too few tiles to fill the GPU.
@@ -57,7 +57,7 @@ struct rbf_plan {
     PBuf<int32_t> cell_blk;    // ncells + 1: blocks of cell c are [cell_blk[c], cell_blk[c+1])
     PBuf<float4> pos;          // binned positions (x, y, z, 0)
     PBuf<int2> blk;            // (start, count)
-    PBuf<float4> blk_c;        // block centre (x, y, z, radius)
+    PBuf<float4> blk_c;        // block centre (x, y, z) and overflow guard (32 / scaled radius)^2
     PBuf<float4> blk_lo, blk_hi;
     PBuf<float4> src;          // per binned source: (2 s_x, 2 s_y, 2 s_z, -|s|^2), s = scaled offset to its block centre
     PBuf<float4> chk_lo, chk_hi;
@@ -90,6 +90,15 @@ int64_t count_pairs(rbf_plan *P, cudaStream_t s);
 // r = b - A~ x in float64 (binned order); counts pairs when cnt != nullptr (device int64).
 void residual_binned_f64(rbf_plan *P, const float *bs, const double *xs, double *rs,
                          unsigned long long *cnt, cudaStream_t s);
+// residual_df.cu: the same residual in double-float arithmetic on the float32 pipes.
+void residual_binned_df(rbf_plan *P, const float *bs, const double *xs, double *rs, cudaStream_t s);
+// dispatch on rbf_residual_mode
+inline void residual_binned(rbf_plan *P, int mode, const float *bs, const double *xs, double *rs, cudaStream_t s) {
+    if (mode == RBF_RESIDUAL_F64)
+        residual_binned_f64(P, bs, xs, rs, nullptr, s);
+    else
+        residual_binned_df(P, bs, xs, rs, s);
+}
 
 // schwarz.cu
 void schwarz_setup(rbf_plan *P, const rbf_schwarz_params &p, int64_t *failed_host, cudaStream_t s);

@@ -1,0 +1,197 @@
+// True residual r = b - A~ x with float64-class accuracy on the float32 pipes.
+//
+// B300's FP64 units run at a small fraction of its FP32 rate, so the residual
+// product (one per restart of the refinement loop) is evaluated in
+// double-float arithmetic: every quantity is an unevaluated sum hi + lo of two
+// float32, combined with the error-free transformations TwoSum (Knuth) and
+// TwoProd (via FMA).  Per pair:
+//   d = p - q exactly (TwoSum per axis; p, q are float32),
+//   r2 = |d|^2 to ~2^-47 relative,
+//   cut-off  r2 < (k sigma)^2 against a double-float constant,
+//   t = r2 log2(e)/(2 sigma^2),
+//   2^-t by the table-driven method of P. T. P. Tang (ACM TOMS 15(2), 1989):
+//     t = e + j/64 + f with |f| <= 1/128, 2^-t = 2^-e 2^(-j/64) exp(-f ln 2),
+//     2^(-j/64) from a 64-entry double-float table built on the host,
+//     exp(-g), |g| <= ln2/128, by its Taylor series to g^5 (truncation < 4e-17),
+//   product with x_j (double-float split of the float64 weight) and
+//   accumulation of each block's <= 32 terms in double-float, added to a float64
+//   accumulator once per block.
+// Per-term relative error is of order 1e-14.
+#include <cmath>
+
+#include "plan.cuh"
+
+namespace {
+
+constexpr int kT = kChunk;   // one thread per target
+
+struct df {
+    float h, l;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ df two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+struct DfConst {
+    float Ch, Cl;     // log2(e) / (2 sigma^2)
+    float Rh, Rl;     // (k sigma)^2, or Rh = +inf when untruncated
+    float Lh, Ll;     // ln 2
+};
+
+__constant__ float2 c_tab[64];   // 2^(-j/64) as (hi, lo)
+
+// sum over one staged block of w_j 2^(-t_ij) for the target (px, py, pz)
+__device__ __forceinline__ df block_terms(float px, float py, float pz, const float4 *__restrict__ sp,
+                                          const float2 *__restrict__ sw, int cnt, const DfConst &k,
+                                          const float2 *__restrict__ tab) {
+    const float Lh = k.Lh, Ll = k.Ll;
+    df acc = {0.f, 0.f};
+    for (int j = 0; j < cnt; ++j) {
+        const float4 q = sp[j];
+        const float2 w = sw[j];
+        df dx = two_sum(px, -q.x), dy = two_sum(py, -q.y), dz = two_sum(pz, -q.z);
+        // squares: dh^2 + 2 dh dl (dl^2 < 2^-48 dh^2 is dropped)
+        df sx = two_prod(dx.h, dx.h), sy = two_prod(dy.h, dy.h), sz = two_prod(dz.h, dz.h);
+        sx.l = __fmaf_rn(2.f * dx.h, dx.l, sx.l);
+        sy.l = __fmaf_rn(2.f * dy.h, dy.l, sy.l);
+        sz.l = __fmaf_rn(2.f * dz.h, dz.l, sz.l);
+        df s = two_sum(sx.h, sy.h);
+        s.l = __fadd_rn(s.l, __fadd_rn(sx.l, sy.l));
+        df r2 = two_sum(s.h, sz.h);
+        r2.l = __fadd_rn(r2.l, __fadd_rn(s.l, sz.l));
+        r2 = two_sum(r2.h, r2.l);
+        const bool in = (r2.h < k.Rh) || (r2.h == k.Rh && r2.l < k.Rl);
+        // t = r2 * C
+        df t = two_prod(r2.h, k.Ch);
+        t.l = __fadd_rn(t.l, __fmaf_rn(r2.h, k.Cl, __fmul_rn(r2.l, k.Ch)));
+        float mf = rintf(__fmul_rn(t.h, 64.f));
+        int m = (int)mf;
+        float fh = __fsub_rn(t.h, __fmul_rn(mf, 0.015625f));        // exact: |fh| <= 1/128
+        // g = (fh + t.l) ln 2
+        df g = two_prod(fh, Lh);
+        g.l = __fadd_rn(g.l, __fmaf_rn(fh, Ll, __fmul_rn(t.l, Lh)));
+        // exp(-g) - 1 = -g + g^2/2 - g^3/6 + g^4/24 - g^5/120
+        df g2 = two_prod(g.h, g.h);
+        g2.l = __fmaf_rn(2.f * g.h, g.l, g2.l);
+        float rest = __fmul_rn(__fmul_rn(g2.h, g.h),
+                               __fmaf_rn(g.h, __fmaf_rn(g.h, -1.f / 120.f, 1.f / 24.f), -1.f / 6.f));
+        df D = two_sum(-g.h, 0.5f * g2.h);
+        D.l = __fadd_rn(D.l, __fadd_rn(__fmaf_rn(0.5f, g2.l, -g.l), rest));
+        // E = T_j (1 + D)
+        const float2 T = tab[m & 63];
+        df p = two_prod(T.x, D.h);
+        df E = two_sum(T.x, p.h);
+        E.l = __fadd_rn(E.l, __fadd_rn(p.l, __fmaf_rn(T.x, D.l, __fmaf_rn(T.y, D.h, T.y))));
+        // 2^-e
+        int e = m >> 6;
+        float sc = e <= 125 ? __int_as_float((127 - e) << 23) : 0.f;
+        E.h = __fmul_rn(E.h, sc);
+        E.l = __fmul_rn(E.l, sc);
+        // term = E * w, accumulated in double-float
+        df P = two_prod(E.h, w.x);
+        P.l = __fadd_rn(P.l, __fmaf_rn(E.h, w.y, __fmul_rn(E.l, w.x)));
+        if (!in) P.h = P.l = 0.f;
+        df a2 = two_sum(acc.h, P.h);
+        acc.h = a2.h;
+        acc.l = __fadd_rn(acc.l, __fadd_rn(a2.l, P.l));
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(kT) k_resid_df(const float4 *__restrict__ pos, const double *__restrict__ x,
+                                                 const int2 *__restrict__ blk, const int32_t *__restrict__ ent,
+                                                 const int4 *__restrict__ seg, int64_t n, DfConst kc,
+                                                 const float *__restrict__ b, double *__restrict__ out, int direct) {
+    __shared__ float4 s_p[kBlk];
+    __shared__ float2 s_w[kBlk];
+    __shared__ float2 s_tab[64];
+    if (threadIdx.x < 64) s_tab[threadIdx.x] = c_tab[threadIdx.x];
+    const int4 sg = seg[blockIdx.x];
+    const int64_t i = (int64_t)sg.x * kChunk + threadIdx.x;
+    const bool valid = i < n;
+    float4 p = valid ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    double acc = 0.0;
+    for (int e = sg.y; e < sg.z; ++e) {
+        int2 bi = blk[ent[e] & 0x7fffffff];
+        __syncthreads();
+        if ((int)threadIdx.x < bi.y) {
+            s_p[threadIdx.x] = pos[bi.x + threadIdx.x];
+            double xv = x[bi.x + threadIdx.x];
+            float xh = (float)xv;
+            s_w[threadIdx.x] = make_float2(xh, (float)(xv - (double)xh));
+        }
+        __syncthreads();
+        df a = block_terms(p.x, p.y, p.z, s_p, s_w, bi.y, kc, s_tab);
+        acc += (double)a.h + (double)a.l;
+    }
+    if (direct) {
+        if (valid) out[i] = (double)b[i] - acc;
+    } else {
+        out[(int64_t)blockIdx.x * kChunk + threadIdx.x] = acc;
+    }
+}
+
+__global__ void k_reduce_resid_df(const int32_t *__restrict__ tile_seg, const double *__restrict__ part, int64_t n,
+                                  const float *__restrict__ b, double *__restrict__ out) {
+    int64_t t = blockIdx.x;
+    int s0 = tile_seg[t], s1 = tile_seg[t + 1];
+    for (int q = threadIdx.x; q < kChunk; q += blockDim.x) {
+        int64_t i = t * kChunk + q;
+        if (i >= n) continue;
+        double v = 0.0;
+        for (int sidx = s0; sidx < s1; ++sidx) v += part[(int64_t)sidx * kChunk + q];
+        out[i] = (double)b[i] - v;
+    }
+}
+
+inline void split(double v, float &h, float &l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+
+bool g_tab_ready[64] = {false};
+
+void upload_table(int device, cudaStream_t s) {
+    if (device >= 0 && device < 64 && g_tab_ready[device]) return;
+    float2 tab[64];
+    for (int j = 0; j < 64; ++j) split(std::exp2(-j / 64.0), tab[j].x, tab[j].y);
+    RBF_CUDA(cudaMemcpyToSymbolAsync(c_tab, tab, sizeof(tab), 0, cudaMemcpyHostToDevice, s));
+    RBF_CUDA(cudaStreamSynchronize(s));
+    if (device >= 0 && device < 64) g_tab_ready[device] = true;
+}
+
+}  // namespace
+
+void residual_binned_df(rbf_plan *P, const float *bs, const double *xs, double *rs, cudaStream_t s) {
+    upload_table(P->ctx->device, s);
+    const PairList &pl = P->pl;
+    DfConst kc;
+    split(1.4426950408889634 * P->inv2s2_64, kc.Ch, kc.Cl);
+    split(0.6931471805599453, kc.Lh, kc.Ll);
+    if (P->rc2_64 > 0.0) {
+        split(P->rc2_64, kc.Rh, kc.Rl);
+    } else {
+        kc.Rh = INFINITY;
+        kc.Rl = 0.f;
+    }
+    DevBuf<double> part;
+    if (!pl.direct) part.alloc((size_t)pl.nseg * kChunk, s);
+    if (pl.nseg > 0) {
+        k_resid_df<<<(unsigned)pl.nseg, kT, 0, s>>>(P->pos.p, xs, P->blk.p, pl.ent.p, pl.seg.p, P->n, kc, bs,
+                                                    pl.direct ? rs : part.p, pl.direct ? 1 : 0);
+        RBF_LAUNCHED();
+    }
+    if (!pl.direct) {
+        k_reduce_resid_df<<<(unsigned)pl.ntiles, kChunk, 0, s>>>(pl.tile_seg.p, part.p, P->n, bs, rs);
+        RBF_LAUNCHED();
+    }
+}
