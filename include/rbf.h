@@ -285,6 +285,33 @@ rbf_status rbf_count_grid_pairs(rbf_plan *plan, const rbf_grid *g, int64_t *coun
 rbf_status rbf_eval_grid(rbf_ctx *ctx, const float *centers, const double *weights, int64_t n,
                          const rbf_plan_params *pp, const rbf_grid *g, float *f, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free untruncated product (the paper has no counterpart: it is a
+ * service to callers of this library that cannot allocate device memory when
+ * they call in, for example a host that reserves its whole device-memory
+ * budget at start-up and forbids later allocation, or code running inside
+ * another framework's memory pool or a real-time loop).
+ *
+ * y = A z with A_ij = exp(-|c_i - c_j|^2 / (2 sigma^2)) over all pairs (no
+ * cut-off, no plan, no binning), float32 arithmetic, caller order; the same
+ * operator as rbf_matvec on a plan with k = 0.
+ *   centers : n float4 (x, y, z, unused), 16-byte aligned; z, y : n float,
+ *             distinct.  All device memory owned by the caller.
+ *   n       : 1 <= n <= 32768; larger n returns RBF_ERR_UNSUPPORTED with the
+ *             limit in rbf_last_error.
+ * The call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine).  Its scratch is a 4 MiB file-scope device array (32 x 32768 float
+ * partial sums) that every GPU loading the library holds until the process
+ * exits.  The first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's
+ * contents; every entry a call reads is written earlier in the same call, so
+ * nothing needs clearing, but calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race on it and must be serialised by the
+ * caller. */
+rbf_status rbf_matvec_dense_noalloc(rbf_ctx *ctx, const float *centers, int64_t n, float sigma, const float *z,
+                                    float *y, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

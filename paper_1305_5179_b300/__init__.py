@@ -35,6 +35,7 @@ EXPORTS = (
     "rbf_build_centers", "rbf_plan_create", "rbf_plan_destroy", "rbf_plan_get_info", "rbf_plan_export_binning",
     "rbf_matvec", "rbf_count_pairs", "rbf_residual", "rbf_schwarz_setup", "rbf_schwarz_apply",
     "rbf_plan_solve", "rbf_solve", "rbf_plan_eval_grid", "rbf_count_grid_pairs", "rbf_eval_grid",
+    "rbf_matvec_dense_noalloc",
 )
 
 
@@ -123,6 +124,7 @@ def lib() -> ctypes.CDLL:
                        ctypes.POINTER(Report), P], I),
         "rbf_plan_eval_grid": ([P, P, ctypes.POINTER(Grid), P, P], I),
         "rbf_count_grid_pairs": ([P, ctypes.POINTER(Grid), ctypes.POINTER(I64), P], I),
+        "rbf_matvec_dense_noalloc": ([P, P, I64, F, P, P, P], I),
         "rbf_eval_grid": ([P, P, P, I64, ctypes.POINTER(PlanParams), ctypes.POINTER(Grid), P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -380,3 +382,19 @@ def eval_grid(ctx: Context, centers, weights, sigma: float, k: float, lo, hi, di
     ctx.check(lib().rbf_eval_grid(ctx._h, _ptr(centers), _ptr(weights), n, ctypes.byref(pp), ctypes.byref(g), _ptr(f),
                                   _stream(stream)), "rbf_eval_grid")
     return f
+
+
+NOALLOC_MAX_N = 32768
+
+
+def matvec_dense_noalloc(ctx: Context, centers, sigma: float, z, out, stream=None):
+    """Untruncated y = A z through the allocation-free entry point; the caller
+    supplies every buffer (``out`` included), the library allocates nothing."""
+    import torch
+    _req(centers, torch.float32, "centers")
+    n = centers.shape[0]
+    _req(z, torch.float32, "z", n)
+    _req(out, torch.float32, "out", n)
+    ctx.check(lib().rbf_matvec_dense_noalloc(ctx._h, _ptr(centers), n, float(sigma), _ptr(z), _ptr(out),
+                                             _stream(stream)), "rbf_matvec_dense_noalloc")
+    return out
