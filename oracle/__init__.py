@@ -225,7 +225,8 @@ def morton3(qx, qy, qz) -> np.ndarray:
     return (part1by2(qx) | (part1by2(qy) << np.uint64(1)) | (part1by2(qz) << np.uint64(2))).astype(np.uint32)
 
 
-def binning(C32: np.ndarray, sigma: float, k: float, cells_per_cutoff: int = 1, levels: int = 3):
+def binning(C32: np.ndarray, sigma: float, k: float, cells_per_cutoff: int = 1, levels: int = 3,
+            kd_leaf: int = 32, kd_tile: int = 128, kd_chunk: int = 4096):
     """Cell binning of the centres in FP32, as a definition.
 
     * lo = componentwise minimum of the centres; ext = hi - lo (FP32);
@@ -235,7 +236,12 @@ def binning(C32: np.ndarray, sigma: float, k: float, cells_per_cutoff: int = 1, 
     * q_d = floor((c_d - lo_d) * inv) in float32 arithmetic;
     * nbits = max(L, bit length of max_d floor(ext_d * inv)) (must be <= 10);
     * key = Morton interleave of (q_x, q_y, q_z); cell = key >> 3L;
-    * stable sort of the centres by key.
+    * stable sort of the centres by key;
+    * then, inside every cell, consecutive runs of at most ``kd_chunk`` centres
+      (counted from the cell start) are reordered by recursive median splits
+      (``_kd_order``) so that the runs of ``kd_tile`` (target tiles) and
+      ``kd_leaf`` (source blocks) counted from the cell start are compact k-d
+      subtrees (cells stay contiguous; ``keys_sorted`` is then sorted by cell only).
     Returns dict(perm, keys_sorted, cell_of_sorted, cell_start, cell_end (dense
     tables over 2^(3(nbits-L)) cell codes), nbits, inv, lo).
     """
@@ -270,8 +276,44 @@ def binning(C32: np.ndarray, sigma: float, k: float, cells_per_cutoff: int = 1, 
         last[:-1] = cell[1:] != cell[:-1]
         start[cell[first]] = np.nonzero(first)[0]
         end[cell[last]] = np.nonzero(last)[0] + 1
+    if kd_leaf:
+        perm = perm.astype(np.int64)
+        for cs, ce in zip(start, end):
+            if ce <= cs:
+                continue
+            for c0 in range(int(cs), int(ce), kd_chunk):
+                c1 = min(int(ce), c0 + kd_chunk)
+                perm[c0:c1] = perm[c0:c1][_kd_order(c[perm[c0:c1]], kd_leaf, kd_tile)]
+        ks = key[perm]
     return dict(perm=perm.astype(np.int64), keys_sorted=ks, cell_of_sorted=cell,
                 cell_start=start, cell_end=end, nbits=nbits, inv=inv, lo=lo)
+
+
+def _kd_order(P: np.ndarray, leaf: int, tile: int) -> np.ndarray:
+    """Order of the rows of P (float32, m x 3) after recursive splits: a run longer
+    than ``leaf`` is split along the axis of its largest float32 extent (first of
+    x, y, z on ties) so that the left part holds the u * ceil(ceil(len/u)/2)
+    smallest coordinates, u = ``tile`` for runs longer than ``tile`` and ``leaf``
+    otherwise (ties keep the current order); runs of <= leaf stop.  Runs of
+    ``tile`` and ``leaf`` counted from the start are then subtrees."""
+    order = np.arange(len(P))
+    stack = [(0, len(P))]
+    while stack:
+        s, e = stack.pop()
+        m = e - s
+        if m <= leaf:
+            continue
+        q = P[order[s:e]]
+        ext = (q.max(0) - q.min(0)).astype(np.float32)
+        axis = int(np.argmax(ext))                 # first maximum: x before y before z
+        col = q[:, axis] + np.float32(0.0)         # -0 and +0 compare equal
+        sub = np.argsort(col, kind="stable")
+        order[s:e] = order[s:e][sub]
+        u = tile if m > tile else leaf
+        left = u * ((-(-m // u) + 1) // 2)
+        stack.append((s + left, e))
+        stack.append((s, s + left))
+    return order
 
 
 # --------------------------------------------------------------------------

@@ -41,7 +41,8 @@ void eval_grid(rbf_plan *P, const double *weights, const rbf_grid &g, float *f, 
     P->zs.ensure(P->n, s);
     permute_to_binned_f64_to_f32(P, weights, P->zs.p, s);
     GridCache &gc = P->grid;
-    if (gc.pl.direct) RBF_CUDA(cudaMemsetAsync(f, 0, (size_t)total * sizeof(float), s));
+    // bricks with no source block within the cut-off are never visited: clear the field first
+    RBF_CUDA(cudaMemsetAsync(f, 0, (size_t)total * sizeof(float), s));
     matvec_grid_launch(P, gc.pl, P->zs.p, g, gc.bricks, f, s);
 }
 

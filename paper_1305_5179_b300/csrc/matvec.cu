@@ -2,16 +2,18 @@
 // (Sec. III.A, Eq. matrixEntries): the operation GMRES repeats (the paper's MatShell).
 //
 // float32 kernel.  One CTA = one segment of a tile's pair list, 4 warps.  Every
-// warp holds all 128 targets of the tile (4 per lane, as 2 packed pairs for the
-// f32x2 FMA unit) and walks every 4th block of the segment.  For a block with
-// centre c_B and scaled source offsets s_j = (x_j - c_B) * scl (precomputed as
-// (2 s_j, -|s_j|^2)), and a target with d = (x_i - c_B) * scl:
+// warp holds all 128 targets of the tile (4 per lane) and walks every 4th block
+// of the segment; a block's 32 sources are staged in shared memory as
+// structure-of-arrays so that one LDS.128 brings four sources' x (two f32x2
+// operands).  For a block with centre c_B and scaled source offsets
+// s_j = (x_j - c_B) * scl (precomputed as (2 s_j, -|s_j|^2)), and a target with
+// d = (x_i - c_B) * scl:
 //      |x_i - x_j|^2 scl^2 = |d|^2 - 2 d.s_j + |s_j|^2,
 //      phi_ij = 2^(-|d|^2) * 2^(d.(2 s_j) - |s_j|^2)
-// so a pair of targets costs 3 FFMA2 + 2 MUFU.EX2 + 1 FFMA2 per source, and the
+// so two sources cost 3 FFMA2 + 2 MUFU.EX2 + 1 FFMA2 per target, and the
 // per (target, block) factor 2^(-|d|^2) is applied once per block.  Blocks that
-// are not entirely inside the cut-off compare d.(2 s_j) - |s_j|^2 against the
-// per-target threshold |d|^2 - R (R = scaled squared cut-off) before adding.
+// are not entirely inside the cut-off multiply each term by set.gt(arg, thr),
+// thr = |d|^2 - R (R = scaled squared cut-off), before adding.
 // When 2 |d| r_B (r_B the scaled block radius) could exceed 64 for some target,
 // the block takes a shifted form 2^(-|d|^2 + c) * 2^(d.(2 s_j) - |s_j|^2 - c),
 // c = 2 |d| r_B, whose inner exponent is never positive (no overflow).
@@ -27,7 +29,6 @@
 namespace {
 
 constexpr int kWarps = 4;
-constexpr int kPacks = kChunk / 64;   // packed target pairs per lane
 
 typedef unsigned long long f2;      // two float32 in one 64-bit register pair
 
@@ -55,6 +56,7 @@ __device__ __forceinline__ f2 sub2(f2 a, f2 b) {
 
 struct MvArgs {
     const float4 *pos;   // binned positions (targets, sorted mode)
+    const int2 *tiles;   // target tiles (start, count) in sorted mode
     const float4 *src;
     const float *w;      // binned weights
     const int2 *blk;
@@ -63,8 +65,8 @@ struct MvArgs {
     const int4 *seg;
     int64_t n;
     float scl, R;
-    float *out;          // direct: y (binned) / grid f; else partial [seg][kChunk]
-    int direct;
+    float *out;          // y (binned) or grid f, for tiles with a single segment
+    float *partial;      // [seg][kChunk] partial sums of split tiles
     // grid targets: bricks of 8 x 4 x 4 nodes
     float glo[3], gstep[3];
     int gdim[3];
@@ -76,8 +78,9 @@ template <bool kGrid>
 __device__ __forceinline__ bool target_xyz(const MvArgs &a, int64_t t, int q, float &x, float &y, float &z,
                                            int64_t &outidx) {
     if (!kGrid) {
-        int64_t i = t * kChunk + q;
-        if (i < a.n) {
+        const int2 tl = a.tiles[t];
+        int64_t i = (int64_t)tl.x + q;
+        if (q < tl.y) {
             float4 p = a.pos[i];
             x = p.x; y = p.y; z = p.z;
             outidx = i;
@@ -98,38 +101,49 @@ __device__ __forceinline__ bool target_xyz(const MvArgs &a, int64_t t, int q, fl
     }
 }
 
-struct Stage {           // one block of sources, duplicated for the f32x2 operands
-    ulonglong2 A[kBlk];  // (2 s_x, 2 s_x), (2 s_y, 2 s_y)
-    ulonglong2 B[kBlk];  // (2 s_z, 2 s_z), (b, b)
-    f2 W[kBlk];          // (w, w)
+__device__ __forceinline__ float set_gt(float a, float b) {
+    float r;
+    asm("set.gt.f32.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));   // 1.0f if a > b else 0.0f
+    return r;
+}
+
+constexpr int kTpl = kChunk / 32;   // targets per lane
+
+struct Stage {            // one block of sources, structure of arrays (2 s_x, 2 s_y, 2 s_z, b, w)
+    float4 x[kBlk / 4], y[kBlk / 4], z[kBlk / 4], b[kBlk / 4], w[kBlk / 4];
 };
 
-// p[k] = sum_j w_j 2^(arg_kj), arg = d.(2 s_j) - |s_j|^2 (- shift); masked: only arg > thr.
+// p[t] = (sum over even j, sum over odd j) of w_j 2^(arg_tj), arg = d_t.(2 s_j) - |s_j|^2 (- shift_t);
+// masked: only terms with arg > thr_t.  Sources are paired in the f32x2 operands, targets broadcast.
 template <bool kMasked, bool kShift>
-__device__ __forceinline__ void block_sum(const Stage &st, int cnt, const f2 (&dx)[kPacks], const f2 (&dy)[kPacks],
-                                          const f2 (&dz)[kPacks], const f2 (&thr)[kPacks], const f2 (&sh)[kPacks],
-                                          f2 (&p)[kPacks]) {
+__device__ __forceinline__ void block_sum(const Stage &st, int cnt4, const f2 (&DX)[kTpl], const f2 (&DY)[kTpl],
+                                          const f2 (&DZ)[kTpl], const f2 (&TH)[kTpl], const f2 (&SH)[kTpl],
+                                          f2 (&P)[kTpl]) {
 #pragma unroll
-    for (int k = 0; k < kPacks; ++k) p[k] = 0ull;
-#pragma unroll 4
-    for (int j = 0; j < cnt; ++j) {
-        const ulonglong2 A = st.A[j];
-        const ulonglong2 B = st.B[j];
-        const f2 W = st.W[j];
+    for (int t = 0; t < kTpl; ++t) P[t] = 0ull;
+#pragma unroll 1
+    for (int q = 0; q < cnt4; ++q) {            // four sources per step: two f32x2 pairs
+        const float4 X = st.x[q], Y = st.y[q], Z = st.z[q], B = st.b[q], W = st.w[q];
+        const f2 X0 = pk(X.x, X.y), X1 = pk(X.z, X.w), Y0 = pk(Y.x, Y.y), Y1 = pk(Y.z, Y.w);
+        const f2 Z0 = pk(Z.x, Z.y), Z1 = pk(Z.z, Z.w), B0 = pk(B.x, B.y), B1 = pk(B.z, B.w);
+        const f2 W0 = pk(W.x, W.y), W1 = pk(W.z, W.w);
 #pragma unroll
-        for (int k = 0; k < kPacks; ++k) {
-            f2 c0 = kShift ? sub2(B.y, sh[k]) : B.y;
-            f2 arg = fma2(dx[k], A.x, fma2(dy[k], A.y, fma2(dz[k], B.x, c0)));
-            float a0, a1;
-            upk(arg, a0, a1);
-            float e0 = ex2_approx(a0), e1 = ex2_approx(a1);
-            if (kMasked) {
-                float t0, t1;
-                upk(thr[k], t0, t1);
-                e0 = a0 > t0 ? e0 : 0.f;
-                e1 = a1 > t1 ? e1 : 0.f;
+        for (int t = 0; t < kTpl; ++t) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const f2 Xs = h ? X1 : X0, Ys = h ? Y1 : Y0, Zs = h ? Z1 : Z0, Ws = h ? W1 : W0;
+                const f2 c0 = kShift ? sub2(h ? B1 : B0, SH[t]) : (h ? B1 : B0);
+                const f2 arg = fma2(DX[t], Xs, fma2(DY[t], Ys, fma2(DZ[t], Zs, c0)));
+                float a0, a1;
+                upk(arg, a0, a1);
+                f2 E = pk(ex2_approx(a0), ex2_approx(a1));
+                if (kMasked) {
+                    float th, th1;
+                    upk(TH[t], th, th1);
+                    E = mul2(E, pk(set_gt(a0, th), set_gt(a1, th)));
+                }
+                P[t] = fma2(Ws, E, P[t]);
             }
-            p[k] = fma2(W, pk(e0, e1), p[k]);
         }
     }
 }
@@ -141,22 +155,25 @@ __global__ void __launch_bounds__(kWarps * 32) k_matvec_f32(MvArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int4 sg = a.seg[blockIdx.x];
     const int64_t t = sg.x;
-    const f2 scl2 = pk(a.scl, a.scl);
+    const f2 scl2 = pk(a.scl, a.scl), R2 = pk(a.R, a.R);
 
-    f2 tx[kPacks], ty[kPacks], tz[kPacks], acc[kPacks];
+    // targets lane + 32 u, kept duplicated (x, x) for the f32x2 operands
+    f2 TX[kTpl], TY[kTpl], TZ[kTpl];
+    float acc[kTpl];
 #pragma unroll
-    for (int k = 0; k < kPacks; ++k) {
-        float x0, y0, z0, x1, y1, z1;
+    for (int u = 0; u < kTpl; ++u) {
+        float x, y, z;
         int64_t oi;
-        target_xyz<kGrid>(a, t, 64 * k + 2 * lane, x0, y0, z0, oi);
-        target_xyz<kGrid>(a, t, 64 * k + 2 * lane + 1, x1, y1, z1, oi);
-        tx[k] = pk(x0, x1);
-        ty[k] = pk(y0, y1);
-        tz[k] = pk(z0, z1);
-        acc[k] = 0ull;
+        target_xyz<kGrid>(a, t, lane + 32 * u, x, y, z, oi);
+        TX[u] = pk(x, x);
+        TY[u] = pk(y, y);
+        TZ[u] = pk(z, z);
+        acc[u] = 0.f;
     }
     Stage &st = s_st[warp];
-    // prefetch the first block
+    float *sx = reinterpret_cast<float *>(st.x), *sy = reinterpret_cast<float *>(st.y),
+          *sz = reinterpret_cast<float *>(st.z), *sb = reinterpret_cast<float *>(st.b),
+          *swt = reinterpret_cast<float *>(st.w);
     int e = sg.y + warp;
     int ent = 0;
     int2 bi = make_int2(0, 0);
@@ -173,13 +190,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_matvec_f32(MvArgs a) {
     for (; e < sg.z; e += kWarps) {
         const bool masked = ent < 0;
         const int b = ent & 0x7fffffff;
-        const int cnt = (bi.y + 3) & ~3;
+        const int cnt4 = (bi.y + 3) >> 2;
         const float4 c = a.blk_c[b];
-        st.A[lane] = make_ulonglong2(pk(sv.x, sv.x), pk(sv.y, sv.y));
-        st.B[lane] = make_ulonglong2(pk(sv.z, sv.z), pk(sv.w, sv.w));
-        st.W[lane] = pk(wv, wv);
+        sx[lane] = sv.x;
+        sy[lane] = sv.y;
+        sz[lane] = sv.z;
+        sb[lane] = sv.w;
+        swt[lane] = wv;      // zero past the block's count: padded terms vanish
         __syncwarp();
-        // prefetch the next block while this one is computed
         const int en = e + kWarps;
         if (en < sg.z) {
             ent = a.ent[en];
@@ -191,76 +209,77 @@ __global__ void __launch_bounds__(kWarps * 32) k_matvec_f32(MvArgs a) {
                 wv = a.w[bi.x + lane];
             }
         }
-        f2 dx[kPacks], dy[kPacks], dz[kPacks], d2[kPacks], thr[kPacks], sh[kPacks], ea[kPacks], p[kPacks];
+        f2 DX[kTpl], DY[kTpl], DZ[kTpl], D2[kTpl], TH[kTpl], SH[kTpl], P[kTpl];
+        float ea[kTpl];
         bool unsafe = false;
-        const f2 cx = pk(c.x, c.x), cy = pk(c.y, c.y), cz = pk(c.z, c.z), R2 = pk(a.R, a.R);
+        const f2 cx = pk(c.x, c.x), cy = pk(c.y, c.y), cz = pk(c.z, c.z);
 #pragma unroll
-        for (int k = 0; k < kPacks; ++k) {
-            dx[k] = mul2(sub2(tx[k], cx), scl2);
-            dy[k] = mul2(sub2(ty[k], cy), scl2);
-            dz[k] = mul2(sub2(tz[k], cz), scl2);
-            d2[k] = fma2(dx[k], dx[k], fma2(dy[k], dy[k], mul2(dz[k], dz[k])));
-            thr[k] = sub2(d2[k], R2);
+        for (int u = 0; u < kTpl; ++u) {
+            DX[u] = mul2(sub2(TX[u], cx), scl2);
+            DY[u] = mul2(sub2(TY[u], cy), scl2);
+            DZ[u] = mul2(sub2(TZ[u], cz), scl2);
+            D2[u] = fma2(DX[u], DX[u], fma2(DY[u], DY[u], mul2(DZ[u], DZ[u])));
+            TH[u] = sub2(D2[u], R2);
             float q0, q1;
-            upk(d2[k], q0, q1);
-            unsafe |= (q0 > c.w) | (q1 > c.w);
+            upk(D2[u], q0, q1);
+            unsafe |= q0 > c.w;
         }
         unsafe = __any_sync(0xffffffffu, unsafe);
         if (!unsafe) {
 #pragma unroll
-            for (int k = 0; k < kPacks; ++k) {
+            for (int u = 0; u < kTpl; ++u) {
                 float q0, q1;
-                upk(d2[k], q0, q1);
-                ea[k] = pk(ex2_approx(-q0), ex2_approx(-q1));
+                upk(D2[u], q0, q1);
+                ea[u] = ex2_approx(-q0);
             }
             if (masked)
-                block_sum<true, false>(st, cnt, dx, dy, dz, thr, sh, p);
+                block_sum<true, false>(st, cnt4, DX, DY, DZ, TH, SH, P);
             else
-                block_sum<false, false>(st, cnt, dx, dy, dz, thr, sh, p);
+                block_sum<false, false>(st, cnt4, DX, DY, DZ, TH, SH, P);
         } else {
-            // shift c = 2 |d| r_B with r_B = 32 / sqrt(U_B)
+            // shift c = 2 |d| r_B with r_B = 32 / sqrt(U_B): the inner exponent is never positive
             const float rB = c.w < INFINITY ? 32.f * rsqrtf(c.w) : 0.f;
 #pragma unroll
-            for (int k = 0; k < kPacks; ++k) {
+            for (int u = 0; u < kTpl; ++u) {
                 float q0, q1, t0, t1;
-                upk(d2[k], q0, q1);
-                upk(thr[k], t0, t1);
-                float c0 = 2.f * sqrtf(q0) * rB, c1 = 2.f * sqrtf(q1) * rB;
-                sh[k] = pk(c0, c1);
-                ea[k] = pk(ex2_approx(c0 - q0), ex2_approx(c1 - q1));
-                thr[k] = pk(t0 - c0, t1 - c1);
+                upk(D2[u], q0, q1);
+                upk(TH[u], t0, t1);
+                const float cs = 2.f * sqrtf(q0) * rB;
+                SH[u] = pk(cs, cs);
+                ea[u] = ex2_approx(cs - q0);
+                TH[u] = pk(t0 - cs, t0 - cs);
             }
-            block_sum<true, true>(st, cnt, dx, dy, dz, thr, sh, p);
+            block_sum<true, true>(st, cnt4, DX, DY, DZ, TH, SH, P);
         }
 #pragma unroll
-        for (int k = 0; k < kPacks; ++k) acc[k] = fma2(ea[k], p[k], acc[k]);
+        for (int u = 0; u < kTpl; ++u) {
+            float p0, p1;
+            upk(P[u], p0, p1);
+            acc[u] = fmaf(ea[u], p0 + p1, acc[u]);
+        }
         __syncwarp();
     }
 #pragma unroll
-    for (int k = 0; k < kPacks; ++k) {
-        float a0, a1;
-        upk(acc[k], a0, a1);
-        s_red[warp][64 * k + 2 * lane] = a0;
-        s_red[warp][64 * k + 2 * lane + 1] = a1;
-    }
+    for (int u = 0; u < kTpl; ++u) s_red[warp][lane + 32 * u] = acc[u];
     __syncthreads();
     for (int q = threadIdx.x; q < kChunk; q += kWarps * 32) {
         float v = ((s_red[0][q] + s_red[1][q]) + s_red[2][q]) + s_red[3][q];
-        if (a.direct) {
+        if (sg.w) {
             float x, y, z;
             int64_t oi;
             if (target_xyz<kGrid>(a, t, q, x, y, z, oi)) a.out[oi] = v;
         } else {
-            a.out[(int64_t)blockIdx.x * kChunk + q] = v;
+            a.partial[(int64_t)blockIdx.x * kChunk + q] = v;
         }
     }
 }
 
-// Sum the segments of each tile in order.
+// Sum the segments of each split tile in order (single-segment tiles wrote directly).
 template <bool kGrid>
 __global__ void k_reduce_segments(MvArgs a, const int32_t *__restrict__ tile_seg, const float *__restrict__ part) {
     int64_t t = blockIdx.x;
     int s0 = tile_seg[t], s1 = tile_seg[t + 1];
+    if (s1 - s0 < 2) return;
     for (int q = threadIdx.x; q < kChunk; q += blockDim.x) {
         float x, y, z;
         int64_t oi;
@@ -274,16 +293,18 @@ __global__ void k_reduce_segments(MvArgs a, const int32_t *__restrict__ tile_seg
 // ---------------------------------------------------------------- float64
 constexpr int kT64 = kChunk;   // one thread per target
 
-__global__ void __launch_bounds__(kT64) k_resid_f64(const float4 *__restrict__ pos, const double *__restrict__ x,
+__global__ void __launch_bounds__(kT64) k_resid_f64(const float4 *__restrict__ pos, const int2 *__restrict__ tiles,
+                                                   const double *__restrict__ x,
                                                    const int2 *__restrict__ blk, const int32_t *__restrict__ ent,
                                                    const int4 *__restrict__ seg, int64_t n, double rc2, double inv2s2,
-                                                   const float *__restrict__ b, double *__restrict__ out, int direct,
-                                                   unsigned long long *__restrict__ cnt) {
+                                                   const float *__restrict__ b, double *__restrict__ out,
+                                                   double *__restrict__ part, unsigned long long *__restrict__ cnt) {
     __shared__ double s_x[kBlk], s_y[kBlk], s_z[kBlk], s_w[kBlk];
     __shared__ unsigned long long s_cnt[kT64 / 32];
     const int4 sg = seg[blockIdx.x];
-    const int64_t i = (int64_t)sg.x * kChunk + threadIdx.x;
-    const bool valid = i < n;
+    const int2 tl = tiles[sg.x];
+    const int64_t i = (int64_t)tl.x + threadIdx.x;
+    const bool valid = (int)threadIdx.x < tl.y;
     double px = 0, py = 0, pz = 0;
     if (valid) {
         float4 p = pos[i];
@@ -312,10 +333,10 @@ __global__ void __launch_bounds__(kT64) k_resid_f64(const float4 *__restrict__ p
             }
         }
     }
-    if (direct) {
+    if (sg.w) {
         if (valid) out[i] = (double)b[i] - acc;
     } else {
-        out[(int64_t)blockIdx.x * kChunk + threadIdx.x] = acc;
+        part[(int64_t)blockIdx.x * kChunk + threadIdx.x] = acc;
     }
     if (cnt) {
         if (!valid) c = 0;
@@ -330,13 +351,15 @@ __global__ void __launch_bounds__(kT64) k_resid_f64(const float4 *__restrict__ p
     }
 }
 
-__global__ void k_reduce_resid(const int32_t *__restrict__ tile_seg, const double *__restrict__ part, int64_t n,
-                               const float *__restrict__ b, double *__restrict__ out) {
+__global__ void k_reduce_resid(const int32_t *__restrict__ tile_seg, const int2 *__restrict__ tiles,
+                               const double *__restrict__ part, const float *__restrict__ b, double *__restrict__ out) {
     int64_t t = blockIdx.x;
     int s0 = tile_seg[t], s1 = tile_seg[t + 1];
+    if (s1 - s0 < 2) return;
+    const int2 tl = tiles[t];
     for (int q = threadIdx.x; q < kChunk; q += blockDim.x) {
-        int64_t i = t * kChunk + q;
-        if (i >= n) continue;
+        int64_t i = (int64_t)tl.x + q;
+        if (q >= tl.y) continue;
         double v = 0.0;
         for (int sidx = s0; sidx < s1; ++sidx) v += part[(int64_t)sidx * kChunk + q];
         out[i] = (double)b[i] - v;
@@ -346,6 +369,7 @@ __global__ void k_reduce_resid(const int32_t *__restrict__ tile_seg, const doubl
 MvArgs base_args(const rbf_plan *P, const PairList &pl, const float *w, float *out, float *partial) {
     MvArgs a{};
     a.pos = P->pos.p;
+    a.tiles = P->tiles.p;
     a.src = P->src.p;
     a.w = w;
     a.blk = P->blk.p;
@@ -355,8 +379,8 @@ MvArgs base_args(const rbf_plan *P, const PairList &pl, const float *w, float *o
     a.n = P->n;
     a.scl = P->scl;
     a.R = P->R;
-    a.direct = pl.direct ? 1 : 0;
-    a.out = pl.direct ? out : partial;
+    a.out = out;
+    a.partial = partial;
     return a;
 }
 
@@ -364,15 +388,14 @@ MvArgs base_args(const rbf_plan *P, const PairList &pl, const float *w, float *o
 
 void matvec_binned(rbf_plan *P, const float *zs, float *ys, cudaStream_t s) {
     const PairList &pl = P->pl;
-    if (!pl.direct) P->partial.ensure((size_t)pl.nseg * kChunk, s);
+    if (pl.any_split) P->partial.ensure((size_t)pl.nseg * kChunk, s);
     MvArgs a = base_args(P, pl, zs, ys, P->partial.p);
     if (pl.nseg > 0) {
         k_matvec_f32<false><<<(unsigned)pl.nseg, kWarps * 32, 0, s>>>(a);
         RBF_LAUNCHED();
     }
-    if (!pl.direct) {
-        a.out = ys;
-        k_reduce_segments<false><<<(unsigned)pl.ntiles, 256, 0, s>>>(a, pl.tile_seg.p, P->partial.p);
+    if (pl.any_split) {
+        k_reduce_segments<false><<<(unsigned)pl.ntiles, kChunk, 0, s>>>(a, pl.tile_seg.p, P->partial.p);
         RBF_LAUNCHED();
     }
 }
@@ -381,15 +404,14 @@ void residual_binned_f64(rbf_plan *P, const float *bs, const double *xs, double 
                          cudaStream_t s) {
     const PairList &pl = P->pl;
     DevBuf<double> part;
-    if (!pl.direct) part.alloc((size_t)pl.nseg * kChunk, s);
+    if (pl.any_split) part.alloc((size_t)pl.nseg * kChunk, s);
     if (pl.nseg > 0) {
-        k_resid_f64<<<(unsigned)pl.nseg, kT64, 0, s>>>(P->pos.p, xs, P->blk.p, pl.ent.p, pl.seg.p, P->n, P->rc2_64,
-                                                       P->inv2s2_64, bs, pl.direct ? rs : part.p, pl.direct ? 1 : 0,
-                                                       cnt);
+        k_resid_f64<<<(unsigned)pl.nseg, kT64, 0, s>>>(P->pos.p, P->tiles.p, xs, P->blk.p, pl.ent.p, pl.seg.p, P->n,
+                                                       P->rc2_64, P->inv2s2_64, bs, rs, part.p, cnt);
         RBF_LAUNCHED();
     }
-    if (!pl.direct) {
-        k_reduce_resid<<<(unsigned)pl.ntiles, 256, 0, s>>>(pl.tile_seg.p, part.p, P->n, bs, rs);
+    if (pl.any_split) {
+        k_reduce_resid<<<(unsigned)pl.ntiles, kChunk, 0, s>>>(pl.tile_seg.p, P->tiles.p, part.p, bs, rs);
         RBF_LAUNCHED();
     }
 }
@@ -397,7 +419,7 @@ void residual_binned_f64(rbf_plan *P, const float *bs, const double *xs, double 
 // Grid evaluation shares the float32 product kernel with grid-generated targets.
 void matvec_grid_launch(rbf_plan *P, const PairList &pl, const float *ws, const rbf_grid &g, const int64_t bricks[3],
                         float *f, cudaStream_t s) {
-    if (!pl.direct) P->partial.ensure((size_t)pl.nseg * kChunk, s);
+    if (pl.any_split) P->partial.ensure((size_t)pl.nseg * kChunk, s);
     MvArgs a = base_args(P, pl, ws, f, P->partial.p);
     for (int d = 0; d < 3; ++d) {
         a.glo[d] = g.lo[d];
@@ -409,9 +431,8 @@ void matvec_grid_launch(rbf_plan *P, const PairList &pl, const float *ws, const 
         k_matvec_f32<true><<<(unsigned)pl.nseg, kWarps * 32, 0, s>>>(a);
         RBF_LAUNCHED();
     }
-    if (!pl.direct) {
-        a.out = f;
-        k_reduce_segments<true><<<(unsigned)pl.ntiles, 256, 0, s>>>(a, pl.tile_seg.p, P->partial.p);
+    if (pl.any_split) {
+        k_reduce_segments<true><<<(unsigned)pl.ntiles, kChunk, 0, s>>>(a, pl.tile_seg.p, P->partial.p);
         RBF_LAUNCHED();
     }
 }
@@ -423,14 +444,16 @@ namespace {
 // float64 only within 1e-5 (relative) of the cut-off, where float32 rounding of
 // the squared distance (< 3e-7 relative) could flip it; so the count equals the
 // float64 decision.
-__global__ void __launch_bounds__(kT64) k_count_pairs(const float4 *__restrict__ pos, const int2 *__restrict__ blk,
+__global__ void __launch_bounds__(kT64) k_count_pairs(const float4 *__restrict__ pos, const int2 *__restrict__ tiles,
+                                                     const int2 *__restrict__ blk,
                                                      const int32_t *__restrict__ ent, const int4 *__restrict__ seg,
                                                      int64_t n, double rc2, unsigned long long *__restrict__ cnt) {
     __shared__ float4 s_p[kBlk];
     __shared__ unsigned long long s_cnt[kT64 / 32];
     const int4 sg = seg[blockIdx.x];
-    const int64_t i = (int64_t)sg.x * kChunk + threadIdx.x;
-    const bool valid = i < n;
+    const int2 tl = tiles[sg.x];
+    const int64_t i = (int64_t)tl.x + threadIdx.x;
+    const bool valid = (int)threadIdx.x < tl.y;
     float4 p = valid ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float rc2f = (float)rc2, lo = rc2f * (1.f - 1e-5f), hi = rc2f * (1.f + 1e-5f);
     unsigned long long c = 0;
@@ -540,7 +563,7 @@ int64_t count_pairs(rbf_plan *P, cudaStream_t s) {
     c.alloc(1, s);
     c.zero(s);
     if (P->pl.nseg > 0) {
-        k_count_pairs<<<(unsigned)P->pl.nseg, kT64, 0, s>>>(P->pos.p, P->blk.p, P->pl.ent.p, P->pl.seg.p, P->n,
+        k_count_pairs<<<(unsigned)P->pl.nseg, kT64, 0, s>>>(P->pos.p, P->tiles.p, P->blk.p, P->pl.ent.p, P->pl.seg.p, P->n,
                                                            P->rc2_64, c.p);
         RBF_LAUNCHED();
     }

@@ -55,20 +55,179 @@ __global__ void k_gather_pos(const float4 *__restrict__ C, const int32_t *__rest
     pos[i] = make_float4(c.x, c.y, c.z, 0.f);
 }
 
-__global__ void k_cell_nblocks(const int32_t *__restrict__ start, const int32_t *__restrict__ end, int64_t ncells,
-                               int32_t *__restrict__ nb) {
+// Runs of at most `len` consecutive binned centres counted from each cell start:
+// source blocks (32), target tiles (128) and k-d chunks (4096) are such runs.
+__global__ void k_cell_nruns(const int32_t *__restrict__ start, const int32_t *__restrict__ end, int64_t ncells,
+                             int len, int32_t *__restrict__ nr) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
     int m = end[c] - start[c];
-    nb[c] = (m + kBlk - 1) / kBlk;
+    nr[c] = (m + len - 1) / len;
 }
 
-__global__ void k_fill_blocks(const int32_t *__restrict__ start, const int32_t *__restrict__ end,
-                              const int32_t *__restrict__ cell_blk, int64_t ncells, int2 *__restrict__ blk) {
+__global__ void k_fill_runs(const int32_t *__restrict__ start, const int32_t *__restrict__ end,
+                            const int32_t *__restrict__ cell_run, int64_t ncells, int len, int2 *__restrict__ run) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
-    int s = start[c], m = end[c] - s, b0 = cell_blk[c];
-    for (int k = 0; k * kBlk < m; ++k) blk[b0 + k] = make_int2(s + k * kBlk, min(kBlk, m - k * kBlk));
+    int s = start[c], m = end[c] - s, r0 = cell_run[c];
+    for (int k = 0; k * len < m; ++k) run[r0 + k] = make_int2(s + k * len, min(len, m - k * len));
+}
+
+// k-d refinement of one run of <= kKdMax centres of a cell: recursive splits
+// along the axis of the largest float32 extent (first of x, y, z on ties); the
+// left part takes the u * ceil(ceil(len/u)/2) smallest coordinates (u = kChunk
+// above kChunk centres, kBlk below; ties keep the current order), so runs of
+// kChunk and kBlk counted from the run start are subtrees.  Every level is one
+// bitonic sort of (segment, coordinate, position) keys in shared memory.
+constexpr int kKdMax = 4096;
+constexpr int kKdThreads = 512;
+constexpr int kKdMaxSeg = kKdMax / kBlk + 8;
+
+__device__ __forceinline__ uint32_t ordered_bits(float v) {
+    uint32_t u = __float_as_uint(v + 0.0f);   // -0 -> +0
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__global__ void __launch_bounds__(kKdThreads) k_kd_refine(const int2 *__restrict__ chunks, float4 *__restrict__ pos,
+                                                          int32_t *__restrict__ perm, uint32_t *__restrict__ keys) {
+    extern __shared__ unsigned long long kd_sm[];
+    unsigned long long *skey = kd_sm;                         // kKdMax
+    float *sx = reinterpret_cast<float *>(skey + kKdMax);     // kKdMax each
+    float *sy = sx + kKdMax;
+    float *sz = sy + kKdMax;
+    uint16_t *ord = reinterpret_cast<uint16_t *>(sz + kKdMax);
+    uint16_t *ord2 = ord + kKdMax;
+    __shared__ int2 seg[kKdMaxSeg];
+    __shared__ int segaxis[kKdMaxSeg];
+    __shared__ int nseg, busy;
+
+    const int2 ch = chunks[blockIdx.x];
+    const int s0 = ch.x, m = ch.y;
+    if (m <= kBlk) return;   // a single leaf: nothing to reorder
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = kKdThreads / 32;
+    for (int i = tid; i < m; i += kKdThreads) {
+        float4 p = pos[s0 + i];
+        sx[i] = p.x;
+        sy[i] = p.y;
+        sz[i] = p.z;
+        ord[i] = (uint16_t)i;
+    }
+    int M = 1;
+    while (M < m) M <<= 1;
+    if (tid == 0) {
+        nseg = 1;
+        seg[0] = make_int2(0, m);
+    }
+    __syncthreads();
+    for (int level = 0; level < 32; ++level) {
+        if (tid == 0) {
+            int b = 0;
+            for (int g = 0; g < nseg; ++g) b |= seg[g].y > kBlk;
+            busy = b;
+        }
+        __syncthreads();
+        if (!busy) break;
+        // axis of every segment that is still split
+        for (int g = warp; g < nseg; g += nwarp) {
+            int2 sgm = seg[g];
+            int ax = -1;
+            if (sgm.y > kBlk) {
+                float mn0 = INFINITY, mn1 = INFINITY, mn2 = INFINITY, mx0 = -INFINITY, mx1 = -INFINITY, mx2 = -INFINITY;
+                for (int i = sgm.x + lane; i < sgm.x + sgm.y; i += 32) {
+                    int o = ord[i];
+                    mn0 = fminf(mn0, sx[o]); mx0 = fmaxf(mx0, sx[o]);
+                    mn1 = fminf(mn1, sy[o]); mx1 = fmaxf(mx1, sy[o]);
+                    mn2 = fminf(mn2, sz[o]); mx2 = fmaxf(mx2, sz[o]);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    mn0 = fminf(mn0, __shfl_xor_sync(0xffffffffu, mn0, o));
+                    mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
+                    mn1 = fminf(mn1, __shfl_xor_sync(0xffffffffu, mn1, o));
+                    mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
+                    mn2 = fminf(mn2, __shfl_xor_sync(0xffffffffu, mn2, o));
+                    mx2 = fmaxf(mx2, __shfl_xor_sync(0xffffffffu, mx2, o));
+                }
+                float e0 = __fsub_rn(mx0, mn0), e1 = __fsub_rn(mx1, mn1), e2 = __fsub_rn(mx2, mn2);
+                ax = 0;
+                float best = e0;
+                if (e1 > best) { ax = 1; best = e1; }
+                if (e2 > best) ax = 2;
+            }
+            if (lane == 0) segaxis[g] = ax;
+        }
+        __syncthreads();
+        // keys (segment, coordinate, position); positions past m sort last
+        for (int g = warp; g < nseg; g += nwarp) {
+            int2 sgm = seg[g];
+            int ax = segaxis[g];
+            const float *col = ax == 0 ? sx : (ax == 1 ? sy : sz);
+            for (int i = sgm.x + lane; i < sgm.x + sgm.y; i += 32) {
+                unsigned long long cb = ax >= 0 ? ordered_bits(col[ord[i]]) : 0u;
+                skey[i] = ((unsigned long long)g << 44) | (cb << 12) | (unsigned long long)i;
+            }
+        }
+        for (int i = m + tid; i < M; i += kKdThreads) skey[i] = ~0ull;
+        __syncthreads();
+        for (int k = 2; k <= M; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = tid; i < M; i += kKdThreads) {
+                    int ixj = i ^ j;
+                    if (ixj > i) {
+                        unsigned long long a = skey[i], b = skey[ixj];
+                        bool up = (i & k) == 0;
+                        if ((a > b) == up) {
+                            skey[i] = b;
+                            skey[ixj] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = tid; i < m; i += kKdThreads) ord2[i] = ord[skey[i] & 0xfffu];
+        __syncthreads();
+        for (int i = tid; i < m; i += kKdThreads) ord[i] = ord2[i];
+        if (tid == 0) {
+            int2 tmp[kKdMaxSeg];
+            int nn = 0;
+            for (int g = 0; g < nseg; ++g) {
+                int2 sgm = seg[g];
+                if (sgm.y > kBlk) {
+                    int u = sgm.y > kChunk ? kChunk : kBlk;
+                    int left = u * ((((sgm.y + u - 1) / u) + 1) / 2);
+                    tmp[nn++] = make_int2(sgm.x, left);
+                    tmp[nn++] = make_int2(sgm.x + left, sgm.y - left);
+                } else {
+                    tmp[nn++] = sgm;
+                }
+            }
+            for (int g = 0; g < nn; ++g) seg[g] = tmp[g];
+            nseg = nn;
+        }
+        __syncthreads();
+    }
+    // apply the order to the binned arrays (read everything, then write)
+    float4 pv[kKdMax / kKdThreads];
+    int32_t iv[kKdMax / kKdThreads];
+    uint32_t kv[kKdMax / kKdThreads];
+    for (int r = 0; r < kKdMax / kKdThreads; ++r) {
+        int i = tid + r * kKdThreads;
+        if (i < m) {
+            int o = ord[i];
+            pv[r] = pos[s0 + o];
+            iv[r] = perm[s0 + o];
+            kv[r] = keys[s0 + o];
+        }
+    }
+    __syncthreads();
+    for (int r = 0; r < kKdMax / kKdThreads; ++r) {
+        int i = tid + r * kKdThreads;
+        if (i < m) {
+            pos[s0 + i] = pv[r];
+            perm[s0 + i] = iv[r];
+            keys[s0 + i] = kv[r];
+        }
+    }
 }
 
 // One warp per block: box, centre, overflow guard, and the scaled source offsets.
@@ -103,21 +262,18 @@ __global__ void k_block_geom(const float4 *__restrict__ pos, const int2 *__restr
     }
 }
 
-// One warp per tile of kChunk consecutive binned centres: its box.
-__global__ void k_chunk_boxes(const float4 *__restrict__ pos, int64_t n, int64_t nchk, float4 *__restrict__ lo,
-                              float4 *__restrict__ hi) {
+// One warp per target tile (a run of <= kChunk binned centres): its box.
+__global__ void k_chunk_boxes(const float4 *__restrict__ pos, const int2 *__restrict__ tiles, int64_t nchk,
+                              float4 *__restrict__ lo, float4 *__restrict__ hi) {
     int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (t >= nchk) return;
-    int64_t base = t * kChunk;
+    const int2 tl = tiles[t];
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int r = 0; r < kChunk / 32; ++r) {
-        int64_t i = base + lane + 32 * r;
-        if (i < n) {
-            float4 p = pos[i];
-            mn[0] = fminf(mn[0], p.x); mn[1] = fminf(mn[1], p.y); mn[2] = fminf(mn[2], p.z);
-            mx[0] = fmaxf(mx[0], p.x); mx[1] = fmaxf(mx[1], p.y); mx[2] = fmaxf(mx[2], p.z);
-        }
+    for (int q = lane; q < tl.y; q += 32) {
+        float4 p = pos[tl.x + q];
+        mn[0] = fminf(mn[0], p.x); mn[1] = fminf(mn[1], p.y); mn[2] = fminf(mn[2], p.z);
+        mx[0] = fmaxf(mx[0], p.x); mx[1] = fmaxf(mx[1], p.y); mx[2] = fmaxf(mx[2], p.z);
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d)
@@ -222,7 +378,7 @@ __global__ void k_seg_count(const int32_t *__restrict__ off, int64_t ntiles, int
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
     int64_t c = off[t + 1] - off[t];
-    ns[t] = c > 0 ? (int32_t)((c - 1) / seglen + 1) : 0;
+    ns[t] = c > 0 ? (int32_t)((c - 1) / seglen + 1) : 0;   // empty tiles have no segment
 }
 
 __global__ void k_seg_fill(const int32_t *__restrict__ off, const int32_t *__restrict__ tseg, int64_t ntiles,
@@ -231,9 +387,10 @@ __global__ void k_seg_fill(const int32_t *__restrict__ off, const int32_t *__res
     if (t >= ntiles) return;
     int64_t e0 = off[t], e1 = off[t + 1];
     int s0 = tseg[t];
+    int single = (tseg[t + 1] - s0) == 1;
     for (int64_t k = 0; e0 + k * seglen < e1; ++k) {
         int64_t a = e0 + k * seglen, b = a + seglen < e1 ? a + seglen : e1;
-        seg[s0 + k] = make_int4((int)t, (int)a, (int)b, 0);
+        seg[s0 + k] = make_int4((int)t, (int)a, (int)b, single);
     }
 }
 
@@ -306,12 +463,15 @@ void build_pairlist(rbf_plan *P, const float4 *tlo, const float4 *thi, int64_t n
                                          pl.ent.p);
     RBF_LAUNCHED();
 
-    // segments: enough independent work items to fill every SM several times
+    // segments: enough independent work items to fill every SM several times, and no
+    // segment much longer than the average tile (a tile whose box straddles a jump of
+    // the Morton order can collect many blocks; splitting it keeps the SMs balanced)
     int64_t want = 8LL * P->ctx->num_sms;
-    int seglen = INT_MAX;
-    if (ntiles < want && len > 0) seglen = (int)std::max<int64_t>(8, ceil_div(len, want));
+    int64_t seglen = len > 0 ? std::max<int64_t>(64, 2 * ceil_div(len, std::max<int64_t>(ntiles, 1))) : 1;
+    if (ntiles < want && len > 0) seglen = std::min<int64_t>(seglen, std::max<int64_t>(8, ceil_div(len, want)));
+    pl.seglen = (int)std::min<int64_t>(seglen, INT_MAX / 2);
     pl.tile_seg.alloc(ntiles + 1, s);
-    k_seg_count<<<grid_for(ntiles), kThreads, 0, s>>>(pl.off.p, ntiles, seglen, cnt.p);
+    k_seg_count<<<grid_for(ntiles), kThreads, 0, s>>>(pl.off.p, ntiles, pl.seglen, cnt.p);
     RBF_LAUNCHED();
     scan_exclusive_i32(cnt.p, pl.tile_seg.p, ntiles, s);
     int32_t nseg = 0;
@@ -319,9 +479,38 @@ void build_pairlist(rbf_plan *P, const float4 *tlo, const float4 *thi, int64_t n
     RBF_CUDA(cudaStreamSynchronize(s));
     pl.nseg = nseg;
     pl.seg.alloc(std::max<int64_t>(nseg, 1), s);
-    k_seg_fill<<<grid_for(ntiles), kThreads, 0, s>>>(pl.off.p, pl.tile_seg.p, ntiles, seglen, pl.seg.p);
+    k_seg_fill<<<grid_for(ntiles), kThreads, 0, s>>>(pl.off.p, pl.tile_seg.p, ntiles, pl.seglen, pl.seg.p);
     RBF_LAUNCHED();
-    pl.direct = seglen == INT_MAX;
+    int64_t nonempty = 0;
+    {
+        std::vector<int32_t> o(2);
+        // a split exists iff there are more segments than non-empty tiles; count the latter on the host
+        std::vector<int32_t> offs(ntiles + 1);
+        RBF_CUDA(cudaMemcpyAsync(offs.data(), pl.off.p, (ntiles + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        RBF_CUDA(cudaStreamSynchronize(s));
+        for (int64_t t = 0; t < ntiles; ++t) nonempty += offs[t + 1] > offs[t];
+    }
+    pl.any_split = nseg > nonempty;
+}
+
+// Runs of <= len centres per cell -> run list (and the per-cell run offsets if asked).
+static int64_t build_runs(rbf_plan *P, int len, PBuf<int2> &runs, PBuf<int32_t> *cell_run_out, cudaStream_t s) {
+    DevBuf<int32_t> nr;
+    nr.alloc(P->ncells, s);
+    k_cell_nruns<<<grid_for(P->ncells), kThreads, 0, s>>>(P->cell_start.p, P->cell_end.p, P->ncells, len, nr.p);
+    RBF_LAUNCHED();
+    PBuf<int32_t> local;
+    PBuf<int32_t> &cr = cell_run_out ? *cell_run_out : local;
+    cr.alloc(P->ncells + 1, s);
+    scan_exclusive_i32(nr.p, cr.p, P->ncells, s);
+    int32_t total = 0;
+    RBF_CUDA(cudaMemcpyAsync(&total, cr.p + P->ncells, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(cudaStreamSynchronize(s));
+    runs.alloc(std::max<int32_t>(total, 1), s);
+    k_fill_runs<<<grid_for(P->ncells), kThreads, 0, s>>>(P->cell_start.p, P->cell_end.p, cr.p, P->ncells, len, runs.p);
+    RBF_LAUNCHED();
+    if (!cell_run_out) RBF_CUDA(cudaStreamSynchronize(s));   // `local` is freed on return
+    return total;
 }
 
 void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s) {
@@ -383,34 +572,32 @@ void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s) {
     k_gather_pos<<<grid_for(n), kThreads, 0, s>>>(centers, P->perm.p, n, P->pos.p);
     RBF_LAUNCHED();
 
-    // 3: source blocks per cell
-    DevBuf<int32_t> nb;
-    nb.alloc(P->ncells, s);
-    k_cell_nblocks<<<grid_for(P->ncells), kThreads, 0, s>>>(P->cell_start.p, P->cell_end.p, P->ncells, nb.p);
-    RBF_LAUNCHED();
-    P->cell_blk.alloc(P->ncells + 1, s);
-    scan_exclusive_i32(nb.p, P->cell_blk.p, P->ncells, s);
-    int32_t nblk = 0;
-    RBF_CUDA(cudaMemcpyAsync(&nblk, P->cell_blk.p + P->ncells, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    RBF_CUDA(cudaStreamSynchronize(s));
-    P->nblk = nblk;
-    P->blk.alloc(nblk, s);
-    k_fill_blocks<<<grid_for(P->ncells), kThreads, 0, s>>>(P->cell_start.p, P->cell_end.p, P->cell_blk.p, P->ncells,
-                                                          P->blk.p);
-    RBF_LAUNCHED();
+    // 3: k-d refinement inside each cell (runs of <= kKdMax), then source blocks,
+    //    target tiles and their boxes
+    PBuf<int2> chunks;
+    int64_t nkd = build_runs(P, kKdMax, chunks, nullptr, s);
+    if (nkd > 0) {
+        size_t smem = (size_t)kKdMax * (8 + 4 * 3 + 2 * 2);
+        RBF_CUDA(cudaFuncSetAttribute(k_kd_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_kd_refine<<<(unsigned)nkd, kKdThreads, smem, s>>>(chunks.p, P->pos.p, P->perm.p, P->keys.p);
+        RBF_LAUNCHED();
+    }
+    P->nblk = build_runs(P, kBlk, P->blk, &P->cell_blk, s);
+    const int64_t nblk = P->nblk;
     P->blk_c.alloc(nblk, s);
     P->blk_lo.alloc(nblk, s);
     P->blk_hi.alloc(nblk, s);
     P->src.alloc(n, s);
-    k_block_geom<<<grid_for((int64_t)nblk * 32), kThreads, 0, s>>>(P->pos.p, P->blk.p, nblk, P->scl, P->blk_c.p,
-                                                                   P->blk_lo.p, P->blk_hi.p, P->src.p);
+    k_block_geom<<<grid_for(nblk * 32), kThreads, 0, s>>>(P->pos.p, P->blk.p, nblk, P->scl, P->blk_c.p, P->blk_lo.p,
+                                                          P->blk_hi.p, P->src.p);
     RBF_LAUNCHED();
 
     // 4: target tiles and the pair list
-    P->nchk = ceil_div(n, kChunk);
+    P->nchk = build_runs(P, kChunk, P->tiles, nullptr, s);
     P->chk_lo.alloc(P->nchk, s);
     P->chk_hi.alloc(P->nchk, s);
-    k_chunk_boxes<<<grid_for(P->nchk * 32), kThreads, 0, s>>>(P->pos.p, n, P->nchk, P->chk_lo.p, P->chk_hi.p);
+    k_chunk_boxes<<<grid_for(P->nchk * 32), kThreads, 0, s>>>(P->pos.p, P->tiles.p, P->nchk, P->chk_lo.p,
+                                                              P->chk_hi.p);
     RBF_LAUNCHED();
     build_pairlist(P, P->chk_lo.p, P->chk_hi.p, P->nchk, P->pl, s);
 }

@@ -7,14 +7,18 @@ constexpr int kChunk = 128;   // targets per tile (4 per lane of a warp, as 2 pa
 
 // A list of (target tile, source block) work: entries of a tile are contiguous,
 // split into segments (one CTA each) when there are too few tiles to fill the GPU.
+// A tile whose list is longer than the segment length is split over several
+// CTAs (segments); a tile with a single segment writes its outputs directly,
+// the others write partial sums that a second kernel adds in segment order.
 struct PairList {
     int64_t ntiles = 0;
     int64_t len = 0;
     int64_t nseg = 0;
-    bool direct = true;            // one segment per tile: write outputs directly
+    int seglen = 0;
+    bool any_split = false;      // some tile has more than one segment
     PBuf<int32_t> off;           // ntiles + 1
     PBuf<int32_t> ent;           // len; bit 31 set = pair-wise cut-off test needed
-    PBuf<int4> seg;              // (tile, e0, e1, unused)
+    PBuf<int4> seg;              // (tile, e0, e1, 1 if the tile has this one segment only)
     PBuf<int32_t> tile_seg;      // ntiles + 1: segments of tile t are [tile_seg[t], tile_seg[t+1])
 };
 
@@ -60,6 +64,7 @@ struct rbf_plan {
     PBuf<float4> blk_c;        // block centre (x, y, z) and overflow guard (32 / scaled radius)^2
     PBuf<float4> blk_lo, blk_hi;
     PBuf<float4> src;          // per binned source: (2 s_x, 2 s_y, 2 s_z, -|s|^2), s = scaled offset to its block centre
+    PBuf<int2> tiles;            // target tiles: (start, count), runs of <= kChunk per cell
     PBuf<float4> chk_lo, chk_hi;
     PairList pl;
 

@@ -107,17 +107,20 @@ __device__ __forceinline__ df block_terms(float px, float py, float pz, const fl
     return acc;
 }
 
-__global__ void __launch_bounds__(kT) k_resid_df(const float4 *__restrict__ pos, const double *__restrict__ x,
+__global__ void __launch_bounds__(kT) k_resid_df(const float4 *__restrict__ pos, const int2 *__restrict__ tiles,
+                                                 const double *__restrict__ x,
                                                  const int2 *__restrict__ blk, const int32_t *__restrict__ ent,
                                                  const int4 *__restrict__ seg, int64_t n, DfConst kc,
-                                                 const float *__restrict__ b, double *__restrict__ out, int direct) {
+                                                 const float *__restrict__ b, double *__restrict__ out,
+                                                 double *__restrict__ part) {
     __shared__ float4 s_p[kBlk];
     __shared__ float2 s_w[kBlk];
     __shared__ float2 s_tab[64];
     if (threadIdx.x < 64) s_tab[threadIdx.x] = c_tab[threadIdx.x];
     const int4 sg = seg[blockIdx.x];
-    const int64_t i = (int64_t)sg.x * kChunk + threadIdx.x;
-    const bool valid = i < n;
+    const int2 tl = tiles[sg.x];
+    const int64_t i = (int64_t)tl.x + threadIdx.x;
+    const bool valid = (int)threadIdx.x < tl.y;
     float4 p = valid ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     double acc = 0.0;
     for (int e = sg.y; e < sg.z; ++e) {
@@ -133,20 +136,23 @@ __global__ void __launch_bounds__(kT) k_resid_df(const float4 *__restrict__ pos,
         df a = block_terms(p.x, p.y, p.z, s_p, s_w, bi.y, kc, s_tab);
         acc += (double)a.h + (double)a.l;
     }
-    if (direct) {
+    if (sg.w) {
         if (valid) out[i] = (double)b[i] - acc;
     } else {
-        out[(int64_t)blockIdx.x * kChunk + threadIdx.x] = acc;
+        part[(int64_t)blockIdx.x * kChunk + threadIdx.x] = acc;
     }
 }
 
-__global__ void k_reduce_resid_df(const int32_t *__restrict__ tile_seg, const double *__restrict__ part, int64_t n,
-                                  const float *__restrict__ b, double *__restrict__ out) {
+__global__ void k_reduce_resid_df(const int32_t *__restrict__ tile_seg, const int2 *__restrict__ tiles,
+                                  const double *__restrict__ part, const float *__restrict__ b,
+                                  double *__restrict__ out) {
     int64_t t = blockIdx.x;
     int s0 = tile_seg[t], s1 = tile_seg[t + 1];
+    if (s1 - s0 < 2) return;
+    const int2 tl = tiles[t];
     for (int q = threadIdx.x; q < kChunk; q += blockDim.x) {
-        int64_t i = t * kChunk + q;
-        if (i >= n) continue;
+        int64_t i = (int64_t)tl.x + q;
+        if (q >= tl.y) continue;
         double v = 0.0;
         for (int sidx = s0; sidx < s1; ++sidx) v += part[(int64_t)sidx * kChunk + q];
         out[i] = (double)b[i] - v;
@@ -184,14 +190,14 @@ void residual_binned_df(rbf_plan *P, const float *bs, const double *xs, double *
         kc.Rl = 0.f;
     }
     DevBuf<double> part;
-    if (!pl.direct) part.alloc((size_t)pl.nseg * kChunk, s);
+    if (pl.any_split) part.alloc((size_t)pl.nseg * kChunk, s);
     if (pl.nseg > 0) {
-        k_resid_df<<<(unsigned)pl.nseg, kT, 0, s>>>(P->pos.p, xs, P->blk.p, pl.ent.p, pl.seg.p, P->n, kc, bs,
-                                                    pl.direct ? rs : part.p, pl.direct ? 1 : 0);
+        k_resid_df<<<(unsigned)pl.nseg, kT, 0, s>>>(P->pos.p, P->tiles.p, xs, P->blk.p, pl.ent.p, pl.seg.p, P->n, kc,
+                                                    bs, rs, part.p);
         RBF_LAUNCHED();
     }
-    if (!pl.direct) {
-        k_reduce_resid_df<<<(unsigned)pl.ntiles, kChunk, 0, s>>>(pl.tile_seg.p, part.p, P->n, bs, rs);
+    if (pl.any_split) {
+        k_reduce_resid_df<<<(unsigned)pl.ntiles, kChunk, 0, s>>>(pl.tile_seg.p, P->tiles.p, part.p, bs, rs);
         RBF_LAUNCHED();
     }
 }

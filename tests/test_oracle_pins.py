@@ -240,7 +240,7 @@ def test_binning_permutation_sorted_stable():
     rng = np.random.default_rng(4)
     C = rng.uniform(-1, 2, (5000, 3)).astype(np.float32)
     C[100:110] = C[7]                          # duplicates: equal keys
-    B = oracle.binning(C, 0.05, 3.0)
+    B = oracle.binning(C, 0.05, 3.0, kd_leaf=0)      # the sort alone, no k-d refinement
     perm = B["perm"]
     assert np.array_equal(np.sort(perm), np.arange(5000))
     ks = B["keys_sorted"].astype(np.int64)
@@ -259,6 +259,44 @@ def test_binning_permutation_sorted_stable():
     for s, e in zip(st, en):
         covered[s:e] += 1
     assert np.all(covered == 1)
+
+
+def test_kd_refinement_keeps_cells_and_permutes_within():
+    rng = np.random.default_rng(5)
+    C = rng.uniform(0, 1, (20000, 3)).astype(np.float32)
+    A = oracle.binning(C, 0.05, 4.0, kd_leaf=0)
+    B = oracle.binning(C, 0.05, 4.0)
+    assert np.array_equal(A["cell_start"], B["cell_start"]) and np.array_equal(A["cell_end"], B["cell_end"])
+    assert np.array_equal(A["cell_of_sorted"], B["cell_of_sorted"])
+    for s, e in zip(B["cell_start"], B["cell_end"]):
+        assert set(A["perm"][s:e]) == set(B["perm"][s:e])
+
+
+def test_kd_order_on_a_line_is_a_sort():
+    """Collinear points along x: every split is along x, so the order sorts x."""
+    rng = np.random.default_rng(6)
+    x = rng.uniform(-1, 1, 300).astype(np.float32)
+    P = np.stack([x, np.zeros_like(x), np.zeros_like(x)], 1)
+    o = oracle._kd_order(P, 32, 128)
+    assert np.array_equal(o, np.argsort(x, kind="stable"))
+
+
+def test_kd_order_leaves_are_compact_squares():
+    """A 16 x 16 lattice in a plane: tiles of 128 are 8 x 16 halves and leaves of 32
+    are 4 x 8 (or 8 x 4) blocks of nodes."""
+    i, j = np.meshgrid(np.arange(16), np.arange(16), indexing="ij")
+    rng = np.random.default_rng(7)
+    P = np.stack([i.ravel(), j.ravel(), np.zeros(256)], 1).astype(np.float32)[rng.permutation(256)]
+    o = oracle._kd_order(P, 32, 128)
+    Q = P[o]
+    for t in range(2):
+        q = Q[128 * t:128 * (t + 1)]
+        ext = sorted((q.max(0) - q.min(0))[:2])
+        assert ext == [7.0, 15.0]
+    for leaf in range(8):
+        q = Q[32 * leaf:32 * (leaf + 1)]
+        ext = sorted((q.max(0) - q.min(0))[:2])
+        assert ext == [3.0, 7.0]
 
 
 def test_binning_cell_edge():
