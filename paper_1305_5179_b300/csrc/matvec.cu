@@ -29,6 +29,9 @@
 namespace {
 
 constexpr int kWarps = 4;
+#ifndef RBF_MV_MINBLOCKS
+#define RBF_MV_MINBLOCKS 4
+#endif
 
 typedef unsigned long long f2;      // two float32 in one 64-bit register pair
 
@@ -117,7 +120,7 @@ struct Stage {            // one block of sources, structure of arrays (2 s_x, 2
 // masked: only terms with arg > thr_t.  Sources are paired in the f32x2 operands, targets broadcast.
 template <bool kMasked, bool kShift>
 __device__ __forceinline__ void block_sum(const Stage &st, int cnt4, const f2 (&DX)[kTpl], const f2 (&DY)[kTpl],
-                                          const f2 (&DZ)[kTpl], const f2 (&TH)[kTpl], const f2 (&SH)[kTpl],
+                                          const f2 (&DZ)[kTpl], const float (&TH)[kTpl], const float (&SH)[kTpl],
                                           f2 (&P)[kTpl]) {
 #pragma unroll
     for (int t = 0; t < kTpl; ++t) P[t] = 0ull;
@@ -132,16 +135,12 @@ __device__ __forceinline__ void block_sum(const Stage &st, int cnt4, const f2 (&
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const f2 Xs = h ? X1 : X0, Ys = h ? Y1 : Y0, Zs = h ? Z1 : Z0, Ws = h ? W1 : W0;
-                const f2 c0 = kShift ? sub2(h ? B1 : B0, SH[t]) : (h ? B1 : B0);
+                const f2 c0 = kShift ? sub2(h ? B1 : B0, pk(SH[t], SH[t])) : (h ? B1 : B0);
                 const f2 arg = fma2(DX[t], Xs, fma2(DY[t], Ys, fma2(DZ[t], Zs, c0)));
                 float a0, a1;
                 upk(arg, a0, a1);
                 f2 E = pk(ex2_approx(a0), ex2_approx(a1));
-                if (kMasked) {
-                    float th, th1;
-                    upk(TH[t], th, th1);
-                    E = mul2(E, pk(set_gt(a0, th), set_gt(a1, th)));
-                }
+                if (kMasked) E = mul2(E, pk(set_gt(a0, TH[t]), set_gt(a1, TH[t])));
                 P[t] = fma2(Ws, E, P[t]);
             }
         }
@@ -149,25 +148,19 @@ __device__ __forceinline__ void block_sum(const Stage &st, int cnt4, const f2 (&
 }
 
 template <bool kGrid>
-__global__ void __launch_bounds__(kWarps * 32) k_matvec_f32(MvArgs a) {
+__global__ void __launch_bounds__(kWarps * 32, RBF_MV_MINBLOCKS) k_matvec_f32(MvArgs a) {
     __shared__ Stage s_st[kWarps];
     __shared__ float s_red[kWarps][kChunk];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int4 sg = a.seg[blockIdx.x];
     const int64_t t = sg.x;
-    const f2 scl2 = pk(a.scl, a.scl), R2 = pk(a.R, a.R);
 
-    // targets lane + 32 u, kept duplicated (x, x) for the f32x2 operands
-    f2 TX[kTpl], TY[kTpl], TZ[kTpl];
-    float acc[kTpl];
+    // targets lane + 32 u
+    float tx[kTpl], ty[kTpl], tz[kTpl], acc[kTpl];
 #pragma unroll
     for (int u = 0; u < kTpl; ++u) {
-        float x, y, z;
         int64_t oi;
-        target_xyz<kGrid>(a, t, lane + 32 * u, x, y, z, oi);
-        TX[u] = pk(x, x);
-        TY[u] = pk(y, y);
-        TZ[u] = pk(z, z);
+        target_xyz<kGrid>(a, t, lane + 32 * u, tx[u], ty[u], tz[u], oi);
         acc[u] = 0.f;
     }
     Stage &st = s_st[warp];
@@ -209,29 +202,23 @@ __global__ void __launch_bounds__(kWarps * 32) k_matvec_f32(MvArgs a) {
                 wv = a.w[bi.x + lane];
             }
         }
-        f2 DX[kTpl], DY[kTpl], DZ[kTpl], D2[kTpl], TH[kTpl], SH[kTpl], P[kTpl];
-        float ea[kTpl];
+        f2 DX[kTpl], DY[kTpl], DZ[kTpl], P[kTpl];
+        float TH[kTpl], SH[kTpl], D2[kTpl], ea[kTpl];
         bool unsafe = false;
-        const f2 cx = pk(c.x, c.x), cy = pk(c.y, c.y), cz = pk(c.z, c.z);
 #pragma unroll
         for (int u = 0; u < kTpl; ++u) {
-            DX[u] = mul2(sub2(TX[u], cx), scl2);
-            DY[u] = mul2(sub2(TY[u], cy), scl2);
-            DZ[u] = mul2(sub2(TZ[u], cz), scl2);
-            D2[u] = fma2(DX[u], DX[u], fma2(DY[u], DY[u], mul2(DZ[u], DZ[u])));
-            TH[u] = sub2(D2[u], R2);
-            float q0, q1;
-            upk(D2[u], q0, q1);
-            unsafe |= q0 > c.w;
+            const float dx = (tx[u] - c.x) * a.scl, dy = (ty[u] - c.y) * a.scl, dz = (tz[u] - c.z) * a.scl;
+            DX[u] = pk(dx, dx);
+            DY[u] = pk(dy, dy);
+            DZ[u] = pk(dz, dz);
+            D2[u] = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            TH[u] = D2[u] - a.R;
+            unsafe |= D2[u] > c.w;
         }
         unsafe = __any_sync(0xffffffffu, unsafe);
         if (!unsafe) {
 #pragma unroll
-            for (int u = 0; u < kTpl; ++u) {
-                float q0, q1;
-                upk(D2[u], q0, q1);
-                ea[u] = ex2_approx(-q0);
-            }
+            for (int u = 0; u < kTpl; ++u) ea[u] = ex2_approx(-D2[u]);
             if (masked)
                 block_sum<true, false>(st, cnt4, DX, DY, DZ, TH, SH, P);
             else
@@ -241,13 +228,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_matvec_f32(MvArgs a) {
             const float rB = c.w < INFINITY ? 32.f * rsqrtf(c.w) : 0.f;
 #pragma unroll
             for (int u = 0; u < kTpl; ++u) {
-                float q0, q1, t0, t1;
-                upk(D2[u], q0, q1);
-                upk(TH[u], t0, t1);
-                const float cs = 2.f * sqrtf(q0) * rB;
-                SH[u] = pk(cs, cs);
-                ea[u] = ex2_approx(cs - q0);
-                TH[u] = pk(t0 - cs, t0 - cs);
+                const float cs = 2.f * sqrtf(D2[u]) * rB;
+                SH[u] = cs;
+                ea[u] = ex2_approx(cs - D2[u]);
+                TH[u] -= cs;
             }
             block_sum<true, true>(st, cnt4, DX, DY, DZ, TH, SH, P);
         }
