@@ -286,6 +286,58 @@ rbf_status rbf_eval_grid(rbf_ctx *ctx, const float *centers, const double *weigh
                          const rbf_plan_params *pp, const rbf_grid *g, float *f, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Batched solve of many independent problems (for example many clouds of
+ * uneven size, each with its own sigma): one plan per problem, solved together
+ * by flexible GMRES in lockstep with every step on the device, so that a whole
+ * solve is a single CUDA graph launch.  The product is a persistent kernel
+ * whose CTAs take (problem, segment) work items, longest first, from an atomic
+ * counter; the Arnoldi reductions are segmented per problem; the Givens
+ * rotations and the triangular solve run on the device.  The iteration count
+ * is fixed (max_it, restarted every m <= 64), as in the paper's timing protocol
+ * (Table II); each problem reports its own float64-class true residual.
+ * ------------------------------------------------------------------------ */
+typedef struct rbf_batch rbf_batch;
+
+typedef struct {
+    double ms_setup;            /* preconditioner set-up and buffers, milliseconds */
+    double ms_solve;            /* gather, graph launch, scatter, milliseconds (CUDA events) */
+    int64_t graph_nodes;        /* nodes of the captured solve (0 when it was replayed) */
+    int recaptured;             /* 1 if this call captured the graph */
+    int persistent_ctas;        /* CTAs of the persistent product */
+    int64_t work_items;         /* (problem, segment) items per product */
+    int converged;              /* problems whose true residual met tol */
+    double worst_residual;      /* largest relative true residual over the problems */
+    int precond_failed_blocks;
+} rbf_batch_stats;
+
+/* Group `nplans` plans (made on `ctx`, kept alive by the caller until the batch
+ * is destroyed) into a batch.  Re-cuts the plans' pair lists into segments of a
+ * common length for the persistent product (the plans stay usable). */
+rbf_status rbf_batch_create(rbf_ctx *ctx, rbf_plan *const *plans, int nplans, rbf_batch **batch, void *stream);
+rbf_status rbf_batch_destroy(rbf_batch *batch);
+
+/* Total number of centres (sum over the plans). */
+int64_t rbf_batch_size(const rbf_batch *batch);
+
+/* y = A~ z for every problem; z, y: concatenations of the problems' vectors in
+ * plan order (caller order within each problem), float. */
+rbf_status rbf_batch_matvec(rbf_batch *batch, const float *z, float *y, void *stream);
+
+/* Solve every problem: b (float) and x (double, out) are concatenations as above;
+ * p->fixed_iterations is implied; p->m <= 64; p->precond NONE or SCHWARZ (the
+ * Schwarz set-up runs on every plan when its block size changes).  reports: host
+ * array of nplans (may be NULL); stats: host (may be NULL). */
+rbf_status rbf_batch_solve(rbf_batch *batch, const float *b, const rbf_solve_params *p, double *x,
+                           rbf_report *reports, rbf_batch_stats *stats, void *stream);
+
+/* Choose the Schwarz subdomain size: for each candidate block size (core = 3/4
+ * of it) run a short solve (min(m, 20) iterations) of b and score it by decades
+ * of worst-case residual reduction per millisecond.  *best receives the winner;
+ * scores (host, ncand, may be NULL) the scores. */
+rbf_status rbf_batch_autotune(rbf_batch *batch, const float *b, const rbf_solve_params *p, const int *candidates,
+                              int ncand, int *best, double *scores, void *stream);
+
+/* ------------------------------------------------------------------------
  * Allocation-free untruncated product (the paper has no counterpart: it is a
  * service to callers of this library that cannot allocate device memory when
  * they call in, for example a host that reserves its whole device-memory

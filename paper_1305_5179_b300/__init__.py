@@ -36,6 +36,8 @@ EXPORTS = (
     "rbf_matvec", "rbf_count_pairs", "rbf_residual", "rbf_schwarz_setup", "rbf_schwarz_apply",
     "rbf_plan_solve", "rbf_solve", "rbf_plan_eval_grid", "rbf_count_grid_pairs", "rbf_eval_grid",
     "rbf_matvec_dense_noalloc",
+    "rbf_batch_create", "rbf_batch_destroy", "rbf_batch_size", "rbf_batch_matvec", "rbf_batch_solve",
+    "rbf_batch_autotune",
 )
 
 
@@ -85,6 +87,13 @@ class ProbeResult(ctypes.Structure):
                 ("ffma_per_clk_sm", ctypes.c_double), ("ffma2_lanes_per_clk_sm", ctypes.c_double)]
 
 
+class BatchStats(ctypes.Structure):
+    _fields_ = [("ms_setup", ctypes.c_double), ("ms_solve", ctypes.c_double), ("graph_nodes", ctypes.c_int64),
+                ("recaptured", ctypes.c_int), ("persistent_ctas", ctypes.c_int), ("work_items", ctypes.c_int64),
+                ("converged", ctypes.c_int), ("worst_residual", ctypes.c_double),
+                ("precond_failed_blocks", ctypes.c_int)]
+
+
 class Grid(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3), ("dims", ctypes.c_int64 * 3)]
 
@@ -125,6 +134,12 @@ def lib() -> ctypes.CDLL:
         "rbf_plan_eval_grid": ([P, P, ctypes.POINTER(Grid), P, P], I),
         "rbf_count_grid_pairs": ([P, ctypes.POINTER(Grid), ctypes.POINTER(I64), P], I),
         "rbf_matvec_dense_noalloc": ([P, P, I64, F, P, P, P], I),
+        "rbf_batch_create": ([P, ctypes.POINTER(P), I, ctypes.POINTER(P), P], I),
+        "rbf_batch_destroy": ([P], I),
+        "rbf_batch_size": ([P], I64),
+        "rbf_batch_matvec": ([P, P, P, P], I),
+        "rbf_batch_solve": ([P, P, ctypes.POINTER(SolveParams), P, P, ctypes.POINTER(BatchStats), P], I),
+        "rbf_batch_autotune": ([P, P, ctypes.POINTER(SolveParams), P, I, ctypes.POINTER(I), P, P], I),
         "rbf_eval_grid": ([P, P, P, I64, ctypes.POINTER(PlanParams), ctypes.POINTER(Grid), P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -398,3 +413,60 @@ def matvec_dense_noalloc(ctx: Context, centers, sigma: float, z, out, stream=Non
     ctx.check(lib().rbf_matvec_dense_noalloc(ctx._h, _ptr(centers), n, float(sigma), _ptr(z), _ptr(out),
                                              _stream(stream)), "rbf_matvec_dense_noalloc")
     return out
+
+
+class Batch:
+    """Many independent problems (one Plan each) solved together: a persistent
+    product kernel over all problems and a lockstep FGMRES captured as one CUDA
+    graph (include/rbf.h, rbf_batch_*).  Keeps references to its plans."""
+
+    def __init__(self, ctx: Context, plans, stream=None):
+        self.ctx = ctx
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        self._h = ctypes.c_void_p()
+        ctx.check(lib().rbf_batch_create(ctx._h, arr, len(self.plans), ctypes.byref(self._h), _stream(stream)),
+                  "rbf_batch_create")
+        self.n = int(lib().rbf_batch_size(self._h))
+        self.device = self.plans[0].device
+
+    def close(self):
+        if self._h:
+            lib().rbf_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def matvec(self, z, stream=None):
+        import torch
+        _req(z, torch.float32, "z", self.n)
+        y = torch.empty_like(z)
+        self.ctx.check(lib().rbf_batch_matvec(self._h, _ptr(z), _ptr(y), _stream(stream)), "rbf_batch_matvec")
+        return y
+
+    def solve(self, b, stream=None, **kw):
+        """Fixed-iteration solve of every problem; returns (x float64, reports, stats)."""
+        import torch
+        _req(b, torch.float32, "b", self.n)
+        x = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        reps = (Report * len(self.plans))()
+        st = BatchStats()
+        sp = _solve_params(**kw)
+        self.ctx.check(lib().rbf_batch_solve(self._h, _ptr(b), ctypes.byref(sp), _ptr(x), reps, ctypes.byref(st),
+                                             _stream(stream)), "rbf_batch_solve")
+        return x, [r.as_dict() for r in reps], {f: getattr(st, f) for f, _ in st._fields_}
+
+    def autotune(self, b, candidates=(32, 64, 96, 128), stream=None, **kw):
+        import torch
+        _req(b, torch.float32, "b", self.n)
+        cand = (ctypes.c_int * len(candidates))(*candidates)
+        scores = (ctypes.c_double * len(candidates))()
+        best = ctypes.c_int(0)
+        sp = _solve_params(**kw)
+        self.ctx.check(lib().rbf_batch_autotune(self._h, _ptr(b), ctypes.byref(sp), cand, len(candidates),
+                                                ctypes.byref(best), scores, _stream(stream)), "rbf_batch_autotune")
+        return int(best.value), list(scores)

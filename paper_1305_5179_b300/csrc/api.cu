@@ -10,6 +10,7 @@
 
 static std::atomic<long long> g_launches{0};
 void rbf_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void rbf_count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 namespace {
 
@@ -327,6 +328,62 @@ rbf_status rbf_eval_grid(rbf_ctx *ctx, const float *centers, const double *weigh
         }
         cudaStreamSynchronize(S(stream));
         delete P;
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_batch_create(rbf_ctx *ctx, rbf_plan *const *plans, int nplans, rbf_batch **batch, void *stream) {
+    if (batch) *batch = nullptr;
+    return guarded(ctx, [&]() {
+        RBF_CHECK(batch, RBF_ERR_INVALID, "null batch output");
+        *batch = batch_create(ctx, plans, nplans, S(stream));
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_batch_destroy(rbf_batch *batch) {
+    if (!batch) return RBF_OK;
+    batch_destroy(batch);
+    return RBF_OK;
+}
+
+int64_t rbf_batch_size(const rbf_batch *batch) { return batch ? batch_size(batch) : 0; }
+
+rbf_status rbf_batch_matvec(rbf_batch *batch, const float *z, float *y, void *stream) {
+    if (!batch) return RBF_ERR_INVALID;
+    rbf_ctx *ctx = batch_ctx(batch);
+    return guarded(ctx, [&]() {
+        RBF_CHECK(z && y && z != y, RBF_ERR_INVALID, "z and y must be distinct device pointers");
+        cudaStream_t s = S(stream);
+        const int64_t N = batch_size(batch);
+        DevBuf<float> zs, ys;
+        zs.alloc(N, s);
+        ys.alloc(N, s);
+        batch_gather_f32(batch, z, zs.p, s);
+        batch_matvec_binned(batch, zs.p, ys.p, s);
+        batch_scatter_f32(batch, ys.p, y, s);
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_batch_solve(rbf_batch *batch, const float *b, const rbf_solve_params *p, double *x,
+                           rbf_report *reports, rbf_batch_stats *stats, void *stream) {
+    if (!batch) return RBF_ERR_INVALID;
+    return guarded(batch_ctx(batch), [&]() {
+        RBF_CHECK(b && p && x, RBF_ERR_INVALID, "null pointer argument");
+        return batch_solve(batch, b, *p, x, reports, stats, S(stream));
+    });
+}
+
+rbf_status rbf_batch_autotune(rbf_batch *batch, const float *b, const rbf_solve_params *p, const int *candidates,
+                              int ncand, int *best, double *scores, void *stream) {
+    if (!batch) return RBF_ERR_INVALID;
+    return guarded(batch_ctx(batch), [&]() {
+        RBF_CHECK(b && p && candidates && ncand > 0 && best, RBF_ERR_INVALID, "null pointer argument");
+        for (int c = 0; c < ncand; ++c)
+            RBF_CHECK(candidates[c] >= 1 && candidates[c] <= 128, RBF_ERR_UNSUPPORTED, "block %d outside 1..128",
+                      candidates[c]);
+        *best = batch_autotune(batch, b, *p, candidates, ncand, scores, S(stream));
         return RBF_OK;
     });
 }

@@ -1,0 +1,37 @@
+// Device-side view of one plan inside a batch (internal).
+#pragma once
+#include "plan.cuh"
+
+struct PlanView {
+    // operator
+    const float4 *pos;
+    const float4 *src;
+    const float4 *blk_c;
+    const int2 *tiles;
+    const int2 *blk;
+    const int32_t *ent;
+    const int4 *seg;
+    const int32_t *tile_seg;
+    const int32_t *perm;
+    float *partial;        // nseg x kChunk partial sums (split tiles only), or null
+    int64_t n;             // centres of this problem
+    int64_t off;           // offset of this problem in the concatenated vectors
+    int nseg, ntiles, any_split;
+    float scl, R;
+    // double-float residual constants
+    float Ch, Cl, Rh, Rl;
+    // restricted additive Schwarz (L == null: no preconditioner data)
+    const float *L;
+    int core, B, restricted;
+    int64_t nsub;
+};
+
+// Uploads the exp2 table once per device (synchronises; call before any capture).
+void residual_df_prepare(int device, cudaStream_t s);
+
+// r = b - A~ x for every problem of a batch (double-float), vectors concatenated in
+// binned order.  items: (problem, segment) pairs; splits: (problem, tile) pairs of
+// split tiles.  (residual_df.cu)
+void residual_df_batched(const PlanView *views, const int2 *items, int64_t nitems, const int2 *splits,
+                         int64_t nsplits, const float *bs, const double *xs, double *rs, double *part_pool,
+                         const int64_t *part_off, int device, cudaStream_t s);

@@ -45,6 +45,7 @@ struct RbfError {
 // Every kernel launch of the library is followed by RBF_LAUNCHED(): it checks the
 // launch and counts it (rbf_launch_count).
 void rbf_count_launch();
+void rbf_count_launches(long long n);
 #define RBF_LAUNCHED()             \
     do {                           \
         rbf_count_launch();        \

@@ -469,28 +469,38 @@ void build_pairlist(rbf_plan *P, const float4 *tlo, const float4 *thi, int64_t n
     int64_t want = 8LL * P->ctx->num_sms;
     int64_t seglen = len > 0 ? std::max<int64_t>(64, 2 * ceil_div(len, std::max<int64_t>(ntiles, 1))) : 1;
     if (ntiles < want && len > 0) seglen = std::min<int64_t>(seglen, std::max<int64_t>(8, ceil_div(len, want)));
-    pl.seglen = (int)std::min<int64_t>(seglen, INT_MAX / 2);
-    pl.tile_seg.alloc(ntiles + 1, s);
-    k_seg_count<<<grid_for(ntiles), kThreads, 0, s>>>(pl.off.p, ntiles, pl.seglen, cnt.p);
+    segment_pairlist(P, pl, seglen, s);
+}
+
+void segment_into(rbf_plan *P, const PairList &pl, int64_t seglen, PBuf<int4> &seg, PBuf<int32_t> &tile_seg,
+                  int64_t &nseg_out, bool &any_split, cudaStream_t s) {
+    const int64_t ntiles = pl.ntiles;
+    const int sl = (int)std::max<int64_t>(1, std::min<int64_t>(seglen, INT_MAX / 2));
+    DevBuf<int32_t> cnt;
+    cnt.alloc(std::max<int64_t>(ntiles, 1), s);
+    tile_seg.alloc(ntiles + 1, s);
+    k_seg_count<<<grid_for(ntiles), kThreads, 0, s>>>(pl.off.p, ntiles, sl, cnt.p);
     RBF_LAUNCHED();
-    scan_exclusive_i32(cnt.p, pl.tile_seg.p, ntiles, s);
+    scan_exclusive_i32(cnt.p, tile_seg.p, ntiles, s);
     int32_t nseg = 0;
-    RBF_CUDA(cudaMemcpyAsync(&nseg, pl.tile_seg.p + ntiles, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(cudaMemcpyAsync(&nseg, tile_seg.p + ntiles, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     RBF_CUDA(cudaStreamSynchronize(s));
-    pl.nseg = nseg;
-    pl.seg.alloc(std::max<int64_t>(nseg, 1), s);
-    k_seg_fill<<<grid_for(ntiles), kThreads, 0, s>>>(pl.off.p, pl.tile_seg.p, ntiles, pl.seglen, pl.seg.p);
+    nseg_out = nseg;
+    seg.alloc(std::max<int64_t>(nseg, 1), s);
+    k_seg_fill<<<grid_for(ntiles), kThreads, 0, s>>>(pl.off.p, tile_seg.p, ntiles, sl, seg.p);
     RBF_LAUNCHED();
+    // a split exists iff there are more segments than non-empty tiles
+    std::vector<int32_t> offs(ntiles + 1);
+    RBF_CUDA(cudaMemcpyAsync(offs.data(), pl.off.p, (ntiles + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(cudaStreamSynchronize(s));
     int64_t nonempty = 0;
-    {
-        std::vector<int32_t> o(2);
-        // a split exists iff there are more segments than non-empty tiles; count the latter on the host
-        std::vector<int32_t> offs(ntiles + 1);
-        RBF_CUDA(cudaMemcpyAsync(offs.data(), pl.off.p, (ntiles + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        RBF_CUDA(cudaStreamSynchronize(s));
-        for (int64_t t = 0; t < ntiles; ++t) nonempty += offs[t + 1] > offs[t];
-    }
-    pl.any_split = nseg > nonempty;
+    for (int64_t t = 0; t < ntiles; ++t) nonempty += offs[t + 1] > offs[t];
+    any_split = nseg > nonempty;
+}
+
+void segment_pairlist(rbf_plan *P, PairList &pl, int64_t seglen, cudaStream_t s) {
+    pl.seglen = (int)std::max<int64_t>(1, std::min<int64_t>(seglen, INT_MAX / 2));
+    segment_into(P, pl, seglen, pl.seg, pl.tile_seg, pl.nseg, pl.any_split, s);
 }
 
 // Runs of <= len centres per cell -> run list (and the per-cell run offsets if asked).

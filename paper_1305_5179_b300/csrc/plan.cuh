@@ -82,6 +82,11 @@ void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s);
 // Pair list of target tiles given by boxes (lo, hi per tile) against the plan's source blocks.
 void build_pairlist(rbf_plan *P, const float4 *tlo, const float4 *thi, int64_t ntiles, PairList &pl,
                     cudaStream_t s);
+// (Re)cut a built pair list into segments of at most seglen entries.
+void segment_pairlist(rbf_plan *P, PairList &pl, int64_t seglen, cudaStream_t s);
+// The same cut into caller-owned arrays (the pair list itself is not modified).
+void segment_into(rbf_plan *P, const PairList &pl, int64_t seglen, PBuf<int4> &seg, PBuf<int32_t> &tile_seg,
+                  int64_t &nseg, bool &any_split, cudaStream_t s);
 void permute_to_binned_f32(const rbf_plan *P, const float *in, float *out, cudaStream_t s);
 void permute_to_binned_f64_to_f32(const rbf_plan *P, const double *in, float *out, cudaStream_t s);
 void permute_to_binned_f64(const rbf_plan *P, const double *in, double *out, cudaStream_t s);
@@ -113,6 +118,19 @@ void schwarz_apply_binned(rbf_plan *P, const double *vd, const float *vf, float 
 // grid.cu
 void eval_grid(rbf_plan *P, const double *weights, const rbf_grid &g, float *f, cudaStream_t s);
 int64_t count_grid_pairs(rbf_plan *P, const rbf_grid &g, cudaStream_t s);
+
+// batch.cu
+rbf_batch *batch_create(rbf_ctx *ctx, rbf_plan *const *plans, int nplans, cudaStream_t s);
+void batch_matvec_binned(rbf_batch *Bt, const float *z, float *y, cudaStream_t s);
+rbf_status batch_solve(rbf_batch *Bt, const float *b, const rbf_solve_params &p, double *x, rbf_report *reps,
+                       rbf_batch_stats *stats, cudaStream_t s);
+int batch_autotune(rbf_batch *Bt, const float *b, const rbf_solve_params &p, const int *cands, int ncand,
+                   double *scores, cudaStream_t s);
+int64_t batch_size(const rbf_batch *Bt);
+void batch_destroy(rbf_batch *Bt);
+rbf_ctx *batch_ctx(rbf_batch *Bt);
+void batch_gather_f32(rbf_batch *Bt, const float *in, float *out, cudaStream_t s);
+void batch_scatter_f32(rbf_batch *Bt, const float *in, float *out, cudaStream_t s);
 
 // fgmres.cu
 rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_params &p, double *x_caller,

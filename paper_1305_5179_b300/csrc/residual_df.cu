@@ -19,7 +19,7 @@
 // Per-term relative error is of order 1e-14.
 #include <cmath>
 
-#include "plan.cuh"
+#include "batch.cuh"
 
 namespace {
 
@@ -107,20 +107,13 @@ __device__ __forceinline__ df block_terms(float px, float py, float pz, const fl
     return acc;
 }
 
-__global__ void __launch_bounds__(kT) k_resid_df(const float4 *__restrict__ pos, const int2 *__restrict__ tiles,
-                                                 const double *__restrict__ x,
-                                                 const int2 *__restrict__ blk, const int32_t *__restrict__ ent,
-                                                 const int4 *__restrict__ seg, int64_t n, DfConst kc,
-                                                 const float *__restrict__ b, double *__restrict__ out,
-                                                 double *__restrict__ part) {
-    __shared__ float4 s_p[kBlk];
-    __shared__ float2 s_w[kBlk];
-    __shared__ float2 s_tab[64];
-    if (threadIdx.x < 64) s_tab[threadIdx.x] = c_tab[threadIdx.x];
-    const int4 sg = seg[blockIdx.x];
-    const int2 tl = tiles[sg.x];
-    const int64_t i = (int64_t)tl.x + threadIdx.x;
-    const bool valid = (int)threadIdx.x < tl.y;
+// One segment of one problem: acc over the segment's blocks for target thread.
+__device__ __forceinline__ double resid_segment(const float4 *__restrict__ pos, const int2 tl, const double *__restrict__ x,
+                                                const int2 *__restrict__ blk, const int32_t *__restrict__ ent,
+                                                const int4 sg, const DfConst &kc, float4 *s_p, float2 *s_w,
+                                                const float2 *s_tab, bool &valid, int64_t &i) {
+    i = (int64_t)tl.x + threadIdx.x;
+    valid = (int)threadIdx.x < tl.y;
     float4 p = valid ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     double acc = 0.0;
     for (int e = sg.y; e < sg.z; ++e) {
@@ -136,6 +129,23 @@ __global__ void __launch_bounds__(kT) k_resid_df(const float4 *__restrict__ pos,
         df a = block_terms(p.x, p.y, p.z, s_p, s_w, bi.y, kc, s_tab);
         acc += (double)a.h + (double)a.l;
     }
+    return acc;
+}
+
+__global__ void __launch_bounds__(kT) k_resid_df(const float4 *__restrict__ pos, const int2 *__restrict__ tiles,
+                                                 const double *__restrict__ x,
+                                                 const int2 *__restrict__ blk, const int32_t *__restrict__ ent,
+                                                 const int4 *__restrict__ seg, int64_t n, DfConst kc,
+                                                 const float *__restrict__ b, double *__restrict__ out,
+                                                 double *__restrict__ part) {
+    __shared__ float4 s_p[kBlk];
+    __shared__ float2 s_w[kBlk];
+    __shared__ float2 s_tab[64];
+    if (threadIdx.x < 64) s_tab[threadIdx.x] = c_tab[threadIdx.x];
+    const int4 sg = seg[blockIdx.x];
+    bool valid;
+    int64_t i;
+    double acc = resid_segment(pos, tiles[sg.x], x, blk, ent, sg, kc, s_p, s_w, s_tab, valid, i);
     if (sg.w) {
         if (valid) out[i] = (double)b[i] - acc;
     } else {
@@ -159,6 +169,51 @@ __global__ void k_reduce_resid_df(const int32_t *__restrict__ tile_seg, const in
     }
 }
 
+// batched: one CTA per (problem, segment)
+__global__ void __launch_bounds__(kT) k_resid_df_batched(const PlanView *__restrict__ views,
+                                                         const int2 *__restrict__ items, float Lh, float Ll,
+                                                         const float *__restrict__ bs, const double *__restrict__ xs,
+                                                         double *__restrict__ rs, double *__restrict__ pool,
+                                                         const int64_t *__restrict__ poff) {
+    __shared__ float4 s_p[kBlk];
+    __shared__ float2 s_w[kBlk];
+    __shared__ float2 s_tab[64];
+    if (threadIdx.x < 64) s_tab[threadIdx.x] = c_tab[threadIdx.x];
+    const int2 it = items[blockIdx.x];
+    const PlanView &v = views[it.x];
+    const int4 sg = v.seg[it.y];
+    DfConst kc;
+    kc.Ch = v.Ch;
+    kc.Cl = v.Cl;
+    kc.Rh = v.Rh;
+    kc.Rl = v.Rl;
+    kc.Lh = Lh;
+    kc.Ll = Ll;
+    bool valid;
+    int64_t i;
+    double acc = resid_segment(v.pos, v.tiles[sg.x], xs + v.off, v.blk, v.ent, sg, kc, s_p, s_w, s_tab, valid, i);
+    if (sg.w) {
+        if (valid) rs[v.off + i] = (double)bs[v.off + i] - acc;
+    } else {
+        pool[poff[it.x] + (int64_t)it.y * kChunk + threadIdx.x] = acc;
+    }
+}
+
+__global__ void k_reduce_resid_df_batched(const PlanView *__restrict__ views, const int2 *__restrict__ splits,
+                                          const double *__restrict__ pool, const int64_t *__restrict__ poff,
+                                          const float *__restrict__ bs, double *__restrict__ rs) {
+    const int2 it = splits[blockIdx.x];
+    const PlanView &v = views[it.x];
+    int s0 = v.tile_seg[it.y], s1 = v.tile_seg[it.y + 1];
+    const int2 tl = v.tiles[it.y];
+    for (int q = threadIdx.x; q < tl.y; q += blockDim.x) {
+        double acc = 0.0;
+        for (int sidx = s0; sidx < s1; ++sidx) acc += pool[poff[it.x] + (int64_t)sidx * kChunk + q];
+        int64_t i = v.off + tl.x + q;
+        rs[i] = (double)bs[i] - acc;
+    }
+}
+
 inline void split(double v, float &h, float &l) {
     h = (float)v;
     l = (float)(v - (double)h);
@@ -176,6 +231,24 @@ void upload_table(int device, cudaStream_t s) {
 }
 
 }  // namespace
+
+void residual_df_prepare(int device, cudaStream_t s) { upload_table(device, s); }
+
+void residual_df_batched(const PlanView *views, const int2 *items, int64_t nitems, const int2 *splits,
+                         int64_t nsplits, const float *bs, const double *xs, double *rs, double *part_pool,
+                         const int64_t *part_off, int device, cudaStream_t s) {
+    upload_table(device, s);
+    float Lh, Ll;
+    split(0.6931471805599453, Lh, Ll);
+    if (nitems > 0) {
+        k_resid_df_batched<<<(unsigned)nitems, kT, 0, s>>>(views, items, Lh, Ll, bs, xs, rs, part_pool, part_off);
+        RBF_LAUNCHED();
+    }
+    if (nsplits > 0) {
+        k_reduce_resid_df_batched<<<(unsigned)nsplits, kChunk, 0, s>>>(views, splits, part_pool, part_off, bs, rs);
+        RBF_LAUNCHED();
+    }
+}
 
 void residual_binned_df(rbf_plan *P, const float *bs, const double *xs, double *rs, cudaStream_t s) {
     upload_table(P->ctx->device, s);
