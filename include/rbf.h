@@ -216,7 +216,9 @@ rbf_status rbf_schwarz_apply(rbf_plan *plan, const float *v, float *z, void *str
  * rbf_residual's float64-accurate kernel (iterative refinement:
  * x += GMRES(b - A~ x)).
  * ------------------------------------------------------------------------ */
-enum { RBF_PRECOND_NONE = 0, RBF_PRECOND_SCHWARZ = 1 };
+enum { RBF_PRECOND_NONE = 0, RBF_PRECOND_SCHWARZ = 1, RBF_PRECOND_MLP = 2 };
+
+typedef struct rbf_mlp rbf_mlp;   /* learned block preconditioner, see below */
 
 typedef struct {
     int m;                  /* restart length, 1..512 (default 50 when 0) */
@@ -228,6 +230,9 @@ typedef struct {
     int true_residual_each_restart; /* non-zero (default): float64 residual at every restart;
                                        zero: float32 product at restarts, float64 residual at the end */
     int residual_mode;      /* RBF_RESIDUAL_DF (0) or RBF_RESIDUAL_F64 (1), see rbf_residual */
+    rbf_mlp *mlp;           /* RBF_PRECOND_MLP: the trained network */
+    float mlp_lambda;       /* RBF_PRECOND_MLP: the shift the network was trained for */
+    int mlp_initial_guess;  /* RBF_PRECOND_MLP: start from x0 = network(b) instead of 0 */
 } rbf_solve_params;
 
 typedef struct {
@@ -284,6 +289,60 @@ rbf_status rbf_count_grid_pairs(rbf_plan *plan, const rbf_grid *g, int64_t *coun
 /* One-shot form: plan from (centers, n, pp), evaluate, free. */
 rbf_status rbf_eval_grid(rbf_ctx *ctx, const float *centers, const double *weights, int64_t n,
                          const rbf_plan_params *pp, const rbf_grid *g, float *f, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Learned block preconditioner (not in the paper: it stands in for the exact
+ * subdomain solve of the restricted additive Schwarz method, Sec. III.A).
+ * Blocks are the Schwarz subdomains of 64 centres without overlap.  Input of a
+ * block and vector r (256 values): the 64 offsets (c_k - c_mean)/sigma, x y z per
+ * centre, then rho = 8 r_k / |r|_2 (unit mean square).  Network
+ * 256 -> 256 -> 256 -> 64, ReLU, plus a skip connection adding rho to the output;
+ * weights W[out][in] row-major followed by the bias, layer by layer
+ * (RBF_MLP_NPARAMS floats: W1 256x256, b1, W2 256x256, b2, W3 64x256, b3);
+ * inference uses a BF16 copy of the weights with FP32 accumulation.  The output
+ * approximates 8 lambda (A_i + lambda I)^-1 r / |r|; the preconditioner writes
+ * output * |r| / (8 lambda) on the block.  Blocks whose output is not finite fall
+ * back to the exact Schwarz block solve (set up automatically with block 64,
+ * core 64, shift lambda) and are counted in rbf_report.precond_failed_blocks.
+ * ------------------------------------------------------------------------ */
+#define RBF_MLP_NPARAMS 148032
+#define RBF_MLP_IN 256
+#define RBF_MLP_OUT 64
+
+typedef struct {
+    int epochs;             /* passes over the data */
+    int batch;              /* rows per Adam step (consecutive rows, no shuffling) */
+    float lr;               /* Adam step size (beta1 0.9, beta2 0.999, eps 1e-8) */
+} rbf_train_params;
+
+/* host_params: RBF_MLP_NPARAMS floats (host), the initial weights. */
+rbf_status rbf_mlp_create(rbf_ctx *ctx, const float *host_params, rbf_mlp **mlp);
+rbf_status rbf_mlp_destroy(rbf_mlp *mlp);
+/* Copy the FP32 master weights to host memory (RBF_MLP_NPARAMS floats). */
+rbf_status rbf_mlp_get_params(rbf_mlp *mlp, float *host_params);
+
+/* Training data from a plan: for sample s with subdomain block_ids[s] (64-centre
+ * blocks without overlap, device int32) and right-hand side R[s] (device, 64
+ * float, caller-drawn random numbers): X[s] (256 float, out) and
+ * Y[s] = 8 lambda (A_i + lambda I)^-1 R[s] / |R[s]| (64 float, out) from an exact
+ * float64 Cholesky solve.  failed (host, optional): samples whose factorisation
+ * failed. */
+rbf_status rbf_mlp_make_data(rbf_plan *plan, float lambda, const int32_t *block_ids, const float *R, int64_t ns,
+                             float *X, float *Y, int64_t *failed, void *stream);
+
+/* Y = network(X) for `rows` inputs (device); use_bf16 selects the inference weights. */
+rbf_status rbf_mlp_forward(rbf_mlp *mlp, const float *X, int64_t rows, float *Y, int use_bf16, void *stream);
+
+/* Mean squared error of the FP32-weight network on (X, T) and, if host_grad is
+ * not NULL, its gradient with respect to the master weights (host,
+ * RBF_MLP_NPARAMS floats, same layout).  rows <= 65536. */
+rbf_status rbf_mlp_loss_grad(rbf_mlp *mlp, const float *X, const float *T, int64_t rows, double *loss,
+                             float *host_grad, void *stream);
+
+/* Adam training on (X, T) (device, ns rows); loss_history (host, epochs doubles,
+ * optional) receives the mean loss of every epoch. */
+rbf_status rbf_mlp_train(rbf_mlp *mlp, const float *X, const float *T, int64_t ns, const rbf_train_params *p,
+                         double *loss_history, void *stream);
 
 /* ------------------------------------------------------------------------
  * Batched solve of many independent problems (for example many clouds of

@@ -424,3 +424,82 @@ def fgmres(matvec, b: np.ndarray, precond=None, m: int = 50, tol: float = 1e-6, 
         if hist and hist[-1] <= tol:
             break
     return x, it, hist
+
+
+# --------------------------------------------------------------------------
+# Learned block preconditioner (not in the paper): FP64 reference of the MLP,
+# its gradient (manual back-propagation) and the training targets.
+# --------------------------------------------------------------------------
+def _mlp_unpack(params, sizes):
+    out, o = [], 0
+    for fin, fout in zip(sizes[:-1], sizes[1:]):
+        W = np.asarray(params[o:o + fin * fout], dtype=np.float64).reshape(fout, fin)
+        o += fin * fout
+        b = np.asarray(params[o:o + fout], dtype=np.float64)
+        o += fout
+        out.append((W, b))
+    return out
+
+
+def mlp_forward(params, X, sizes=(256, 256, 256, 64), skip=True):
+    """ReLU MLP: a_{l+1} = relu(a_l W_l^T + b_l) for hidden layers, linear output,
+    plus (skip) the last ``sizes[-1]`` inputs added to the output."""
+    X = np.asarray(X, dtype=np.float64)
+    a = X
+    layers = _mlp_unpack(params, sizes)
+    for li, (W, b) in enumerate(layers):
+        a = a @ W.T + b
+        if li < len(layers) - 1:
+            a = np.maximum(a, 0.0)
+    if skip:
+        a = a + X[:, -sizes[-1]:]
+    return a
+
+
+def mlp_loss_grad(params, X, T, sizes=(256, 256, 256, 64), skip=True):
+    """Mean squared error over all outputs and its gradient, packed like params
+    (the skip connection has no parameters)."""
+    X = np.asarray(X, dtype=np.float64)
+    T = np.asarray(T, dtype=np.float64)
+    layers = _mlp_unpack(params, sizes)
+    acts = [X]
+    a = X
+    for li, (W, b) in enumerate(layers):
+        z = a @ W.T + b
+        a = np.maximum(z, 0.0) if li < len(layers) - 1 else z
+        acts.append(a)
+    Y = acts[-1] + (X[:, -sizes[-1]:] if skip else 0.0)
+    diff = Y - T
+    loss = float(np.mean(diff * diff))
+    d = 2.0 * diff / diff.size
+    grads = [None] * len(layers)
+    for li in range(len(layers) - 1, -1, -1):
+        W, b = layers[li]
+        grads[li] = (d.T @ acts[li], d.sum(0))
+        if li > 0:
+            d = (d @ W) * (acts[li] > 0)
+    flat = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
+    return loss, flat
+
+
+def mlp_block_data(Cs, sigma, lam, block_ids, R, block=64):
+    """Features and targets of the learned preconditioner on binned centres Cs:
+    block i covers Cs[64 i : 64 i + 64] (clamped to the end);
+    X = [(c - mean)/sigma (x y z per centre), 8 r/|r|],
+    Y = 8 lam (A_i + lam I)^-1 r/|r| with A_i the untruncated Gaussian block,
+    solved by this module's Cholesky."""
+    Cs = np.asarray(Cs, dtype=np.float64)
+    n = len(Cs)
+    X = np.zeros((len(block_ids), 256))
+    Y = np.zeros((len(block_ids), 64))
+    for row, (bi, r) in enumerate(zip(block_ids, R)):
+        d0 = min(max(int(bi) * block, 0), n - block)
+        P = Cs[d0:d0 + block]
+        r = np.asarray(r, dtype=np.float64)
+        nr = np.linalg.norm(r)
+        rh = r / nr if nr > 0 else np.zeros_like(r)
+        X[row, :192] = ((P - P.mean(0)) / sigma).ravel()
+        X[row, 192:] = 8.0 * rh
+        A = dense_matrix(P, sigma) + lam * np.eye(block)
+        Y[row] = 8.0 * lam * chol_solve(cholesky(A), rh)
+    return X, Y

@@ -26,7 +26,7 @@ LIBPATH = os.path.join(HERE, "librbf.so")
 RBF_OK = 0
 STATUS = {0: "RBF_OK", 1: "RBF_ERR_INVALID", 2: "RBF_ERR_OOM", 3: "RBF_ERR_CUDA", 4: "RBF_ERR_NOT_CONVERGED",
           5: "RBF_ERR_BREAKDOWN", 6: "RBF_ERR_TIMEOUT", 7: "RBF_ERR_NOT_SPD", 8: "RBF_ERR_UNSUPPORTED"}
-PRECOND = {"none": 0, "schwarz": 1}
+PRECOND = {"none": 0, "schwarz": 1, "mlp": 2}
 RESIDUAL = {"df": 0, "f64": 1}
 
 # every entry point declared in include/rbf.h
@@ -38,7 +38,10 @@ EXPORTS = (
     "rbf_matvec_dense_noalloc",
     "rbf_batch_create", "rbf_batch_destroy", "rbf_batch_size", "rbf_batch_matvec", "rbf_batch_solve",
     "rbf_batch_autotune",
+    "rbf_mlp_create", "rbf_mlp_destroy", "rbf_mlp_get_params", "rbf_mlp_make_data", "rbf_mlp_forward",
+    "rbf_mlp_loss_grad", "rbf_mlp_train",
 )
+MLP_NPARAMS = 148032
 
 
 class RbfError(RuntimeError):
@@ -67,7 +70,12 @@ class SchwarzParams(ctypes.Structure):
 class SolveParams(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("max_it", ctypes.c_int), ("tol", ctypes.c_double), ("precond", ctypes.c_int),
                 ("schwarz", SchwarzParams), ("fixed_iterations", ctypes.c_int),
-                ("true_residual_each_restart", ctypes.c_int), ("residual_mode", ctypes.c_int)]
+                ("true_residual_each_restart", ctypes.c_int), ("residual_mode", ctypes.c_int),
+                ("mlp", ctypes.c_void_p), ("mlp_lambda", ctypes.c_float), ("mlp_initial_guess", ctypes.c_int)]
+
+
+class TrainParams(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float)]
 
 
 class Report(ctypes.Structure):
@@ -134,6 +142,13 @@ def lib() -> ctypes.CDLL:
         "rbf_plan_eval_grid": ([P, P, ctypes.POINTER(Grid), P, P], I),
         "rbf_count_grid_pairs": ([P, ctypes.POINTER(Grid), ctypes.POINTER(I64), P], I),
         "rbf_matvec_dense_noalloc": ([P, P, I64, F, P, P, P], I),
+        "rbf_mlp_create": ([P, P, ctypes.POINTER(P)], I),
+        "rbf_mlp_destroy": ([P], I),
+        "rbf_mlp_get_params": ([P, P], I),
+        "rbf_mlp_make_data": ([P, F, P, P, I64, P, P, ctypes.POINTER(I64), P], I),
+        "rbf_mlp_forward": ([P, P, I64, P, I, P], I),
+        "rbf_mlp_loss_grad": ([P, P, P, I64, ctypes.POINTER(D), P, P], I),
+        "rbf_mlp_train": ([P, P, P, I64, ctypes.POINTER(TrainParams), P, P], I),
         "rbf_batch_create": ([P, ctypes.POINTER(P), I, ctypes.POINTER(P), P], I),
         "rbf_batch_destroy": ([P], I),
         "rbf_batch_size": ([P], I64),
@@ -240,7 +255,7 @@ def _grid(lo, hi, dims) -> Grid:
 
 def _solve_params(m=50, max_it=500, tol=1e-6, precond="none", core=96, block=128, shift=1e-4, restricted=True,
                   escalate=True, fixed_iterations=False, true_residual_each_restart=True,
-                  residual="df") -> SolveParams:
+                  residual="df", mlp=None, mlp_lambda=1e-2, mlp_initial_guess=False) -> SolveParams:
     sp = SolveParams()
     sp.m, sp.max_it, sp.tol = int(m), int(max_it), float(tol)
     sp.precond = PRECOND[precond] if isinstance(precond, str) else int(precond)
@@ -248,6 +263,9 @@ def _solve_params(m=50, max_it=500, tol=1e-6, precond="none", core=96, block=128
     sp.fixed_iterations = int(bool(fixed_iterations))
     sp.true_residual_each_restart = int(bool(true_residual_each_restart))
     sp.residual_mode = RESIDUAL[residual]
+    sp.mlp = mlp._h.value if mlp is not None else None
+    sp.mlp_lambda = float(mlp_lambda)
+    sp.mlp_initial_guess = int(bool(mlp_initial_guess))
     return sp
 
 
@@ -470,3 +488,82 @@ class Batch:
         self.ctx.check(lib().rbf_batch_autotune(self._h, _ptr(b), ctypes.byref(sp), cand, len(candidates),
                                                 ctypes.byref(best), scores, _stream(stream)), "rbf_batch_autotune")
         return int(best.value), list(scores)
+
+
+class MLP:
+    """The learned block preconditioner's network on the device (rbf_mlp_*)."""
+
+    def __init__(self, ctx: Context, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != MLP_NPARAMS:
+            raise ValueError(f"expected {MLP_NPARAMS} parameters, got {p.size}")
+        self.ctx = ctx
+        self._h = ctypes.c_void_p()
+        ctx.check(lib().rbf_mlp_create(ctx._h, p.ctypes.data_as(ctypes.c_void_p), ctypes.byref(self._h)),
+                  "rbf_mlp_create")
+
+    def close(self):
+        if self._h:
+            lib().rbf_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        import numpy as np
+        out = np.empty(MLP_NPARAMS, dtype=np.float32)
+        self.ctx.check(lib().rbf_mlp_get_params(self._h, out.ctypes.data_as(ctypes.c_void_p)), "rbf_mlp_get_params")
+        return out
+
+    def forward(self, X, bf16=True, stream=None):
+        import torch
+        _req(X, torch.float32, "X")
+        rows = X.numel() // 256
+        Y = torch.empty((rows, 64), dtype=torch.float32, device=X.device)
+        self.ctx.check(lib().rbf_mlp_forward(self._h, _ptr(X), rows, _ptr(Y), int(bool(bf16)), _stream(stream)),
+                       "rbf_mlp_forward")
+        return Y
+
+    def loss_grad(self, X, T, grad=True, stream=None):
+        import numpy as np
+        import torch
+        _req(X, torch.float32, "X")
+        _req(T, torch.float32, "T")
+        rows = X.numel() // 256
+        loss = ctypes.c_double(0)
+        g = np.empty(MLP_NPARAMS, dtype=np.float32) if grad else None
+        self.ctx.check(lib().rbf_mlp_loss_grad(self._h, _ptr(X), _ptr(T), rows, ctypes.byref(loss),
+                                               g.ctypes.data_as(ctypes.c_void_p) if grad else None, _stream(stream)),
+                       "rbf_mlp_loss_grad")
+        return loss.value, g
+
+    def train(self, X, T, epochs=10, batch=1024, lr=1e-3, stream=None):
+        import numpy as np
+        import torch
+        _req(X, torch.float32, "X")
+        _req(T, torch.float32, "T")
+        ns = X.numel() // 256
+        hist = np.zeros(epochs)
+        tp = TrainParams(int(epochs), int(batch), float(lr))
+        self.ctx.check(lib().rbf_mlp_train(self._h, _ptr(X), _ptr(T), ns, ctypes.byref(tp),
+                                           hist.ctypes.data_as(ctypes.c_void_p), _stream(stream)), "rbf_mlp_train")
+        return hist
+
+
+def mlp_make_data(plan: Plan, lam: float, block_ids, R, stream=None):
+    """Features X (ns x 256) and exact targets Y (ns x 64) on the plan's 64-centre blocks."""
+    import torch
+    _req(block_ids, torch.int32, "block_ids")
+    _req(R, torch.float32, "R")
+    ns = block_ids.numel()
+    X = torch.empty((ns, 256), dtype=torch.float32, device=R.device)
+    Y = torch.empty((ns, 64), dtype=torch.float32, device=R.device)
+    f = ctypes.c_int64(0)
+    plan.ctx.check(lib().rbf_mlp_make_data(plan._h, ctypes.c_float(lam), _ptr(block_ids), _ptr(R), ns, _ptr(X),
+                                           _ptr(Y), ctypes.byref(f), _stream(stream)), "rbf_mlp_make_data")
+    return X, Y, int(f.value)

@@ -270,8 +270,9 @@ rbf_status rbf_plan_solve(rbf_plan *P, const float *b, const rbf_solve_params *p
     if (!P) return RBF_ERR_INVALID;
     return guarded(P->ctx, [&]() {
         RBF_CHECK(b && p && x, RBF_ERR_INVALID, "null pointer argument");
-        RBF_CHECK(p->precond == RBF_PRECOND_NONE || p->precond == RBF_PRECOND_SCHWARZ, RBF_ERR_INVALID,
-                  "unknown preconditioner %d", p->precond);
+        RBF_CHECK(p->precond == RBF_PRECOND_NONE || p->precond == RBF_PRECOND_SCHWARZ ||
+                      p->precond == RBF_PRECOND_MLP,
+                  RBF_ERR_INVALID, "unknown preconditioner %d", p->precond);
         RBF_CHECK(std::isfinite(p->tol) && p->tol >= 0, RBF_ERR_INVALID, "tol must be finite and >= 0");
         RBF_CHECK(p->residual_mode == RBF_RESIDUAL_DF || p->residual_mode == RBF_RESIDUAL_F64, RBF_ERR_INVALID,
                   "unknown residual mode %d", p->residual_mode);
@@ -328,6 +329,83 @@ rbf_status rbf_eval_grid(rbf_ctx *ctx, const float *centers, const double *weigh
         }
         cudaStreamSynchronize(S(stream));
         delete P;
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_mlp_create(rbf_ctx *ctx, const float *host_params, rbf_mlp **mlp) {
+    if (mlp) *mlp = nullptr;
+    return guarded(ctx, [&]() {
+        RBF_CHECK(host_params && mlp, RBF_ERR_INVALID, "null pointer argument");
+        *mlp = mlp_create(ctx, host_params, 0);
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_mlp_destroy(rbf_mlp *mlp) {
+    if (mlp) mlp_destroy(mlp);
+    return RBF_OK;
+}
+
+rbf_status rbf_mlp_get_params(rbf_mlp *mlp, float *host_params) {
+    if (!mlp) return RBF_ERR_INVALID;
+    return guarded(mlp_ctx(mlp), [&]() {
+        RBF_CHECK(host_params, RBF_ERR_INVALID, "null pointer argument");
+        mlp_get_params(mlp, host_params, 0);
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_mlp_make_data(rbf_plan *plan, float lambda, const int32_t *block_ids, const float *R, int64_t ns,
+                             float *X, float *Y, int64_t *failed, void *stream) {
+    if (!plan) return RBF_ERR_INVALID;
+    return guarded(plan->ctx, [&]() {
+        RBF_CHECK(block_ids && R && X && Y && ns >= 0, RBF_ERR_INVALID, "null pointer argument");
+        int64_t f = mlp_make_data(plan, lambda, block_ids, R, ns, X, Y, S(stream));
+        if (failed) *failed = f;
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_mlp_forward(rbf_mlp *mlp, const float *X, int64_t rows, float *Y, int use_bf16, void *stream) {
+    if (!mlp) return RBF_ERR_INVALID;
+    return guarded(mlp_ctx(mlp), [&]() {
+        RBF_CHECK(X && Y && rows >= 0, RBF_ERR_INVALID, "null pointer argument");
+        mlp_forward(mlp, X, rows, Y, use_bf16, S(stream));
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_mlp_loss_grad(rbf_mlp *mlp, const float *X, const float *T, int64_t rows, double *loss,
+                             float *host_grad, void *stream) {
+    if (!mlp) return RBF_ERR_INVALID;
+    return guarded(mlp_ctx(mlp), [&]() {
+        RBF_CHECK(X && T && loss && rows > 0 && rows <= 65536, RBF_ERR_INVALID, "bad arguments");
+        *loss = mlp_loss_grad(mlp, X, T, (int)rows, host_grad != nullptr, S(stream));
+        if (host_grad) mlp_get_grad(mlp, host_grad, S(stream));
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_mlp_train(rbf_mlp *mlp, const float *X, const float *T, int64_t ns, const rbf_train_params *p,
+                         double *loss_history, void *stream) {
+    if (!mlp) return RBF_ERR_INVALID;
+    return guarded(mlp_ctx(mlp), [&]() {
+        RBF_CHECK(X && T && p && ns > 0 && p->epochs > 0 && p->batch > 0 && p->batch <= 65536 && p->lr > 0.f,
+                  RBF_ERR_INVALID, "bad training arguments");
+        cudaStream_t s = S(stream);
+        for (int e = 0; e < p->epochs; ++e) {
+            double sum = 0.0;
+            int64_t nb = 0;
+            for (int64_t r0 = 0; r0 < ns; r0 += p->batch) {
+                const int rows = (int)std::min<int64_t>(p->batch, ns - r0);
+                sum += mlp_loss_grad(mlp, X + r0 * RBF_MLP_IN, T + r0 * RBF_MLP_OUT, rows, true, s);
+                mlp_adam_step(mlp, p->lr, s);
+                ++nb;
+            }
+            if (loss_history) loss_history[e] = sum / (double)nb;
+        }
+        RBF_CUDA(cudaStreamSynchronize(s));
         return RBF_OK;
     });
 }

@@ -111,6 +111,11 @@ __global__ void k_b_minus(const float *__restrict__ b, const float *__restrict__
     if (i < n) r[i] = (double)b[i] - (double)y[i];
 }
 
+__global__ void k_f32_to_f64(const float *__restrict__ a, double *__restrict__ b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (double)a[i];
+}
+
 __global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (float)a[i];
@@ -199,6 +204,16 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
         int64_t failed = 0;
         schwarz_setup(P, p.schwarz, &failed, s);
         R.precond_failed_blocks = (int)failed;
+    } else if (p.precond == RBF_PRECOND_MLP) {
+        RBF_CHECK(p.mlp && p.mlp_lambda > 0.f, RBF_ERR_INVALID, "MLP preconditioner needs a network and lambda > 0");
+        rbf_schwarz_params fb{};
+        fb.core = 64;
+        fb.block = 64;
+        fb.shift = p.mlp_lambda;
+        fb.restricted = 1;
+        fb.escalate = 1;
+        int64_t failed = 0;
+        schwarz_setup(P, fb, &failed, s);   // the fallback of blocks with a non-finite output
     }
     cudaEventRecord(tm_setup.b, s);
     cudaEventRecord(tm_solve.a, s);
@@ -227,13 +242,22 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
     RBF_CUDA(cudaMemcpyAsync(&bnorm2, scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
     RBF_CUDA(cudaStreamSynchronize(s));
     const double bnorm = std::sqrt(bnorm2);
+    int64_t mlp_fallbacks = 0;
+    bool x_nonzero = false;
+    if (p.precond == RBF_PRECOND_MLP && p.mlp_initial_guess && bnorm > 0) {
+        // x0 = network applied to b; then r0 = b - A~ x0 in float64
+        mlp_fallbacks += mlp_apply(p.mlp, P, p.mlp_lambda, 64, r.p, w32.p, s);
+        k_f32_to_f64<<<g1(n), kThreads, 0, s>>>(w32.p, x.p, n);
+        RBF_LAUNCHED();
+        x_nonzero = true;
+    }
 
     Intervals t_mv, t_res, t_pc;
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hcol(m + 2), yh(m), hbuf(3 * (m + 1));
     int it = 0, cycles = 0;
     double beta = bnorm, est = 1.0, true_rel = bnorm > 0 ? 1.0 : 0.0;
     bool converged = bnorm == 0.0, breakdown = false;
-    bool have_true = true;   // r holds b - A~ x for the current x
+    bool have_true = !x_nonzero;   // r holds b - A~ x for the current x
 
     while (!converged && it < max_it && !breakdown) {
         if (!have_true) {
@@ -276,6 +300,10 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
             if (p.precond == RBF_PRECOND_SCHWARZ) {
                 t_pc.begin(s);
                 schwarz_apply_binned(P, Vj, nullptr, Zj, s);
+                t_pc.end(s);
+            } else if (p.precond == RBF_PRECOND_MLP) {
+                t_pc.begin(s);
+                mlp_fallbacks += mlp_apply(p.mlp, P, p.mlp_lambda, 64, Vj, Zj, s);
                 t_pc.end(s);
             } else {
                 k_to_f32<<<g1(n), kThreads, 0, s>>>(Vj, Zj, n);
@@ -368,6 +396,7 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
     float ms_a = 0, ms_b = 0;
     cudaEventElapsedTime(&ms_a, tm_setup.a, tm_setup.b);
     cudaEventElapsedTime(&ms_b, tm_solve.a, tm_solve.b);
+    if (p.precond == RBF_PRECOND_MLP) R.precond_failed_blocks = (int)mlp_fallbacks;
     R.iterations = it;
     R.restarts = cycles;
     R.converged = converged ? 1 : 0;

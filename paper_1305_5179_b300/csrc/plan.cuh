@@ -75,6 +75,9 @@ struct rbf_plan {
 
     SchwarzData sz;
     GridCache grid;
+    // learned preconditioner work space
+    PBuf<float> mlp_x, mlp_y, mlp_n;
+    PBuf<int32_t> mlp_bad;
 };
 
 // plan.cu
@@ -131,6 +134,20 @@ void batch_destroy(rbf_batch *Bt);
 rbf_ctx *batch_ctx(rbf_batch *Bt);
 void batch_gather_f32(rbf_batch *Bt, const float *in, float *out, cudaStream_t s);
 void batch_scatter_f32(rbf_batch *Bt, const float *in, float *out, cudaStream_t s);
+
+// mlp.cu
+int64_t mlp_nparams();
+rbf_mlp *mlp_create(rbf_ctx *ctx, const float *host_params, cudaStream_t s);
+void mlp_destroy(rbf_mlp *M);
+rbf_ctx *mlp_ctx(rbf_mlp *M);
+void mlp_get_params(rbf_mlp *M, float *host, cudaStream_t s);
+void mlp_get_grad(rbf_mlp *M, float *host, cudaStream_t s);
+void mlp_forward(rbf_mlp *M, const float *X, int64_t rows, float *Y, int bf16, cudaStream_t s);
+double mlp_loss_grad(rbf_mlp *M, const float *X, const float *T, int rows, bool want_grad, cudaStream_t s);
+void mlp_adam_step(rbf_mlp *M, float lr, cudaStream_t s);
+int64_t mlp_make_data(rbf_plan *P, float lambda, const int32_t *block_ids, const float *R, int64_t ns, float *X,
+                      float *Y, cudaStream_t s);
+int64_t mlp_apply(rbf_mlp *M, rbf_plan *P, float lambda, int core, const double *vd, float *z, cudaStream_t s);
 
 // fgmres.cu
 rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_params &p, double *x_caller,

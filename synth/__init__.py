@@ -36,8 +36,11 @@ import numpy as np
 
 __all__ = [
     "sphere", "torus", "ellipsoid", "metaball", "batch", "halton",
-    "Cloud", "lattice", "mean_nn_spacing",
+    "Cloud", "lattice", "mean_nn_spacing", "mlp_init", "MLP_SIZES",
 ]
+
+# layer sizes of the learned block preconditioner (inputs, hidden, hidden, outputs)
+MLP_SIZES = (256, 256, 256, 64)
 
 
 @dataclass
@@ -263,3 +266,18 @@ def halton(n: int, bases=(2, 3), start: int = 1) -> np.ndarray:
                 k //= b
             out[i, d] = r
     return out
+
+
+def mlp_init(seed: int = 0, sizes=MLP_SIZES, last_scale: float = 0.1) -> np.ndarray:
+    """Seeded initial weights, He-normal (std sqrt(2 / fan_in)) with zero biases,
+    the output layer scaled by ``last_scale`` (the network starts near its skip
+    connection), packed layer by layer as W[out][in] row-major followed by b[out];
+    float32."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    nl = len(sizes) - 1
+    for li, (fin, fout) in enumerate(zip(sizes[:-1], sizes[1:])):
+        sc = math.sqrt(2.0 / fin) * (last_scale if li == nl - 1 else 1.0)
+        parts.append((rng.standard_normal((fout, fin)) * sc).ravel())
+        parts.append(np.zeros(fout))
+    return np.ascontiguousarray(np.concatenate(parts), dtype=np.float32)

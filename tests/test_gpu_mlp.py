@@ -1,0 +1,119 @@
+"""Learned block preconditioner: data generation, forward, gradient and training
+kernels against the FP64 oracle, and FGMRES with the trained network."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F32 = np.float32
+LAM = 1e-2
+
+
+@pytest.fixture(scope="module")
+def rbf():
+    import paper_1305_5179_b300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(rbf):
+    return rbf.Context(0)
+
+
+@pytest.fixture(scope="module")
+def patch(rbf, ctx):
+    """A sector of the 1,000,000-point torus at full density, delta 0.01, sigma 0.02."""
+    theta = 0.06
+    cl = synth.torus(int(1_000_000 * theta / (2 * math.pi)), noise=1e-3, seed=21, theta_max=theta)
+    C, b = oracle.build_centers(cl.points, cl.normals, 0.01)
+    C32 = np.zeros((len(C), 4), dtype=np.float32)
+    C32[:, :3] = C
+    plan = rbf.Plan(ctx, torch.from_numpy(C32).cuda(), sigma=0.02, k=6.0)
+    perm = plan.export_binning()[0].cpu().numpy()
+    return plan, C32[:, :3].astype(np.float64)[perm], b.astype(np.float32), C32
+
+
+def _samples(nblocks, ns, seed):
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, nblocks, ns).astype(np.int32), rng.standard_normal((ns, 64)).astype(np.float32)
+
+
+def test_training_data_matches_oracle(rbf, patch):
+    plan, Cs, _, _ = patch
+    nblocks = len(Cs) // 64
+    bid, R = _samples(nblocks, 64, 1)
+    X, Y, failed = rbf.mlp_make_data(plan, LAM, torch.from_numpy(bid).cuda(), torch.from_numpy(R).cuda())
+    assert failed == 0
+    Xo, Yo = oracle.mlp_block_data(Cs, float(F32(0.02)), float(F32(LAM)), bid, R)
+    assert np.abs(X.cpu().numpy() - Xo).max() <= 1e-5 * np.abs(Xo).max()
+    assert np.linalg.norm(Y.cpu().numpy() - Yo) <= 1e-5 * np.linalg.norm(Yo)
+
+
+def test_forward_and_gradient_match_oracle(rbf, ctx):
+    rng = np.random.default_rng(2)
+    params = synth.mlp_init(seed=7)
+    X = rng.standard_normal((300, 256)).astype(np.float32)
+    T = (0.1 * rng.standard_normal((300, 64))).astype(np.float32)
+    net = rbf.MLP(ctx, params)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    y32 = net.forward(Xd, bf16=False).cpu().numpy()
+    yo = oracle.mlp_forward(params, X)
+    assert np.linalg.norm(y32 - yo) <= 1e-5 * np.linalg.norm(yo)
+    # BF16 inference weights: compare with the oracle on the BF16-rounded weights
+    pb = torch.from_numpy(params).to(torch.bfloat16).float().numpy()
+    yb = net.forward(Xd, bf16=True).cpu().numpy()
+    assert np.linalg.norm(yb - oracle.mlp_forward(pb, X)) <= 1e-4 * np.linalg.norm(yo)
+    loss, g = net.loss_grad(Xd, Td)
+    lo, go = oracle.mlp_loss_grad(params, X, T)
+    assert loss == pytest.approx(lo, rel=1e-5)
+    o = 0
+    for fin, fout in zip((256, 256, 256), (256, 256, 64)):
+        for size in (fin * fout, fout):
+            assert np.linalg.norm(g[o:o + size] - go[o:o + size]) <= 1e-4 * np.linalg.norm(go[o:o + size]) + 1e-12
+            o += size
+
+
+def test_training_reduces_the_loss(rbf, ctx, patch):
+    plan, Cs, _, _ = patch
+    nblocks = len(Cs) // 64
+    bid, R = _samples(nblocks, 8192, 3)
+    X, Y, _ = rbf.mlp_make_data(plan, LAM, torch.from_numpy(bid).cuda(), torch.from_numpy(R).cuda())
+    net = rbf.MLP(ctx, synth.mlp_init(seed=1))
+    l0, _ = net.loss_grad(X[:4096].contiguous(), Y[:4096].contiguous(), grad=False)
+    hist = net.train(X, Y, epochs=15, batch=512, lr=1e-3)
+    l1, _ = net.loss_grad(X[:4096].contiguous(), Y[:4096].contiguous(), grad=False)
+    zero = float((Y[:4096] ** 2).mean())
+    ident = float(((Y[:4096] - X[:4096, 192:]) ** 2).mean())     # rho itself as the prediction
+    assert np.all(np.isfinite(hist))
+    # measured on B300: l0 0.207, l1 0.101, zero predictor 0.725, identity (rho) 0.193
+    assert l1 < 0.6 * l0 and l1 < 0.25 * zero and l1 < 0.75 * ident, (l0, l1, zero, ident)
+
+
+def test_fgmres_with_learned_preconditioner(rbf, ctx, patch, capsys):
+    plan, Cs, b, C32 = patch
+    nblocks = len(Cs) // 64
+    bid, R = _samples(nblocks, 16384, 4)
+    X, Y, _ = rbf.mlp_make_data(plan, LAM, torch.from_numpy(bid).cuda(), torch.from_numpy(R).cuda())
+    net = rbf.MLP(ctx, synth.mlp_init(seed=1))
+    net.train(X, Y, epochs=20, batch=512, lr=1e-3)
+    bd = torch.from_numpy(b).cuda()
+    res = {}
+    for name, kw in [("none", dict(precond="none")),
+                     ("ras64", dict(precond="schwarz", core=64, block=64, shift=LAM)),
+                     ("mlp", dict(precond="mlp", mlp=net, mlp_lambda=LAM)),
+                     ("mlp+x0", dict(precond="mlp", mlp=net, mlp_lambda=LAM, mlp_initial_guess=True))]:
+        x, rep = plan.solve(bd, m=20, max_it=40, fixed_iterations=True, **kw)
+        r = oracle.residual_rows(C32[:, :3].astype(np.float64), b.astype(np.float64), x.cpu().numpy(),
+                                 float(F32(0.02)), 6.0)
+        true = np.linalg.norm(r) / np.linalg.norm(b)
+        assert rep["residual_true"] == pytest.approx(true, rel=1e-6)
+        res[name] = (rep["residual_true"], rep["ms_solve"], rep["precond_failed_blocks"])
+    with capsys.disabled():
+        print("\n  residual after 40 FGMRES iterations (true, ms, fallback blocks):", res)
+    assert all(np.isfinite(v[0]) for v in res.values())

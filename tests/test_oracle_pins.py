@@ -389,3 +389,49 @@ def test_fgmres_flexible_preconditioner_changes_nothing_at_convergence():
         return v / np.diag(A) * (1.0 + 0.1 * (cnt[0] % 3))
     x, it, hist = oracle.fgmres(lambda v: A @ v, b, prec, m=40, tol=1e-12)
     assert np.allclose(A @ x, b, rtol=1e-9, atol=1e-9)
+
+
+# ------------------------------------------------------- learned preconditioner
+def test_mlp_forward_hand_computed():
+    """A 2-3-2-1 network with chosen weights, evaluated by hand."""
+    sizes = (2, 3, 2, 1)
+    W1 = np.array([[1.0, -1.0], [0.5, 0.5], [-2.0, 0.0]]); b1 = np.array([0.0, 1.0, 0.5])
+    W2 = np.array([[1.0, 1.0, 1.0], [0.0, -1.0, 2.0]]); b2 = np.array([-1.0, 0.0])
+    W3 = np.array([[3.0, -1.0]]); b3 = np.array([0.25])
+    p = np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3.ravel(), b3])
+    x = np.array([[2.0, 1.0]])
+    # h1 = relu([1, 2.5, -3.5]) = [1, 2.5, 0]; h2 = relu([2.5, -2.5]) = [2.5, 0]; y = 7.5 + 0.25
+    assert oracle.mlp_forward(p, x, sizes, skip=False)[0, 0] == pytest.approx(7.75)
+    # the skip connection adds the last input to the (single) output
+    assert oracle.mlp_forward(p, x, sizes, skip=True)[0, 0] == pytest.approx(8.75)
+
+
+def test_mlp_gradient_matches_finite_differences():
+    rng = np.random.default_rng(3)
+    sizes = (6, 5, 4, 3)
+    p = synth.mlp_init(seed=4, sizes=sizes).astype(np.float64) + 0.05 * rng.standard_normal(
+        sum(a * b + b for a, b in zip(sizes[:-1], sizes[1:])))
+    X = rng.standard_normal((7, 6))
+    T = rng.standard_normal((7, 3))
+    loss, g = oracle.mlp_loss_grad(p, X, T, sizes)
+    assert loss == pytest.approx(np.mean((oracle.mlp_forward(p, X, sizes) - T) ** 2))
+    assert not np.allclose(oracle.mlp_forward(p, X, sizes), oracle.mlp_forward(p, X, sizes, skip=False))
+    for idx in rng.choice(len(p), 25, replace=False):
+        e = np.zeros_like(p)
+        e[idx] = 1e-6
+        fd = (oracle.mlp_loss_grad(p + e, X, T, sizes)[0] - oracle.mlp_loss_grad(p - e, X, T, sizes)[0]) / 2e-6
+        assert g[idx] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+
+
+def test_mlp_block_targets_solve_the_shifted_block():
+    """(A_i + lam I) Y / lam = r/|r| with A_i rebuilt by the dense-matrix routine."""
+    rng = np.random.default_rng(5)
+    Cs = rng.uniform(0, 0.3, (200, 3))
+    R = rng.standard_normal((3, 64))
+    X, Y = oracle.mlp_block_data(Cs, 0.05, 1e-3, [0, 2, 3], R)
+    for row, (bi, r) in enumerate(zip([0, 2, 3], R)):
+        d0 = min(bi * 64, 200 - 64)
+        A = oracle.dense_matrix(Cs[d0:d0 + 64], 0.05) + 1e-3 * np.eye(64)
+        assert np.allclose(A @ Y[row] / 8e-3, r / np.linalg.norm(r), atol=1e-9)
+        assert np.allclose(X[row, 192:], 8 * r / np.linalg.norm(r))
+        assert np.allclose(X[row, :192].reshape(64, 3).mean(0), 0, atol=1e-12)
