@@ -39,7 +39,7 @@ UNIT = "pair-evals/s"
 
 WORKLOADS = {
     "torus1m": dict(desc="torus R=1 r=0.35 noise 1e-3, N=1,000,000 points -> 3,000,000 centres",
-                    N=1_000_000, delta=0.01, sigma=0.02, k=6.0, grid=256, core=96, block=128, shift=1e-4,
+                    N=1_000_000, delta=0.01, sigma=0.02, k=6.0, grid=256, core=96, block=128, shift=1.0,
                     iters=50, m=50, precond="schwarz"),
     "sphere1500": dict(desc="unit sphere N=1,500 -> 4,500 centres, untruncated", N=1500, delta=0.05, sigma=0.1,
                        k=0.0, grid=64, core=96, block=128, shift=1e-4, iters=50, m=50, precond="none"),

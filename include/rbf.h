@@ -54,7 +54,8 @@ typedef enum {
     RBF_ERR_CUDA = 3,           /* a CUDA runtime call or kernel launch failed */
     RBF_ERR_NOT_CONVERGED = 4,  /* solver stopped at its iteration cap above tolerance (weights still valid) */
     RBF_ERR_BREAKDOWN = 5,      /* Arnoldi produced a non-finite value */
-    RBF_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired */
+    RBF_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired (reported by the next call on the
+                                   context that launches a product or synchronises) */
     RBF_ERR_NOT_SPD = 7,        /* a block factorisation failed even after the shift escalation */
     RBF_ERR_UNSUPPORTED = 8     /* configuration outside the implemented range (message says which) */
 } rbf_status;
@@ -117,7 +118,15 @@ typedef struct {
     float k;                /* cut-off factor: pairs with |d| < k sigma; 0 = untruncated */
     int cells_per_cutoff;   /* s in hc = k sigma / s; 0 selects 1 */
     int levels;             /* fine levels per cell (0..7); -1 selects 3 */
+    int product;            /* kernel of the float32 product and grid evaluation: RBF_PRODUCT_TC (0) or
+                               RBF_PRODUCT_SIMT (1); both compute the same sum (see rbf_matvec) */
 } rbf_plan_params;
+
+enum {
+    RBF_PRODUCT_TC = 0,     /* exponents -|u - v|^2 of a 128 x 32 tile by tcgen05.mma (tf32 head + tail
+                               split, ~22 bits), exp2 and the sum on the CUDA cores */
+    RBF_PRODUCT_SIMT = 1    /* everything on the CUDA cores (packed float32 FMA) */
+};
 
 typedef struct {
     int64_t n;              /* centres */

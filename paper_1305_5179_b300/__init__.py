@@ -52,7 +52,10 @@ class RbfError(RuntimeError):
 
 class PlanParams(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_float), ("k", ctypes.c_float), ("cells_per_cutoff", ctypes.c_int),
-                ("levels", ctypes.c_int)]
+                ("levels", ctypes.c_int), ("product", ctypes.c_int)]
+
+
+PRODUCTS = {"tc": 0, "simt": 1}
 
 
 class PlanInfo(ctypes.Structure):
@@ -273,7 +276,7 @@ class Plan:
     """The matrix-free truncated Gaussian operator over a fixed set of centres."""
 
     def __init__(self, ctx: Context, centers, sigma: float, k: float = 0.0, cells_per_cutoff: int = 1,
-                 levels: int = 3, stream=None):
+                 levels: int = 3, product: str = "tc", stream=None):
         import torch
         _req(centers, torch.float32, "centers")
         if centers.dim() != 2 or centers.shape[1] != 4:
@@ -281,7 +284,7 @@ class Plan:
         self.ctx = ctx
         self.n = int(centers.shape[0])
         self.device = centers.device
-        self.params = PlanParams(float(sigma), float(k), int(cells_per_cutoff), int(levels))
+        self.params = PlanParams(float(sigma), float(k), int(cells_per_cutoff), int(levels), PRODUCTS[product])
         self._h = ctypes.c_void_p()
         ctx.check(lib().rbf_plan_create(ctx._h, _ptr(centers), self.n, ctypes.byref(self.params),
                                         ctypes.byref(self._h), _stream(stream)), "rbf_plan_create")
@@ -385,13 +388,13 @@ class Plan:
         return f
 
 
-def solve(ctx: Context, centers, targets, sigma: float, k: float = 0.0, stream=None, **kw):
+def solve(ctx: Context, centers, targets, sigma: float, k: float = 0.0, product: str = "tc", stream=None, **kw):
     """One-shot step 2 (plan + FGMRES + free)."""
     import torch
     _req(centers, torch.float32, "centers")
     n = centers.shape[0]
     _req(targets, torch.float32, "targets", n)
-    pp = PlanParams(float(sigma), float(k), 1, 3)
+    pp = PlanParams(float(sigma), float(k), 1, 3, PRODUCTS[product])
     x = torch.empty(n, dtype=torch.float64, device=centers.device)
     rep = Report()
     sp = _solve_params(**kw)
@@ -403,13 +406,14 @@ def solve(ctx: Context, centers, targets, sigma: float, k: float = 0.0, stream=N
     return x, d
 
 
-def eval_grid(ctx: Context, centers, weights, sigma: float, k: float, lo, hi, dims, stream=None):
+def eval_grid(ctx: Context, centers, weights, sigma: float, k: float, lo, hi, dims, product: str = "tc",
+              stream=None):
     """One-shot step 3."""
     import torch
     _req(centers, torch.float32, "centers")
     n = centers.shape[0]
     _req(weights, torch.float64, "weights", n)
-    pp = PlanParams(float(sigma), float(k), 1, 3)
+    pp = PlanParams(float(sigma), float(k), 1, 3, PRODUCTS[product])
     f = torch.empty((int(dims[2]), int(dims[1]), int(dims[0])), dtype=torch.float32, device=centers.device)
     g = _grid(lo, hi, dims)
     ctx.check(lib().rbf_eval_grid(ctx._h, _ptr(centers), _ptr(weights), n, ctypes.byref(pp), ctypes.byref(g), _ptr(f),

@@ -48,7 +48,22 @@ void check_plan_params(const rbf_plan_params *p) {
     RBF_CHECK(std::isfinite(p->k) && p->k >= 0.f && p->k <= 12.f, RBF_ERR_INVALID, "k must be in [0, 12]");
     RBF_CHECK(p->cells_per_cutoff >= 0 && p->cells_per_cutoff <= 4, RBF_ERR_INVALID, "cells_per_cutoff in 0..4");
     RBF_CHECK(p->levels >= -1 && p->levels <= 7, RBF_ERR_INVALID, "levels in -1..7");
+    RBF_CHECK(p->product == RBF_PRODUCT_TC || p->product == RBF_PRODUCT_SIMT, RBF_ERR_INVALID,
+              "product must be RBF_PRODUCT_TC or RBF_PRODUCT_SIMT");
 }
+
+}  // namespace
+
+unsigned *ctx_error_word(rbf_ctx *ctx) { return ctx->err_dev; }
+
+void ctx_check_device_error(rbf_ctx *ctx) {
+    if (ctx->err_host && *(volatile unsigned *)ctx->err_host) {
+        *(volatile unsigned *)ctx->err_host = 0u;
+        rbf_fail(RBF_ERR_TIMEOUT, "a bounded wait inside a product kernel expired (results of that launch invalid)");
+    }
+}
+
+namespace {
 
 rbf_plan *make_plan(rbf_ctx *ctx, const float *centers, int64_t n, const rbf_plan_params *p, cudaStream_t s) {
     check_plan_params(p);
@@ -62,6 +77,7 @@ rbf_plan *make_plan(rbf_ctx *ctx, const float *centers, int64_t n, const rbf_pla
         P->k = p->k;
         P->cells_per_cutoff = p->cells_per_cutoff > 0 ? p->cells_per_cutoff : 1;
         P->levels = p->levels >= 0 ? p->levels : 3;
+        P->product = p->product;
         plan_build(P, (const float4 *)centers, s);
     } catch (...) {
         delete P;
@@ -105,16 +121,21 @@ rbf_status rbf_ctx_create(rbf_ctx **ctx, int device) {
     if (!c) return RBF_ERR_OOM;
     c->device = device;
     if (cudaSetDevice(device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaHostAlloc((void **)&c->err_host, sizeof(unsigned), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&c->err_dev, c->err_host, 0) != cudaSuccess) {
+        if (c->err_host) cudaFreeHost(c->err_host);
         (void)cudaGetLastError();
         delete c;
         return RBF_ERR_CUDA;
     }
+    *c->err_host = 0u;
     *ctx = c;
     return RBF_OK;
 }
 
 rbf_status rbf_ctx_destroy(rbf_ctx *ctx) {
+    if (ctx && ctx->err_host) cudaFreeHost(ctx->err_host);
     delete ctx;
     return RBF_OK;
 }

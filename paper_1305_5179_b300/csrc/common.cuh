@@ -15,7 +15,16 @@ struct rbf_ctx {
     int device = 0;
     int num_sms = 148;
     std::string last_error;
+    // Device error word in pinned, mapped host memory: kernels with bounded waits
+    // set it when a wait expires; the host reads it without a copy.
+    unsigned *err_host = nullptr;
+    unsigned *err_dev = nullptr;
 };
+
+// The context's device error word (device pointer), and the host-side check that
+// turns a raised word into RBF_ERR_TIMEOUT (clearing it).
+unsigned *ctx_error_word(rbf_ctx *ctx);
+void ctx_check_device_error(rbf_ctx *ctx);
 
 // ------------------------------------------------------------------ errors
 struct RbfError {

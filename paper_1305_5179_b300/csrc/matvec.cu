@@ -140,6 +140,7 @@ MvArgs base_args(const rbf_plan *P, const PairList &pl, const float *w, float *o
     a.blk = P->blk.p;
     a.blk_c = P->blk_c.p;
     a.ent = pl.ent.p;
+    a.ebi = pl.ebi.p;
     a.seg = pl.seg.p;
     a.n = P->n;
     a.scl = P->scl;
@@ -155,7 +156,10 @@ void matvec_binned(rbf_plan *P, const float *zs, float *ys, cudaStream_t s) {
     const PairList &pl = P->pl;
     if (pl.any_split) P->partial.ensure((size_t)pl.nseg * kChunk, s);
     MvArgs a = base_args(P, pl, zs, ys, P->partial.p);
-    if (pl.nseg > 0) {
+    ctx_check_device_error(P->ctx);
+    if (P->product == RBF_PRODUCT_TC) {
+        product_tc_launch(P, pl, a, false, s);
+    } else if (pl.nseg > 0) {
         k_matvec_f32<false><<<(unsigned)pl.nseg, kWarps * 32, 0, s>>>(a);
         RBF_LAUNCHED();
     }
@@ -192,7 +196,10 @@ void matvec_grid_launch(rbf_plan *P, const PairList &pl, const float *ws, const 
         a.gdim[d] = (int)g.dims[d];
         a.bdim[d] = (int)bricks[d];
     }
-    if (pl.nseg > 0) {
+    ctx_check_device_error(P->ctx);
+    if (P->product == RBF_PRODUCT_TC) {
+        product_tc_launch(P, pl, a, true, s);
+    } else if (pl.nseg > 0) {
         k_matvec_f32<true><<<(unsigned)pl.nseg, kWarps * 32, 0, s>>>(a);
         RBF_LAUNCHED();
     }

@@ -432,6 +432,18 @@ void permute_from_binned_f64(const rbf_plan *P, const double *in, double *out, c
     RBF_LAUNCHED();
 }
 
+namespace {
+// Each entry's block as (start, count | cut-off flag): one load per block in the tensor-core product.
+__global__ void k_pl_expand(const int32_t *__restrict__ ent, const int2 *__restrict__ blk, int64_t len,
+                            int2 *__restrict__ ebi) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= len) return;
+    const int v = ent[e];
+    const int2 b = blk[v & 0x7fffffff];
+    ebi[e] = make_int2(b.x, b.y | (v & (int)0x80000000));
+}
+}  // namespace
+
 void build_pairlist(rbf_plan *P, const float4 *tlo, const float4 *thi, int64_t ntiles, PairList &pl,
                     cudaStream_t s) {
     CellGridArgs g;
@@ -462,6 +474,11 @@ void build_pairlist(rbf_plan *P, const float4 *tlo, const float4 *thi, int64_t n
     k_pl_fill<<<wgrid, kThreads, 0, s>>>(g, tlo, thi, ntiles, P->cell_blk.p, P->blk_lo.p, P->blk_hi.p, pl.off.p,
                                          pl.ent.p);
     RBF_LAUNCHED();
+    pl.ebi.alloc(std::max<int64_t>(len, 1), s);
+    if (len > 0) {
+        k_pl_expand<<<grid_for(len), kThreads, 0, s>>>(pl.ent.p, P->blk.p, len, pl.ebi.p);
+        RBF_LAUNCHED();
+    }
 
     // segments: enough independent work items to fill every SM several times, and no
     // segment much longer than the average tile (a tile whose box straddles a jump of

@@ -18,6 +18,7 @@ struct PairList {
     bool any_split = false;      // some tile has more than one segment
     PBuf<int32_t> off;           // ntiles + 1
     PBuf<int32_t> ent;           // len; bit 31 set = pair-wise cut-off test needed
+    PBuf<int2> ebi;              // len; (start, count | bit 31 of ent) of the entry's block
     PBuf<int4> seg;              // (tile, e0, e1, 1 if the tile has this one segment only)
     PBuf<int32_t> tile_seg;      // ntiles + 1: segments of tile t are [tile_seg[t], tile_seg[t+1])
 };
@@ -44,6 +45,7 @@ struct rbf_plan {
     int64_t n = 0;
     float sigma = 0.f, k = 0.f;
     int cells_per_cutoff = 1, levels = 3, nbits = 0;
+    int product = RBF_PRODUCT_TC;   // kernel of the float32 product and grid evaluation
     float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     float inv = 0.f;          // fine cells per unit length
     int cdim = 0;             // cells per axis in the cell table (2^(nbits - levels))

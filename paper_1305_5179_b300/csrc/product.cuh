@@ -43,6 +43,7 @@ struct MvArgs {
     const int2 *blk;
     const float4 *blk_c; // (centre, overflow guard U_B = (32 / r_B)^2 in scaled units)
     const int32_t *ent;
+    const int2 *ebi;     // per entry (block start, count | cut-off flag)
     const int4 *seg;
     int64_t n;
     float scl, R;
@@ -238,3 +239,6 @@ __device__ __forceinline__ void product_segment(const MvArgs &a, const int4 sg, 
 
 
 }  // namespace rbfk
+
+// product_tc.cu: the same product with the exponents from tcgen05.mma (pl.nseg CTAs).
+void product_tc_launch(const rbf_plan *P, const PairList &pl, const rbfk::MvArgs &a, bool grid, cudaStream_t s);

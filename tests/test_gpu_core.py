@@ -125,9 +125,12 @@ def test_binning_bit_exact_ragged_and_duplicates(ctx, rbf, n):
 
 
 # ---------------------------------------------------------------------- product
-def _matvec_check(ctx, rbf, C, sigma, k, rows=None, seeds=(0, 1), tol=1e-5):
+PRODUCTS = pytest.mark.parametrize("product", ["tc", "simt"])
+
+
+def _matvec_check(ctx, rbf, C, sigma, k, rows=None, seeds=(0, 1), tol=1e-5, product="tc"):
     Cd, C64 = c4(C)
-    plan = rbf.Plan(ctx, Cd, sigma=sigma, k=k)
+    plan = rbf.Plan(ctx, Cd, sigma=sigma, k=k, product=product)
     n = len(C)
     for sd in seeds:
         rng = np.random.default_rng(100 + sd)
@@ -139,31 +142,46 @@ def _matvec_check(ctx, rbf, C, sigma, k, rows=None, seeds=(0, 1), tol=1e-5):
     return plan
 
 
-def test_matvec_dense_c1_all_rows(ctx, rbf, sphere_c1):
+@PRODUCTS
+def test_matvec_dense_c1_all_rows(ctx, rbf, sphere_c1, product):
     C, _ = oracle.build_centers(sphere_c1.points, sphere_c1.normals, 0.05)
-    _matvec_check(ctx, rbf, C, 0.1, 0.0)
+    _matvec_check(ctx, rbf, C, 0.1, 0.0, product=product)
 
 
-def test_matvec_truncated_torus_patch(ctx, rbf):
+@PRODUCTS
+def test_matvec_truncated_torus_patch(ctx, rbf, product):
     _, C, _ = torus_patch(theta=0.15)
     rows = np.random.default_rng(5).choice(len(C), 3000, replace=False)
-    _matvec_check(ctx, rbf, C, 0.02, 6.0, rows=rows)
+    _matvec_check(ctx, rbf, C, 0.02, 6.0, rows=rows, product=product)
 
 
+@PRODUCTS
 @pytest.mark.parametrize("n,k", [(1, 3.0), (2, 0.0), (31, 3.0), (33, 0.0), (255, 3.0), (257, 6.0), (1000, 2.0),
                                  (5000, 4.0)])
-def test_matvec_ragged(ctx, rbf, n, k):
+def test_matvec_ragged(ctx, rbf, n, k, product):
     rng = np.random.default_rng(n)
     C = rng.uniform(0, 1, (n, 3))
-    _matvec_check(ctx, rbf, C, 0.08, k)
+    _matvec_check(ctx, rbf, C, 0.08, k, product=product)
 
 
-def test_matvec_deterministic(ctx, rbf):
+@PRODUCTS
+def test_matvec_deterministic(ctx, rbf, product):
     _, C, _ = torus_patch(theta=0.1)
     Cd, _ = c4(C)
-    plan = rbf.Plan(ctx, Cd, sigma=0.02, k=6.0)
+    plan = rbf.Plan(ctx, Cd, sigma=0.02, k=6.0, product=product)
     z = dev(np.random.default_rng(0).standard_normal(len(C)))
     assert torch.equal(plan.matvec(z), plan.matvec(z))
+
+
+def test_matvec_products_agree(ctx, rbf):
+    """The tensor-core and the CUDA-core products compute the same sum: they agree to
+    a few float32 roundings per term on a full-density torus sector."""
+    _, C, _ = torus_patch(theta=0.1)
+    Cd, _ = c4(C)
+    z = dev(np.random.default_rng(3).standard_normal(len(C)))
+    y_tc = rbf.Plan(ctx, Cd, sigma=0.02, k=6.0, product="tc").matvec(z).double()
+    y_simt = rbf.Plan(ctx, Cd, sigma=0.02, k=6.0, product="simt").matvec(z).double()
+    assert float((y_tc - y_simt).norm() / y_simt.norm()) <= 3e-6
 
 
 def test_pair_count_exact(ctx, rbf):
@@ -182,14 +200,16 @@ def test_pair_count_exact(ctx, rbf):
     assert plan3.count_pairs() == 3000 * 3000
 
 
-def test_matvec_large_blocks_overflow_guard(ctx, rbf):
-    """Sparse centres with a wide cut-off make blocks large in units of sigma:
-    the product switches those blocks to the shifted form (no exp2 overflow)."""
+@PRODUCTS
+def test_matvec_large_blocks_overflow_guard(ctx, rbf, product):
+    """Sparse centres with a wide cut-off make blocks and tiles large in units of
+    sigma: the CUDA-core product switches those blocks to the shifted form, the
+    tensor-core product's exponent -|u - v|^2 is never positive."""
     rng = np.random.default_rng(12)
     C = rng.uniform(0, 1, (300, 3))
-    _matvec_check(ctx, rbf, C, 0.02, 12.0)
+    _matvec_check(ctx, rbf, C, 0.02, 12.0, product=product)
     C2 = np.concatenate([rng.uniform(0, 0.2, (2000, 3)), rng.uniform(0.8, 1.0, (50, 3))])
-    _matvec_check(ctx, rbf, C2, 0.03, 0.0)
+    _matvec_check(ctx, rbf, C2, 0.03, 0.0, product=product)
 
 
 @pytest.mark.parametrize("mode", ["df", "f64"])
@@ -359,20 +379,22 @@ def _grid_check(plan, C64, w, sigma, k, lo, hi, dims, nsample=20000, seed=0):
     return f
 
 
-def test_eval_grid_c1_with_oracle_weights(ctx, rbf, sphere_c1):
+@PRODUCTS
+def test_eval_grid_c1_with_oracle_weights(ctx, rbf, sphere_c1, product):
     """The whole evaluation path on the 64^3 grid over [-1.2, 1.2]^3 with the
     oracle's dense-Cholesky weights."""
     C, b = oracle.build_centers(sphere_c1.points, sphere_c1.normals, 0.05)
     Cd, C64 = c4(C)
     xo, res = oracle.solve_dense(C64, b, float(F32(0.1)))
-    plan = rbf.Plan(ctx, Cd, sigma=0.1, k=0.0)
+    plan = rbf.Plan(ctx, Cd, sigma=0.1, k=0.0, product=product)
     _grid_check(plan, C64, xo, 0.1, 0.0, (-1.2,) * 3, (1.2,) * 3, (64, 64, 64))
 
 
-def test_eval_grid_truncated_ragged(ctx, rbf):
+@PRODUCTS
+def test_eval_grid_truncated_ragged(ctx, rbf, product):
     _, C, _ = torus_patch(theta=0.1)
     Cd, C64 = c4(C)
-    plan = rbf.Plan(ctx, Cd, sigma=0.02, k=6.0)
+    plan = rbf.Plan(ctx, Cd, sigma=0.02, k=6.0, product=product)
     w = np.random.default_rng(7).standard_normal(len(C))
     lo = C64.min(0) - 0.05
     hi = C64.max(0) + 0.05
@@ -382,11 +404,12 @@ def test_eval_grid_truncated_ragged(ctx, rbf):
     assert np.array_equal(f1.astype(np.float32), f2)        # cached pair list, same result
 
 
-def test_eval_grid_single_node_and_far_grid(ctx, rbf):
+@PRODUCTS
+def test_eval_grid_single_node_and_far_grid(ctx, rbf, product):
     rng = np.random.default_rng(1)
     C = rng.uniform(0, 1, (500, 3))
     Cd, C64 = c4(C)
-    plan = rbf.Plan(ctx, Cd, sigma=0.05, k=4.0)
+    plan = rbf.Plan(ctx, Cd, sigma=0.05, k=4.0, product=product)
     w = rng.standard_normal(500)
     f = plan.eval_grid(dev(w, torch.float64), (0.5, 0.5, 0.5), (0.5, 0.5, 0.5), (1, 1, 1)).cpu().numpy()
     f64 = oracle.eval_points(C64, w, float(F32(0.05)), float(F32(4.0)), np.array([[0.5, 0.5, 0.5]]))
