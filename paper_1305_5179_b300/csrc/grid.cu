@@ -15,15 +15,31 @@ int64_t count_grid_pairs_launch(rbf_plan *P, const PairList &pl, const rbf_grid 
 
 namespace {
 
+// Brick boxes, and the boxes of its four quarters of 32 nodes (the z layers of the
+// brick; a layer outside the grid gets lo > hi).
 __global__ void k_brick_boxes(int64_t nb, int bx, int by, int gx, int gy, int gz, float lox, float loy, float loz,
-                              float sx, float sy, float sz, float4 *__restrict__ lo, float4 *__restrict__ hi) {
+                              float sx, float sy, float sz, float4 *__restrict__ lo, float4 *__restrict__ hi,
+                              float4 *__restrict__ qlo, float4 *__restrict__ qhi) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nb) return;
     int ix = (int)(t % bx), iy = (int)((t / bx) % by), iz = (int)(t / ((int64_t)bx * by));
     int x0 = ix * 8, y0 = iy * 4, z0 = iz * 4;
     int x1 = min(x0 + 7, gx - 1), y1 = min(y0 + 3, gy - 1), z1 = min(z0 + 3, gz - 1);
-    lo[t] = make_float4(fmaf((float)x0, sx, lox), fmaf((float)y0, sy, loy), fmaf((float)z0, sz, loz), 0.f);
-    hi[t] = make_float4(fmaf((float)x1, sx, lox), fmaf((float)y1, sy, loy), fmaf((float)z1, sz, loz), 0.f);
+    const float X0 = fmaf((float)x0, sx, lox), Y0 = fmaf((float)y0, sy, loy);
+    const float X1 = fmaf((float)x1, sx, lox), Y1 = fmaf((float)y1, sy, loy);
+    lo[t] = make_float4(X0, Y0, fmaf((float)z0, sz, loz), 0.f);
+    hi[t] = make_float4(X1, Y1, fmaf((float)z1, sz, loz), 0.f);
+    for (int u = 0; u < 4; ++u) {
+        const int zu = z0 + u;
+        const float Z = fmaf((float)zu, sz, loz);
+        if (zu < gz) {
+            qlo[4 * t + u] = make_float4(X0, Y0, Z, 0.f);
+            qhi[4 * t + u] = make_float4(X1, Y1, Z, 0.f);
+        } else {
+            qlo[4 * t + u] = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+            qhi[4 * t + u] = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+        }
+    }
 }
 
 bool same_grid(const rbf_grid &a, const rbf_grid &b) {
@@ -72,15 +88,17 @@ static int64_t grid_prepare(rbf_plan *P, const rbf_grid &g, cudaStream_t s) {
         float st[3];
         for (int d = 0; d < 3; ++d)
             st[d] = g.dims[d] > 1 ? (float)(((double)g.hi[d] - (double)g.lo[d]) / (double)(g.dims[d] - 1)) : 0.f;
-        DevBuf<float4> blo, bhi;
+        DevBuf<float4> blo, bhi, qlo, qhi;
         blo.alloc(nb, s);
         bhi.alloc(nb, s);
+        qlo.alloc(4 * nb, s);
+        qhi.alloc(4 * nb, s);
         k_brick_boxes<<<(unsigned)ceil_div(nb, 256), 256, 0, s>>>(nb, (int)gc.bricks[0], (int)gc.bricks[1],
                                                                   (int)g.dims[0], (int)g.dims[1], (int)g.dims[2],
                                                                   g.lo[0], g.lo[1], g.lo[2], st[0], st[1], st[2],
-                                                                  blo.p, bhi.p);
+                                                                  blo.p, bhi.p, qlo.p, qhi.p);
         RBF_LAUNCHED();
-        build_pairlist(P, blo.p, bhi.p, nb, gc.pl, s);
+        build_pairlist(P, blo.p, bhi.p, qlo.p, qhi.p, nb, gc.pl, s);
         gc.valid = true;
     }
     return total;

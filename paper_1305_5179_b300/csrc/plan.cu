@@ -262,25 +262,38 @@ __global__ void k_block_geom(const float4 *__restrict__ pos, const int2 *__restr
     }
 }
 
-// One warp per target tile (a run of <= kChunk binned centres): its box.
+// One warp per target tile (a run of <= kChunk binned centres): its box, and the
+// boxes of its four quarters of 32 targets (an empty quarter gets lo > hi).
 __global__ void k_chunk_boxes(const float4 *__restrict__ pos, const int2 *__restrict__ tiles, int64_t nchk,
-                              float4 *__restrict__ lo, float4 *__restrict__ hi) {
+                              float4 *__restrict__ lo, float4 *__restrict__ hi, float4 *__restrict__ qlo,
+                              float4 *__restrict__ qhi) {
     int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (t >= nchk) return;
     const int2 tl = tiles[t];
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int q = lane; q < tl.y; q += 32) {
-        float4 p = pos[tl.x + q];
-        mn[0] = fminf(mn[0], p.x); mn[1] = fminf(mn[1], p.y); mn[2] = fminf(mn[2], p.z);
-        mx[0] = fmaxf(mx[0], p.x); mx[1] = fmaxf(mx[1], p.y); mx[2] = fmaxf(mx[2], p.z);
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-        for (int o = 16; o > 0; o >>= 1) {
-            mn[d] = fminf(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
-            mx[d] = fmaxf(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+    for (int u = 0; u < kChunk / 32; ++u) {
+        const int q = lane + 32 * u;
+        float a[3] = {INFINITY, INFINITY, INFINITY}, b[3] = {-INFINITY, -INFINITY, -INFINITY};
+        if (q < tl.y) {
+            float4 p = pos[tl.x + q];
+            a[0] = b[0] = p.x; a[1] = b[1] = p.y; a[2] = b[2] = p.z;
         }
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            for (int o = 16; o > 0; o >>= 1) {
+                a[d] = fminf(a[d], __shfl_xor_sync(0xffffffffu, a[d], o));
+                b[d] = fmaxf(b[d], __shfl_xor_sync(0xffffffffu, b[d], o));
+            }
+        if (lane == 0) {
+            qlo[4 * t + u] = make_float4(a[0], a[1], a[2], 0.f);
+            qhi[4 * t + u] = make_float4(b[0], b[1], b[2], 0.f);
+        }
+        for (int d = 0; d < 3; ++d) {
+            mn[d] = fminf(mn[d], a[d]);
+            mx[d] = fmaxf(mx[d], b[d]);
+        }
+    }
     if (lane == 0) {
         lo[t] = make_float4(mn[0], mn[1], mn[2], 0.f);
         hi[t] = make_float4(mx[0], mx[1], mx[2], 0.f);
@@ -433,19 +446,55 @@ void permute_from_binned_f64(const rbf_plan *P, const double *in, double *out, c
 }
 
 namespace {
-// Each entry's block as (start, count | cut-off flag): one load per block in the tensor-core product.
-__global__ void k_pl_expand(const int32_t *__restrict__ ent, const int2 *__restrict__ blk, int64_t len,
-                            int2 *__restrict__ ebi) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= len) return;
-    const int v = ent[e];
-    const int2 b = blk[v & 0x7fffffff];
-    ebi[e] = make_int2(b.x, b.y | (v & (int)0x80000000));
+// Per entry, for the tensor-core product: its block (start, count) and, for each
+// quarter u of 32 targets of the tile, a 2-bit code at bit 8 + 2u of the count word:
+// 0 = no pair of the quarter and the block within the cut-off, 1 = pair-wise test
+// needed, 2 = every pair within it (the box tests of the tile list, on the quarter's
+// box).  Bit 31 keeps the tile's own flag.  One warp per tile.
+__global__ void k_pl_expand(CellGridArgs g, const int32_t *__restrict__ off, int64_t ntiles,
+                            const int32_t *__restrict__ ent, const int2 *__restrict__ blk,
+                            const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
+                            const float4 *__restrict__ qlo, const float4 *__restrict__ qhi, int2 *__restrict__ ebi) {
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= ntiles) return;
+    float4 ql[4], qh[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        ql[u] = qlo[4 * t + u];
+        qh[u] = qhi[4 * t + u];
+    }
+    for (int e = off[t] + lane; e < off[t + 1]; e += 32) {
+        const int v = ent[e];
+        const int b = v & 0x7fffffff;
+        const int2 bi = blk[b];
+        const float4 l = blo[b], h = bhi[b];
+        int codes = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (!(ql[u].x <= qh[u].x)) continue;          // empty quarter
+            const float gx = fmaxf(0.f, fmaxf(l.x - qh[u].x, ql[u].x - h.x));
+            const float gy = fmaxf(0.f, fmaxf(l.y - qh[u].y, ql[u].y - h.y));
+            const float gz = fmaxf(0.f, fmaxf(l.z - qh[u].z, ql[u].z - h.z));
+            if (!(gx * gx + gy * gy + gz * gz < g.keep2)) continue;
+            int c = 1;
+            if (g.dense) {
+                c = 2;
+            } else {
+                const float mx = fmaxf(h.x - ql[u].x, qh[u].x - l.x);
+                const float my = fmaxf(h.y - ql[u].y, qh[u].y - l.y);
+                const float mz = fmaxf(h.z - ql[u].z, qh[u].z - l.z);
+                if (mx * mx + my * my + mz * mz < g.full2) c = 2;
+            }
+            codes |= c << (2 * u);
+        }
+        ebi[e] = make_int2(bi.x, bi.y | (codes << 8) | (v & (int)0x80000000));
+    }
 }
 }  // namespace
 
-void build_pairlist(rbf_plan *P, const float4 *tlo, const float4 *thi, int64_t ntiles, PairList &pl,
-                    cudaStream_t s) {
+void build_pairlist(rbf_plan *P, const float4 *tlo, const float4 *thi, const float4 *qlo, const float4 *qhi,
+                    int64_t ntiles, PairList &pl, cudaStream_t s) {
     CellGridArgs g;
     for (int d = 0; d < 3; ++d) g.lo[d] = P->lo[d];
     g.inv = P->inv;
@@ -476,7 +525,8 @@ void build_pairlist(rbf_plan *P, const float4 *tlo, const float4 *thi, int64_t n
     RBF_LAUNCHED();
     pl.ebi.alloc(std::max<int64_t>(len, 1), s);
     if (len > 0) {
-        k_pl_expand<<<grid_for(len), kThreads, 0, s>>>(pl.ent.p, P->blk.p, len, pl.ebi.p);
+        k_pl_expand<<<wgrid, kThreads, 0, s>>>(g, pl.off.p, ntiles, pl.ent.p, P->blk.p, P->blk_lo.p, P->blk_hi.p, qlo,
+                                               qhi, pl.ebi.p);
         RBF_LAUNCHED();
     }
 
@@ -623,8 +673,11 @@ void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s) {
     P->nchk = build_runs(P, kChunk, P->tiles, nullptr, s);
     P->chk_lo.alloc(P->nchk, s);
     P->chk_hi.alloc(P->nchk, s);
+    DevBuf<float4> qlo, qhi;
+    qlo.alloc(4 * P->nchk, s);
+    qhi.alloc(4 * P->nchk, s);
     k_chunk_boxes<<<grid_for(P->nchk * 32), kThreads, 0, s>>>(P->pos.p, P->tiles.p, P->nchk, P->chk_lo.p,
-                                                              P->chk_hi.p);
+                                                              P->chk_hi.p, qlo.p, qhi.p);
     RBF_LAUNCHED();
-    build_pairlist(P, P->chk_lo.p, P->chk_hi.p, P->nchk, P->pl, s);
+    build_pairlist(P, P->chk_lo.p, P->chk_hi.p, qlo.p, qhi.p, P->nchk, P->pl, s);
 }

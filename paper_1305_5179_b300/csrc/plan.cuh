@@ -18,7 +18,8 @@ struct PairList {
     bool any_split = false;      // some tile has more than one segment
     PBuf<int32_t> off;           // ntiles + 1
     PBuf<int32_t> ent;           // len; bit 31 set = pair-wise cut-off test needed
-    PBuf<int2> ebi;              // len; (start, count | bit 31 of ent) of the entry's block
+    PBuf<int2> ebi;              // len; (start, count | 2-bit codes of the tile's target quarters << 8
+                                 //       | bit 31 of ent) of the entry's block
     PBuf<int4> seg;              // (tile, e0, e1, 1 if the tile has this one segment only)
     PBuf<int32_t> tile_seg;      // ntiles + 1: segments of tile t are [tile_seg[t], tile_seg[t+1])
 };
@@ -84,9 +85,10 @@ struct rbf_plan {
 
 // plan.cu
 void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s);
-// Pair list of target tiles given by boxes (lo, hi per tile) against the plan's source blocks.
-void build_pairlist(rbf_plan *P, const float4 *tlo, const float4 *thi, int64_t ntiles, PairList &pl,
-                    cudaStream_t s);
+// Pair list of target tiles given by boxes (lo, hi per tile; qlo, qhi per quarter of
+// 32 targets, 4 per tile) against the plan's source blocks.
+void build_pairlist(rbf_plan *P, const float4 *tlo, const float4 *thi, const float4 *qlo, const float4 *qhi,
+                    int64_t ntiles, PairList &pl, cudaStream_t s);
 // (Re)cut a built pair list into segments of at most seglen entries.
 void segment_pairlist(rbf_plan *P, PairList &pl, int64_t seglen, cudaStream_t s);
 // The same cut into caller-owned arrays (the pair list itself is not modified).

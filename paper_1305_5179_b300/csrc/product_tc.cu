@@ -21,7 +21,11 @@
 // per lane) and issue its MMAs into one of 4 TMEM stages of 32 columns; warps 0-3
 // (consumers) each
 // own 32 targets (TMEM lanes 32w..32w+31), read their 32 x 32 exponents,
-// and accumulate z_j 2^t over the segment.  full[s] completes when the stage's
+// and accumulate z_j 2^t over the segment.  The pair list carries, per block, a
+// 2-bit code for each quarter of 32 targets (box tests on the quarter's box): a
+// consumer skips a block its quarter cannot reach, tests pairs against the cut-off
+// only when some may fail it, and a producer issues no MMA for a block no quarter
+// reaches.  full[s] completes when the stage's
 // MMAs have finished and the producer has written its weights; empty[s] when
 // all four consumers have read it.  Every wait is bounded (1 s); on expiry the
 // kernel raises the context's device error word and returns after freeing its
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(kThreadsTc, 4) k_product_tc(MvArgs a, unsigned
         auto issue = [&](int pj) {
             if (pj < my_nb) {
                 const int2 e = S.lst[pw][(pj / kL) & 1][pj % kL];
-                if (lane < (e.y & 0x7fffffff)) {
+                if (lane < (e.y & 0xff)) {
                     tc5::cp_async16(&S.rpos[pw][pj % kR][lane], a.pos + e.x + lane);
                     tc5::cp_async4(&S.rz[pw][pj % kR][lane], a.w + e.x + lane);
                 }
@@ -209,13 +213,23 @@ __global__ void __launch_bounds__(kThreadsTc, 4) k_product_tc(MvArgs a, unsigned
             const int2 e = S.lst[pw][(j / kL) & 1][j % kL];
             float4 cp = make_float4(c[0], c[1], c[2], 0.f);
             float cz = 0.f;
-            if (lane < (e.y & 0x7fffffff)) {
+            if (lane < (e.y & 0xff)) {
                 cp = S.rpos[pw][j % kR][lane];
                 cz = S.rz[pw][j % kR][lane];
             }
             if (b >= kStages && !tc5::mbar_wait(&S.empty[s], (k - 1) & 1u, &S.abort, kWaitNs)) {
                 raise_error(S, err);
                 break;
+            }
+            if (lane == 0) S.flag[s] = e.y;
+            if (((e.y >> 8) & 0xff) == 0) {   // no quarter of the tile meets this block: no MMA
+                __syncwarp();
+                if (lane == 0) {
+                    tc5::mbar_arrive(&S.full[s]);
+                    tc5::mbar_arrive(&S.full[s]);
+                }
+                __syncwarp();
+                continue;
             }
             const float wx = (cp.x - c[0]) * s2, wy = (cp.y - c[1]) * s2, wz = (cp.z - c[2]) * s2;
             const float q = -0.25f * fmaf(wx, wx, fmaf(wy, wy, wz * wz));
@@ -227,7 +241,6 @@ __global__ void __launch_bounds__(kThreadsTc, 4) k_product_tc(MvArgs a, unsigned
             put4(Bs, lane, 1, Ly, Hy, Hz, Lz);
             put4(Bs, lane, 2, Hz, qh, ql, 1.f);
             S.z[s][lane] = cz;      // zero past the block's count: padded sources vanish
-            if (lane == 0) S.flag[s] = e.y < 0;
             tc5::fence_async_smem();
             __syncwarp();
             if (lane == 0) {
@@ -264,11 +277,17 @@ __global__ void __launch_bounds__(kThreadsTc, 4) k_product_tc(MvArgs a, unsigned
                 raise_error(S, err);
                 break;
             }
+            const int code = (S.flag[s] >> (8 + 2 * warp)) & 3;   // this warp's quarter vs the block
+            if (code == 0) {
+                __syncwarp();
+                if (lane == 0) tc5::mbar_arrive(&S.empty[s]);
+                continue;
+            }
             tc5::fence_after_sync();
             float tv[32];
             tc5::tmem_ld_32x32(trow + (uint32_t)(s * kBlk), tv);
             const float4 *zz = reinterpret_cast<const float4 *>(S.z[s]);
-            if (!S.flag[s]) {
+            if (code == 2) {
 #pragma unroll
                 for (int g = 0; g < 8; ++g) {
                     const float4 Z = zz[g];
