@@ -41,6 +41,10 @@ WORKLOADS = {
     "torus1m": dict(desc="torus R=1 r=0.35 noise 1e-3, N=1,000,000 points -> 3,000,000 centres",
                     N=1_000_000, delta=0.01, sigma=0.02, k=6.0, grid=256, core=96, block=128, shift=1.0,
                     iters=50, m=50, precond="schwarz"),
+    "torus_sector": dict(desc="sector 0 <= theta < 0.6 of the torus R=1 r=0.35 at the density of the 1,000,000-point "
+                              "cloud (95,492 points -> 286,476 centres); a small case of the same operator for profiling",
+                         N=95_492, theta=0.6, delta=0.01, sigma=0.02, k=6.0, grid=96, core=96, block=128, shift=1.0,
+                         iters=50, m=50, precond="schwarz"),
     "sphere1500": dict(desc="unit sphere N=1,500 -> 4,500 centres, untruncated", N=1500, delta=0.05, sigma=0.1,
                        k=0.0, grid=64, core=96, block=128, shift=1e-4, iters=50, m=50, precond="none"),
     "batch512": dict(desc="512 ellipsoids/tori, log-uniform 500-20,000 points each, delta 0.02, "
@@ -49,10 +53,33 @@ WORKLOADS = {
 }
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_product_tc launch on the
+# 3,000,000-centre torus, from one ncu capture (profiles/k_product_tc_torus_sector.md gives the
+# command); valid only while the kernel sources hash to the values it was taken with.
+PRODUCT_TRAFFIC = {"torus1m": (156.64e6 + 9.10e6, {
+    "paper_1305_5179_b300/csrc/product_tc.cu": "7b1c29d5c5703c35308666b6511ff095d8634c978a1696da5ed8eff6e4430cf6",
+    "paper_1305_5179_b300/csrc/tcgen05.cuh": "eb1c4ef3c7182b1729de9e68052cb52ca5850d77a3c93fff07681ddd33baa43f"})}
+
+
+def product_traffic(name):
+    import hashlib
+    if name not in PRODUCT_TRAFFIC:
+        return None
+    nbytes, hashes = PRODUCT_TRAFFIC[name]
+    here = os.path.dirname(os.path.abspath(__file__))
+    for rel, h in hashes.items():
+        with open(os.path.join(here, rel), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != h:
+                return None
+    return nbytes
+
+
 def make_cloud(wl):
     import synth
     if wl["N"] == 1500:
         return synth.sphere(1500, seed=0)
+    if "theta" in wl:
+        return synth.torus(wl["N"], noise=1e-3, seed=0, theta_max=wl["theta"])
     return synth.torus(wl["N"], noise=1e-3, seed=0)
 
 
@@ -283,8 +310,8 @@ def run_ours(args, wl):
     peak = probe["num_sms"] * f_mhz * 1e6 * probe["ex2_per_clk_sm"]   # one ex2 per pair
     achieved = pairs_mv / (mv_ms * 1e-3)
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
-            "frac": achieved / peak, "traffic": None,
-            "kernel": "k_matvec_f32 (float32 truncated product)",
+            "frac": achieved / peak, "traffic": product_traffic(args.workload), "traffic_unit": "bytes per launch",
+            "kernel": "k_product_tc (truncated product: exponents by tcgen05.mma, float32 exp2 and sums)",
             "peak_basis": f"{probe['num_sms']} SMs x {f_mhz:.0f} MHz (median SM clock in the timed region) x "
                           f"{probe['ex2_per_clk_sm']:.2f} ex2/clk/SM (measured by rbf_probe_peaks): "
                           f"one MUFU.EX2 per pair",

@@ -5,7 +5,10 @@
  * ex2.approx.f32 (the special-function unit), scalar FP32 FMA and packed
  * f32x2 FMA, each as operations per SM per clock, with the SM clock derived
  * from the cycle counter and the global nanosecond timer of the probe run.
- * These are the denominators of the product kernels' roofline.
+ * These are the denominators of the product kernels' roofline.  It also times,
+ * on one thread per SM, the issue-to-completion latency of the tensor-core step
+ * of the product (two dependent tcgen05.mma of kind::tf32, M = 128, N = 32,
+ * K = 8, then tcgen05.commit to an mbarrier), alone and four in a row.
  */
 #ifndef RBF_PROBE_H
 #define RBF_PROBE_H
@@ -22,10 +25,14 @@ typedef struct {
     double ex2_per_clk_sm;          /* MUFU.EX2 results per SM per clock */
     double ffma_per_clk_sm;         /* scalar FP32 FMA per SM per clock */
     double ffma2_lanes_per_clk_sm;  /* packed f32x2 FMA, FP32 lanes per SM per clock */
+    double mma_commit_cycles;       /* SM cycles from issuing one MMA pair + commit to the mbarrier phase */
+    double mma_commit4_cycles;      /* the same for four pairs (each with its commit) issued back to back */
 } rbf_probe_result;
 
-/* Runs three short kernels (about 10 ms each) on `device` (default stream) and
- * fills *r.  Errors: RBF_ERR_INVALID (null r), RBF_ERR_CUDA. */
+/* Runs three short kernels (about 10 ms each) and the latency kernel (under 1 ms)
+ * on `device` (default stream) and fills *r.  Errors: RBF_ERR_INVALID (null r),
+ * RBF_ERR_CUDA, RBF_ERR_TIMEOUT (an mbarrier wait of the latency kernel expired;
+ * its waits are bounded at 100 ms). */
 rbf_status rbf_probe_peaks(int device, rbf_probe_result *r);
 
 #ifdef __cplusplus

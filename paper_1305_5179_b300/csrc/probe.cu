@@ -2,6 +2,7 @@
 // FP32 FMA (scalar and packed f32x2) per SM per clock, with the SM clock read
 // from the cycle counter against the global nanosecond timer during the run.
 #include "common.cuh"
+#include "tcgen05.cuh"
 #include "../../include/rbf_probe.h"
 
 namespace {
@@ -56,6 +57,79 @@ __global__ void __launch_bounds__(kThreads) k_probe(int iters, float seed, float
     }
 }
 
+// Latency of the product's tensor-core step: thread 0 of each CTA issues `stages` pairs of
+// dependent tf32 MMAs (M 128, N 32, K 8; operands zero) into distinct TMEM columns, each
+// pair followed by a commit to its own mbarrier, then waits for every phase; averaged
+// over `rounds`.  Every wait gives up after 100 ms and reports it in out[2].
+__global__ void __launch_bounds__(128) k_probe_mma(int rounds, int stages, unsigned long long *out) {
+    __shared__ __align__(1024) uint8_t A[128 * 64];
+    __shared__ __align__(1024) uint8_t B[32 * 64];
+    __shared__ uint64_t bar[4];
+    __shared__ uint32_t tm;
+    const int warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < (int)(sizeof(A) / 4); i += blockDim.x) reinterpret_cast<float *>(A)[i] = 0.f;
+    for (int i = threadIdx.x; i < (int)(sizeof(B) / 4); i += blockDim.x) reinterpret_cast<float *>(B)[i] = 0.f;
+    if (warp == 0) {
+        tc5::tmem_alloc(&tm, 128);
+        tc5::tmem_relinquish();
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 4; ++s) tc5::mbar_init(&bar[s], 1);
+        tc5::mbar_init_fence();
+    }
+    tc5::fence_async_smem();
+    tc5::fence_before_sync();
+    __syncthreads();
+    tc5::fence_after_sync();
+    const uint32_t tmem = tm;
+    if (threadIdx.x == 0) {
+        const uint32_t idesc = tc5::idesc_tf32(128, 32), a = tc5::smem_u32(A), b = tc5::smem_u32(B);
+        unsigned long long tot = 0;
+        bool late = false;
+        for (int it = 0; it < rounds && !late; ++it) {
+            const long long t0 = clock64();
+            for (int s = 0; s < stages; ++s) {
+                const uint32_t d = tmem + 32u * (uint32_t)s;
+                tc5::mma_tf32(d, tc5::smem_desc(a, 128, 512), tc5::smem_desc(b, 128, 512), idesc, 0u);
+                tc5::mma_tf32(d, tc5::smem_desc(a + 256, 128, 512), tc5::smem_desc(b + 256, 128, 512), idesc, 1u);
+                tc5::mma_commit(&bar[s]);
+            }
+            for (int s = 0; s < stages; ++s) {
+                const uint64_t g0 = tc5::global_ns();
+                while (!tc5::mbar_try_wait(&bar[s], (uint32_t)it & 1u)) {
+                    if (tc5::global_ns() - g0 > 100000000ull) {
+                        late = true;
+                        break;
+                    }
+                }
+            }
+            tot += (unsigned long long)(clock64() - t0);
+        }
+        if (late) atomicAdd(&out[2], 1ull);
+        atomicAdd(&out[0], tot / (unsigned long long)rounds);
+        atomicAdd(&out[1], 1ull);
+    }
+    tc5::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc5::fence_after_sync();
+        tc5::tmem_dealloc(tmem, 128);
+    }
+}
+
+double run_probe_mma(int num_sms, int stages, cudaStream_t s) {
+    DevBuf<unsigned long long> out;
+    out.alloc(3, s);
+    out.zero(s);
+    k_probe_mma<<<num_sms, 128, 0, s>>>(200, stages, out.p);
+    RBF_LAUNCHED();
+    unsigned long long h[3];
+    RBF_CUDA(cudaMemcpyAsync(h, out.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(cudaStreamSynchronize(s));
+    RBF_CHECK(h[2] == 0, RBF_ERR_TIMEOUT, "tensor-core latency probe: an mbarrier wait expired");
+    return h[1] ? (double)h[0] / (double)h[1] : 0.0;
+}
+
 template <int kMode>
 double run_probe(int num_sms, double ops_per_iter_per_thread, double *mhz, cudaStream_t s) {
     const int blocks = num_sms * 8, iters = 20000;
@@ -100,6 +174,8 @@ extern "C" rbf_status rbf_probe_peaks(int device, rbf_probe_result *r) {
         r->ffma_per_clk_sm = run_probe<1>(sms, kChains, &m1, 0);
         r->ffma2_lanes_per_clk_sm = run_probe<2>(sms, kChains, &m2, 0);
         r->sm_mhz = (m0 + m1 + m2) / 3.0;
+        r->mma_commit_cycles = run_probe_mma(sms, 1, 0);
+        r->mma_commit4_cycles = run_probe_mma(sms, 4, 0);
         return RBF_OK;
     } catch (const RbfError &e) {
         return e.status;

@@ -64,8 +64,8 @@ def test_struct_layouts_match_header():
 #include "rbf.h"
 #include "rbf_probe.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(rbf_plan_params), sizeof(rbf_plan_info), sizeof(rbf_schwarz_params),
-         sizeof(rbf_solve_params), sizeof(rbf_report), sizeof(rbf_grid));
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(rbf_plan_params), sizeof(rbf_plan_info), sizeof(rbf_schwarz_params),
+         sizeof(rbf_solve_params), sizeof(rbf_report), sizeof(rbf_grid), sizeof(rbf_probe_result));
   return 0;
 }
 """
@@ -76,8 +76,7 @@ int main(void) {
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         sizes = list(map(int, subprocess.check_output([exe]).split()))
     mine = [ctypes.sizeof(t) for t in (rbf.PlanParams, rbf.PlanInfo, rbf.SchwarzParams, rbf.SolveParams,
-                                       rbf.Report, rbf.Grid)]
-    assert ctypes.sizeof(rbf.ProbeResult) == 40
+                                       rbf.Report, rbf.Grid, rbf.ProbeResult)]
     assert sizes == mine
 
 
