@@ -393,6 +393,7 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
     permute_from_binned_f64(P, x.p, x_caller, s);
     cudaEventRecord(tm_solve.b, s);
     RBF_CUDA(cudaStreamSynchronize(s));
+    ctx_check_device_error(P->ctx);   // a product launch of this solve gave up on a bounded wait
     float ms_a = 0, ms_b = 0;
     cudaEventElapsedTime(&ms_a, tm_setup.a, tm_setup.b);
     cudaEventElapsedTime(&ms_b, tm_solve.a, tm_solve.b);

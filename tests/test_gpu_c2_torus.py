@@ -1,7 +1,7 @@
 """The benchmark workload at full size, in the configuration bench.py times:
 1,000,000 torus points (R = 1, r = 0.35, noise 1e-3), delta 0.01 -> 3,000,000
-centres, sigma 0.02, cut-off 6 sigma, Schwarz subdomains of 128 (core 96), 50
-FGMRES iterations, 256^3 grid.  Sampled outputs against the FP64 oracle: 10,000
+centres, sigma 0.02, cut-off 6 sigma, Schwarz subdomains of 128 (core 96, shift 1),
+50 FGMRES iterations, 256^3 grid.  Sampled outputs against the FP64 oracle: 10,000
 rows of the product and of the true residual, 10,000 grid nodes."""
 import numpy as np
 import pytest
@@ -25,7 +25,7 @@ def c2():
                                 delta=DELTA)
     plan = rbf.Plan(ctx, C, sigma=SIGMA, k=K)
     x, rep = plan.solve(b, m=50, max_it=50, fixed_iterations=True, precond="schwarz", core=96, block=128,
-                        shift=1e-4, escalate=True)
+                        shift=1.0, escalate=True)
     C64 = C[:, :3].double().cpu().numpy()
     rows = np.random.default_rng(5).choice(len(C64), 10_000, replace=False)
     return rbf, plan, C, b, x, rep, C64, rows, cl
@@ -50,6 +50,8 @@ def test_c2_solve_residual_sampled_rows(c2):
     assert np.abs(r.cpu().numpy()[rows] - r64).max() <= 1e-11 * scale.max()
     assert rep["residual_true"] == pytest.approx(rn / bn, rel=1e-9)
     assert rep["precond_failed_blocks"] == 0
+    # the position noise (1e-3, a tenth of delta) leaves about 0.1 that no smooth interpolant removes
+    assert rep["residual_true"] < 0.2
     print(f"  C2 after 50 RAS-FGMRES iterations: relative residual {rep['residual_true']:.4f}")
 
 
