@@ -74,6 +74,27 @@ struct TcSmem {
 };
 static_assert(sizeof(TcSmem) <= kSmemTc, "shared memory layout");
 
+#ifndef RBF_TC_SUM
+#define RBF_TC_SUM 0
+#endif
+// Two exponentials / two cut-off masks (1.0 or 0.0) written straight into a register pair.
+__device__ __forceinline__ f2 ex2_pair(float a, float b) {
+    f2 r;
+    asm("{\n\t.reg .f32 lo, hi;\n\tex2.approx.ftz.f32 lo, %1;\n\tex2.approx.ftz.f32 hi, %2;\n\t"
+        "mov.b64 %0, {lo, hi};\n\t}"
+        : "=l"(r)
+        : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ f2 gt_pair(float a, float b, float thr) {
+    f2 r;
+    asm("{\n\t.reg .f32 lo, hi;\n\tset.gt.f32.f32 lo, %1, %3;\n\tset.gt.f32.f32 hi, %2, %3;\n\t"
+        "mov.b64 %0, {lo, hi};\n\t}"
+        : "=l"(r)
+        : "f"(a), "f"(b), "f"(thr));
+    return r;
+}
+
 __device__ __forceinline__ uint32_t core_off(int row, int chunk) {
     return (uint32_t)((row >> 3) * kSbo + chunk * kLbo + (row & 7) * 16);
 }
@@ -169,7 +190,14 @@ __global__ void __launch_bounds__(kThreadsTc, 4) k_product_tc(MvArgs a, unsigned
         const int pw = warp - kCons;
         const int my_nb = nb > pw ? (nb - pw + kProd - 1) / kProd : 0;
         const float s2 = 2.f * a.scl;
-        const uint32_t a_addr = tc5::smem_u32(S.a);
+        // descriptors: A's two K halves are fixed; a B stage's differ from stage 0's only in
+        // the start address field (address >> 4, added without carry out of the field)
+        const uint64_t da0 = tc5::smem_desc(tc5::smem_u32(S.a), kLbo, kSbo);
+        const uint64_t da1 = tc5::smem_desc(tc5::smem_u32(S.a) + 2 * kLbo, kLbo, kSbo);
+        const uint64_t db0 = tc5::smem_desc(tc5::smem_u32(S.b[0]), kLbo, kSbo);
+        const uint32_t row_off = core_off(lane, 0);   // this lane's B row within a stage
+        const float4 *pos_l = a.pos + lane;
+        const float *w_l = a.w + lane;
         const int2 *ebi = a.ebi + sg.y + pw;
         int2 nx[kL / 32];
         auto fetch = [&](int ch) {
@@ -187,8 +215,8 @@ __global__ void __launch_bounds__(kThreadsTc, 4) k_product_tc(MvArgs a, unsigned
             if (pj < my_nb) {
                 const int2 e = S.lst[pw][(pj / kL) & 1][pj % kL];
                 if (lane < (e.y & 0xff)) {
-                    tc5::cp_async16(&S.rpos[pw][pj % kR][lane], a.pos + e.x + lane);
-                    tc5::cp_async4(&S.rz[pw][pj % kR][lane], a.w + e.x + lane);
+                    tc5::cp_async16(&S.rpos[pw][pj % kR][lane], pos_l + e.x);
+                    tc5::cp_async4(&S.rz[pw][pj % kR][lane], w_l + e.x);
                 }
             }
             tc5::cp_async_commit();
@@ -236,20 +264,19 @@ __global__ void __launch_bounds__(kThreadsTc, 4) k_product_tc(MvArgs a, unsigned
             const float Hx = tc5::to_tf32(wx), Hy = tc5::to_tf32(wy), Hz = tc5::to_tf32(wz);
             const float Lx = tc5::to_tf32(wx - Hx), Ly = tc5::to_tf32(wy - Hy), Lz = tc5::to_tf32(wz - Hz);
             const float qh = tc5::to_tf32(q), ql = tc5::to_tf32(q - qh);
-            uint8_t *Bs = S.b[s];
-            put4(Bs, lane, 0, Hx, Lx, Hx, Hy);
-            put4(Bs, lane, 1, Ly, Hy, Hz, Lz);
-            put4(Bs, lane, 2, Hz, qh, ql, 1.f);
+            uint8_t *Bs = S.b[s] + row_off;
+            *reinterpret_cast<float4 *>(Bs) = make_float4(Hx, Lx, Hx, Hy);
+            *reinterpret_cast<float4 *>(Bs + kLbo) = make_float4(Ly, Hy, Hz, Lz);
+            *reinterpret_cast<float4 *>(Bs + 2 * kLbo) = make_float4(Hz, qh, ql, 1.f);
             S.z[s][lane] = cz;      // zero past the block's count: padded sources vanish
             tc5::fence_async_smem();
             __syncwarp();
             if (lane == 0) {
                 tc5::fence_after_sync();
-                const uint32_t b_addr = tc5::smem_u32(Bs);
+                const uint64_t db = db0 + (uint64_t)((s * kBBytes) >> 4);
                 const uint32_t d = tmem + (uint32_t)(s * kBlk);
-                tc5::mma_tf32(d, tc5::smem_desc(a_addr, kLbo, kSbo), tc5::smem_desc(b_addr, kLbo, kSbo), kIdesc, 0u);
-                tc5::mma_tf32(d, tc5::smem_desc(a_addr + 2 * kLbo, kLbo, kSbo),
-                              tc5::smem_desc(b_addr + 2 * kLbo, kLbo, kSbo), kIdesc, 1u);
+                tc5::mma_tf32(d, da0, db, kIdesc, 0u);
+                tc5::mma_tf32(d, da1, db + ((2 * kLbo) >> 4), kIdesc, 1u);
                 tc5::mma_commit(&S.full[s]);
                 tc5::mbar_arrive(&S.full[s]);
             }
@@ -287,12 +314,37 @@ __global__ void __launch_bounds__(kThreadsTc, 4) k_product_tc(MvArgs a, unsigned
             float tv[32];
             tc5::tmem_ld_32x32(trow + (uint32_t)(s * kBlk), tv);
             const float4 *zz = reinterpret_cast<const float4 *>(S.z[s]);
+#if RBF_TC_SUM == 1
+            // scalar FMAs, four accumulators
+            float sa[4] = {0.f, 0.f, 0.f, 0.f};
             if (code == 2) {
 #pragma unroll
                 for (int g = 0; g < 8; ++g) {
                     const float4 Z = zz[g];
-                    const f2 e0 = pk(ex2_approx(tv[4 * g]), ex2_approx(tv[4 * g + 1]));
-                    const f2 e1 = pk(ex2_approx(tv[4 * g + 2]), ex2_approx(tv[4 * g + 3]));
+                    sa[0] = fmaf(ex2_approx(tv[4 * g]), Z.x, sa[0]);
+                    sa[1] = fmaf(ex2_approx(tv[4 * g + 1]), Z.y, sa[1]);
+                    sa[2] = fmaf(ex2_approx(tv[4 * g + 2]), Z.z, sa[2]);
+                    sa[3] = fmaf(ex2_approx(tv[4 * g + 3]), Z.w, sa[3]);
+                }
+            } else {
+#pragma unroll
+                for (int g = 0; g < 8; ++g) {
+                    const float4 Z = zz[g];
+                    sa[0] = fmaf(ex2_approx(tv[4 * g]), Z.x * set_gt(tv[4 * g], thr), sa[0]);
+                    sa[1] = fmaf(ex2_approx(tv[4 * g + 1]), Z.y * set_gt(tv[4 * g + 1], thr), sa[1]);
+                    sa[2] = fmaf(ex2_approx(tv[4 * g + 2]), Z.z * set_gt(tv[4 * g + 2], thr), sa[2]);
+                    sa[3] = fmaf(ex2_approx(tv[4 * g + 3]), Z.w * set_gt(tv[4 * g + 3], thr), sa[3]);
+                }
+            }
+            acc[0] = fma2(pk(sa[0], sa[1]), pk(1.f, 1.f), acc[0]);
+            acc[1] = fma2(pk(sa[2], sa[3]), pk(1.f, 1.f), acc[1]);
+#else
+            if (code == 2) {
+#pragma unroll
+                for (int g = 0; g < 8; ++g) {
+                    const float4 Z = zz[g];
+                    const f2 e0 = ex2_pair(tv[4 * g], tv[4 * g + 1]);
+                    const f2 e1 = ex2_pair(tv[4 * g + 2], tv[4 * g + 3]);
                     acc[2 * (g & 1)] = fma2(e0, pk(Z.x, Z.y), acc[2 * (g & 1)]);
                     acc[2 * (g & 1) + 1] = fma2(e1, pk(Z.z, Z.w), acc[2 * (g & 1) + 1]);
                 }
@@ -301,12 +353,13 @@ __global__ void __launch_bounds__(kThreadsTc, 4) k_product_tc(MvArgs a, unsigned
                 for (int g = 0; g < 8; ++g) {
                     const float4 Z = zz[g];
                     const float t0 = tv[4 * g], t1 = tv[4 * g + 1], t2 = tv[4 * g + 2], t3 = tv[4 * g + 3];
-                    const f2 m0 = pk(set_gt(t0, thr), set_gt(t1, thr)), m1 = pk(set_gt(t2, thr), set_gt(t3, thr));
-                    const f2 e0 = pk(ex2_approx(t0), ex2_approx(t1)), e1 = pk(ex2_approx(t2), ex2_approx(t3));
+                    const f2 m0 = gt_pair(t0, t1, thr), m1 = gt_pair(t2, t3, thr);
+                    const f2 e0 = ex2_pair(t0, t1), e1 = ex2_pair(t2, t3);
                     acc[2 * (g & 1)] = fma2(e0, mul2(m0, pk(Z.x, Z.y)), acc[2 * (g & 1)]);
                     acc[2 * (g & 1) + 1] = fma2(e1, mul2(m1, pk(Z.z, Z.w)), acc[2 * (g & 1) + 1]);
                 }
             }
+#endif
             tc5::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc5::mbar_arrive(&S.empty[s]);

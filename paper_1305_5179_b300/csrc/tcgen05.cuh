@@ -84,6 +84,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
+// The same test, letting the thread sleep until the phase completes or `hint_ns` passes
+// (instead of spinning on the issue slots other warps need).
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *mbar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return done != 0;
+}
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -96,7 +108,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, const
     if (mbar_try_wait(mbar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (true) {
-        if (mbar_try_wait(mbar, parity)) return true;
+        if (mbar_try_wait_sleep(mbar, parity, 200000u)) return true;
         if (*abort) return false;
         if (global_ns() - t0 > limit_ns) return false;
     }
