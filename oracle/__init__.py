@@ -503,3 +503,47 @@ def mlp_block_data(Cs, sigma, lam, block_ids, R, block=64):
         A = dense_matrix(P, sigma) + lam * np.eye(block)
         Y[row] = 8.0 * lam * chol_solve(cholesky(A), rh)
     return X, Y
+
+
+# ---------------------------------------------------------------- density measures
+def nn_distances(X: np.ndarray, rows=None, chunk: int = 2048) -> np.ndarray:
+    """Distance from each point (or each point of `rows`) to its nearest other point
+    of X, by brute force over all points (the min over i != j in the separation
+    distance of Eq. sepDist and in h_max of Sec. IV).  A duplicate point has
+    distance 0."""
+    X = np.asarray(X, dtype=np.float64)
+    idx = np.arange(len(X)) if rows is None else np.asarray(rows)
+    out = np.empty(len(idx))
+    for s in range(0, len(idx), chunk):
+        r = idx[s:s + chunk]
+        d2 = ((X[r, None, :] - X[None, :, :]) ** 2).sum(-1)
+        d2[np.arange(len(r)), r] = np.inf
+        out[s:s + chunk] = np.sqrt(d2.min(1))
+    return out
+
+
+def fill_distance(X: np.ndarray, probes: np.ndarray, chunk: int = 2048) -> float:
+    """Eq. fillDist with the sup over the domain replaced by a max over the given
+    probe points of the domain: max_p min_j |p - x_j| (brute force)."""
+    X = np.asarray(X, dtype=np.float64)
+    P = np.asarray(probes, dtype=np.float64)
+    h = 0.0
+    for s in range(0, len(P), chunk):
+        d2 = ((P[s:s + chunk, None, :] - X[None, :, :]) ** 2).sum(-1)
+        h = max(h, float(np.sqrt(d2.min(1)).max()))
+    return h
+
+
+def density_measures(X: np.ndarray, probes=None) -> dict:
+    """Density measures of Sec. IV: separation distance q = 1/2 min_{i!=j} |x_i - x_j|
+    (Eq. sepDist), h_max = max_j min_{i!=j} |x_i - x_j|, the mean nearest-neighbour
+    distance, and, with probe points of the domain, the fill distance (Eq. fillDist);
+    with the sigma rules sigma ~ 2 q (Eq. h1), sigma ~ h sqrt(2) (Eq. h2) and
+    h ~ h_max sqrt(2) (Eq. hmax)."""
+    d = nn_distances(X)
+    out = {"q": 0.5 * float(d.min()), "h_max": float(d.max()), "mean_nn": float(d.mean())}
+    out["fill"] = fill_distance(X, probes) if probes is not None and len(probes) else float("nan")
+    out["sigma_q"] = 2.0 * out["q"]
+    out["sigma_fill"] = out["fill"] * np.sqrt(2.0)
+    out["sigma_hmax"] = out["h_max"] * np.sqrt(2.0)
+    return out

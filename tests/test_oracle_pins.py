@@ -435,3 +435,55 @@ def test_mlp_block_targets_solve_the_shifted_block():
         assert np.allclose(A @ Y[row] / 8e-3, r / np.linalg.norm(r), atol=1e-9)
         assert np.allclose(X[row, 192:], 8 * r / np.linalg.norm(r))
         assert np.allclose(X[row, :192].reshape(64, 3).mean(0), 0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- Section IV: density measures
+def test_density_halton_example_of_the_paper():
+    """The worked example of Fig. filDist: 25 Halton points on [0,1]^2 have
+    q ~ 0.0597 and fill distance ~ 0.2667 (tests/golden/density_halton25.json)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "density_halton25.json")))
+    P = synth.halton(25, bases=(2, 3), start=1)
+    X = np.c_[P, np.zeros(25)]
+    m = 1201
+    u = np.linspace(0.0, 1.0, m)
+    gx, gy = np.meshgrid(u, u, indexing="ij")
+    probes = np.c_[gx.ravel(), gy.ravel(), np.zeros(m * m)]
+    d = oracle.density_measures(X, probes)
+    half = 0.5 * 10.0 ** -(g["printed_digits"])
+    assert abs(d["q"] - g["q"]) <= half
+    # the max over a probe grid of spacing 1/1200 is within 1/1200 of the sup
+    assert abs(d["fill"] - g["fill"]) <= half + 1.0 / (m - 1)
+    assert d["sigma_q"] == pytest.approx(2 * d["q"]) and d["sigma_fill"] == pytest.approx(d["fill"] * math.sqrt(2))
+
+
+def test_density_square_lattice_closed_forms():
+    """Square lattice of spacing s: every nearest neighbour is at s, so q = s/2,
+    h_max = mean = s; the farthest domain points from the lattice are the cell
+    centres, at s / sqrt(2)."""
+    s = 0.37
+    g = np.arange(7) * s
+    gx, gy = np.meshgrid(g, g, indexing="ij")
+    X = np.c_[gx.ravel(), gy.ravel(), np.zeros(49)]
+    cx, cy = np.meshgrid(g[:-1] + s / 2, g[:-1] + s / 2, indexing="ij")
+    probes = np.c_[cx.ravel(), cy.ravel(), np.zeros(36)]
+    d = oracle.density_measures(X, probes)
+    assert d["q"] == pytest.approx(s / 2, rel=1e-12)
+    assert d["h_max"] == pytest.approx(s, rel=1e-12) and d["mean_nn"] == pytest.approx(s, rel=1e-12)
+    assert d["fill"] == pytest.approx(s / math.sqrt(2), rel=1e-12)
+
+
+def test_density_nearest_neighbours_match_a_kd_tree():
+    """Brute-force nearest-neighbour distances equal SciPy's k-d tree query (an
+    independent algorithm) on a 3-D torus sample with duplicates."""
+    from scipy.spatial import cKDTree
+    cl = synth.torus(3000, noise=1e-3, seed=4)
+    X = np.concatenate([cl.points.astype(np.float64), cl.points[:5].astype(np.float64)])   # 5 duplicates
+    d = oracle.nn_distances(X)
+    dd, _ = cKDTree(X).query(X, k=2)
+    assert np.allclose(d, dd[:, 1], rtol=0, atol=1e-15)
+    assert oracle.density_measures(X)["q"] == 0.0
+    two = np.array([[0.0, 0.0, 0.0], [0.3, 0.4, 0.0]])
+    t = oracle.density_measures(two)
+    assert t["q"] == pytest.approx(0.25) and t["h_max"] == pytest.approx(0.5)
