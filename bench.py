@@ -45,6 +45,9 @@ WORKLOADS = {
                               "cloud (95,492 points -> 286,476 centres); a small case of the same operator for profiling",
                          N=95_492, theta=0.6, delta=0.01, sigma=0.02, k=6.0, grid=96, core=96, block=128, shift=1.0,
                          iters=50, m=50, precond="schwarz"),
+    "density": dict(desc="density measures (Sec. IV) of the 1,000,000-point torus cloud: nearest neighbour of every "
+                         "point and fill distance over 1,000,000 probe points on the noise-free torus",
+                    N=1_000_000, probes=1_000_000),
     "sphere1500": dict(desc="unit sphere N=1,500 -> 4,500 centres, untruncated", N=1500, delta=0.05, sigma=0.1,
                        k=0.0, grid=64, core=96, block=128, shift=1e-4, iters=50, m=50, precond="none"),
     "batch512": dict(desc="512 ellipsoids/tori, log-uniform 500-20,000 points each, delta 0.02, "
@@ -364,6 +367,94 @@ def run_ours(args, wl):
     return 0
 
 
+def run_density(args, wl):
+    """Row f1: the density measures that choose sigma (rbf_density_measures) on the C2
+    cloud: N nearest-neighbour queries plus M probe queries per step."""
+    import numpy as np
+    import torch
+    import paper_1305_5179_b300 as rbf
+    import synth
+
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    ctx = rbf.Context(local)
+    dev = torch.device("cuda", local)
+    cl = synth.torus(wl["N"], noise=1e-3, seed=0)
+    pr = synth.torus(wl["probes"], noise=0.0, seed=1)
+    P = np.zeros((wl["N"], 4), dtype=np.float32)
+    P[:, :3] = cl.points
+    Q = np.zeros((wl["probes"], 4), dtype=np.float32)
+    Q[:, :3] = pr.points
+    Ph = torch.from_numpy(P).pin_memory()
+    Qh = torch.from_numpy(Q).pin_memory()
+    Pd, Qd = Ph.to(dev), Qh.to(dev)
+    for _ in range(args.warmup):
+        d = rbf.density_measures(ctx, Pd, Qd)
+    torch.cuda.synchronize()
+    steps = max(args.steps, 100)     # a step lasts a few ms: enough of them for the clock samples
+    l0 = rbf.launch_count()
+    with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            d = rbf.density_measures(ctx, Pd, Qd)
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    launches = rbf.launch_count() - l0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        d = rbf.density_measures(ctx, Ph.to(dev, non_blocking=True), Qh.to(dev, non_blocking=True))
+    torch.cuda.synchronize()
+    ms_e2e = 1e3 * (time.perf_counter() - t0) / steps
+    q = wl["N"] + wl["probes"]
+    if rank == 0:
+        out = {"metric": "nearest-neighbour queries/s (density measures: separation, h_max, fill distance)",
+               "value": q / (ms * 1e-3), "unit": "queries/s", "n_gpus": 1, "steps": steps,
+               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": wl["desc"], "points": wl["N"], "probes": wl["probes"],
+                          "cell": d["cell"]},
+               "result": {k: d[k] for k in ("q", "h_max", "mean_nn", "fill", "sigma_q", "sigma_fill", "sigma_hmax")},
+               "e2e": {"value": q / (ms_e2e * 1e-3), "unit": "queries/s", "ms_per_step": ms_e2e,
+                       "h2d_bytes_per_step": Ph.numel() * 4 + Qh.numel() * 4, "d2h_bytes_per_step": 64},
+               "gpu_launches": launches, "clocks": clk.summary()}
+        print(json.dumps(out))
+    return 0
+
+
+def run_density_reference(args, wl):
+    """The oracle's brute-force nearest neighbours on a bounded sample of the queries."""
+    import numpy as np
+    import oracle
+    import synth
+    rank, world, _ = dist_setup()
+    if rank != 0:
+        return 0
+    X = synth.torus(wl["N"], noise=1e-3, seed=0).points.astype(np.float32).astype(np.float64)
+    rows = min(args.ref_rows, 200)
+    rng = np.random.default_rng(0)
+    oracle.nn_distances(X, rng.choice(len(X), max(10, rows // 10), replace=False))   # warm-up
+    t = 0.0
+    for k in range(args.steps):
+        r = np.random.default_rng(k + 1).choice(len(X), rows, replace=False)
+        t0 = time.perf_counter()
+        oracle.nn_distances(X, r)
+        t += time.perf_counter() - t0
+    v = rows * args.steps / t
+    out = {"impl": "reference", "metric": "nearest-neighbour queries/s (density measures: separation, h_max, "
+                                          "fill distance)",
+           "value": v, "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "config": {"workload": wl["desc"]},
+           "cpu_baseline": {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{rows} sampled points per step, brute force over all {len(X):,} points"},
+           "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
 def run_batch(args, wl):
     """C4: many clouds solved together (rbf_batch_*): centres and plans per cloud,
     the batch, the Schwarz subdomain size chosen by the autotuner, then the
@@ -452,6 +543,8 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.workload == "batch512":
         return run_batch(args, wl)
+    if args.workload == "density":
+        return run_density_reference(args, wl) if args.impl == "reference" else run_density(args, wl)
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_ours(args, wl)

@@ -275,6 +275,33 @@ rbf_status rbf_solve(rbf_ctx *ctx, const float *centers, const float *targets, i
                      rbf_report *report, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Density measures of the cloud (Sec. IV), for choosing sigma: nearest-neighbour
+ * distances, the separation distance (Eq. sepDist), h_max, and the fill
+ * distance (Eq. fillDist) over caller-given probe points of the domain Omega,
+ * with the paper's sigma rules.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double q;            /* separation distance 1/2 min_{i!=j} |x_i - x_j| (0 with duplicate points) */
+    double h_max;        /* max_j min_{i!=j} |x_i - x_j| */
+    double mean_nn;      /* mean nearest-neighbour distance */
+    double fill;         /* max over the probes of the distance to the nearest point; NaN without probes */
+    double sigma_q;      /* 2 q (Eq. h1) */
+    double sigma_fill;   /* fill sqrt(2) (Eq. h2) */
+    double sigma_hmax;   /* h_max sqrt(2), the fill distance estimate of Eq. hmax */
+    float cell;          /* cell edge the search used */
+} rbf_density;
+
+/* points: n float4 (x, y, z, unused), probes: m float4 or NULL (m = 0), device,
+ * 16-byte aligned; cell: search cell edge, <= 0 chooses one; nn: NULL or n
+ * floats receiving each point's nearest-neighbour distance (caller order).
+ * Distances are float32 (exact nearest neighbour, float32 arithmetic).
+ * Synchronises `stream`.  Errors: RBF_ERR_INVALID (n < 2, non-finite
+ * coordinates, null or misaligned pointers), RBF_ERR_UNSUPPORTED (extent too
+ * large for the binning), RBF_ERR_OOM, RBF_ERR_CUDA. */
+rbf_status rbf_density_measures(rbf_ctx *ctx, const float *points, int64_t n, const float *probes, int64_t m,
+                                float cell, float *nn, rbf_density *out, void *stream);
+
+/* ------------------------------------------------------------------------
  * Step 3 (Eq. matxvet): P_f at the nodes of a structured grid,
  * xi = lo + i (hi - lo)/(dims - 1) per axis (dims = 1 puts the node at lo),
  * written x fastest: f[(iz * dims[1] + iy) * dims[0] + ix].  The sum uses the

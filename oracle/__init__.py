@@ -506,13 +506,14 @@ def mlp_block_data(Cs, sigma, lam, block_ids, R, block=64):
 
 
 # ---------------------------------------------------------------- density measures
-def nn_distances(X: np.ndarray, rows=None, chunk: int = 2048) -> np.ndarray:
+def nn_distances(X: np.ndarray, rows=None, chunk: int = 0) -> np.ndarray:
     """Distance from each point (or each point of `rows`) to its nearest other point
     of X, by brute force over all points (the min over i != j in the separation
     distance of Eq. sepDist and in h_max of Sec. IV).  A duplicate point has
     distance 0."""
     X = np.asarray(X, dtype=np.float64)
     idx = np.arange(len(X)) if rows is None else np.asarray(rows)
+    chunk = chunk or max(1, (1 << 24) // max(1, len(X)))   # rows per pass: about 400 MB of temporaries
     out = np.empty(len(idx))
     for s in range(0, len(idx), chunk):
         r = idx[s:s + chunk]
@@ -522,11 +523,12 @@ def nn_distances(X: np.ndarray, rows=None, chunk: int = 2048) -> np.ndarray:
     return out
 
 
-def fill_distance(X: np.ndarray, probes: np.ndarray, chunk: int = 2048) -> float:
+def fill_distance(X: np.ndarray, probes: np.ndarray, chunk: int = 0) -> float:
     """Eq. fillDist with the sup over the domain replaced by a max over the given
     probe points of the domain: max_p min_j |p - x_j| (brute force)."""
     X = np.asarray(X, dtype=np.float64)
     P = np.asarray(probes, dtype=np.float64)
+    chunk = chunk or max(1, (1 << 24) // max(1, len(X)))
     h = 0.0
     for s in range(0, len(P), chunk):
         d2 = ((P[s:s + chunk, None, :] - X[None, :, :]) ** 2).sum(-1)

@@ -35,6 +35,7 @@ EXPORTS = (
     "rbf_build_centers", "rbf_plan_create", "rbf_plan_destroy", "rbf_plan_get_info", "rbf_plan_export_binning",
     "rbf_matvec", "rbf_count_pairs", "rbf_residual", "rbf_schwarz_setup", "rbf_schwarz_apply",
     "rbf_plan_solve", "rbf_solve", "rbf_plan_eval_grid", "rbf_count_grid_pairs", "rbf_eval_grid",
+    "rbf_density_measures",
     "rbf_matvec_dense_noalloc",
     "rbf_batch_create", "rbf_batch_destroy", "rbf_batch_size", "rbf_batch_matvec", "rbf_batch_solve",
     "rbf_batch_autotune",
@@ -99,6 +100,12 @@ class ProbeResult(ctypes.Structure):
                 ("mma_commit_cycles", ctypes.c_double), ("mma_commit4_cycles", ctypes.c_double)]
 
 
+class Density(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_double), ("h_max", ctypes.c_double), ("mean_nn", ctypes.c_double),
+                ("fill", ctypes.c_double), ("sigma_q", ctypes.c_double), ("sigma_fill", ctypes.c_double),
+                ("sigma_hmax", ctypes.c_double), ("cell", ctypes.c_float)]
+
+
 class BatchStats(ctypes.Structure):
     _fields_ = [("ms_setup", ctypes.c_double), ("ms_solve", ctypes.c_double), ("graph_nodes", ctypes.c_int64),
                 ("recaptured", ctypes.c_int), ("persistent_ctas", ctypes.c_int), ("work_items", ctypes.c_int64),
@@ -126,6 +133,7 @@ def lib() -> ctypes.CDLL:
         "rbf_version": ([], I),
         "rbf_launch_count": ([], I64),
         "rbf_probe_peaks": ([I, ctypes.POINTER(ProbeResult)], I),
+        "rbf_density_measures": ([P, P, I64, P, I64, F, P, ctypes.POINTER(Density), P], I),
         "rbf_status_string": ([I], ctypes.c_char_p),
         "rbf_ctx_create": ([ctypes.POINTER(P), I], I),
         "rbf_ctx_destroy": ([P], I),
@@ -232,6 +240,31 @@ def probe_peaks(device: int = 0) -> dict:
     if st != RBF_OK:
         raise RbfError(st, "rbf_probe_peaks")
     return {f: getattr(r, f) for f, _ in r._fields_}
+
+
+def density_measures(ctx: Context, points, probes=None, cell: float = 0.0, return_nn: bool = False, stream=None):
+    """Density measures of Sec. IV on device float4 points (n, 4): separation distance,
+    h_max, mean nearest-neighbour distance, fill distance over probe points (m, 4),
+    and the paper's sigma rules.  Returns a dict (and the nearest-neighbour
+    distances when return_nn)."""
+    import torch
+    _req(points, torch.float32, "points")
+    if points.dim() != 2 or points.shape[1] != 4:
+        raise ValueError("points must be (n, 4) float32")
+    n = int(points.shape[0])
+    m = 0
+    if probes is not None:
+        _req(probes, torch.float32, "probes")
+        if probes.dim() != 2 or probes.shape[1] != 4:
+            raise ValueError("probes must be (m, 4) float32")
+        m = int(probes.shape[0])
+    nn = torch.empty(n, dtype=torch.float32, device=points.device) if return_nn else None
+    d = Density()
+    ctx.check(lib().rbf_density_measures(ctx._h, _ptr(points), n, _ptr(probes) if m else None, m, float(cell),
+                                         _ptr(nn) if return_nn else None, ctypes.byref(d), _stream(stream)),
+              "rbf_density_measures")
+    out = {f: getattr(d, f) for f, _ in d._fields_}
+    return (out, nn) if return_nn else out
 
 
 def build_centers(ctx: Context, pts, nrm, delta: float = 0.0, target: float = 0.0, stream=None):

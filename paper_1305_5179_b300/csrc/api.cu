@@ -337,6 +337,19 @@ rbf_status rbf_count_grid_pairs(rbf_plan *P, const rbf_grid *g, int64_t *count, 
     });
 }
 
+rbf_status rbf_density_measures(rbf_ctx *ctx, const float *points, int64_t n, const float *probes, int64_t m,
+                                float cell, float *nn, rbf_density *out, void *stream) {
+    return guarded(ctx, [&]() {
+        RBF_CHECK(points && out && aligned16(points), RBF_ERR_INVALID,
+                  "points must be a 16-byte aligned device pointer, out non-null");
+        RBF_CHECK(m == 0 || (probes && aligned16(probes)), RBF_ERR_INVALID, "probes must be 16-byte aligned");
+        RBF_CHECK(n < (1LL << 31) - 1 && m < (1LL << 31) - 1, RBF_ERR_INVALID, "n or m out of range");
+        RBF_CHECK(std::isfinite(cell), RBF_ERR_INVALID, "cell must be finite");
+        density_measures(ctx, (const float4 *)points, n, (const float4 *)probes, m, cell, nn, out, S(stream));
+        return RBF_OK;
+    });
+}
+
 rbf_status rbf_eval_grid(rbf_ctx *ctx, const float *centers, const double *weights, int64_t n,
                          const rbf_plan_params *pp, const rbf_grid *g, float *f, void *stream) {
     return guarded(ctx, [&]() {

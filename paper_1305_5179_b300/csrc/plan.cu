@@ -590,7 +590,20 @@ static int64_t build_runs(rbf_plan *P, int len, PBuf<int2> &runs, PBuf<int32_t> 
     return total;
 }
 
-void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s) {
+void plan_sorted_copy(const rbf_plan *P, const float4 *pts, int64_t m, float4 *sorted, cudaStream_t s) {
+    DevBuf<uint32_t> keys;
+    DevBuf<int32_t> order;
+    keys.alloc(m, s);
+    order.alloc(m, s);
+    k_keys<<<grid_for(m), kThreads, 0, s>>>(pts, m, P->lo[0], P->lo[1], P->lo[2], P->inv,
+                                            (uint32_t)((1 << P->nbits) - 1), keys.p, order.p);
+    RBF_LAUNCHED();
+    radix_sort_pairs(keys.p, order.p, m, 3 * P->nbits, s);
+    k_gather_pos<<<grid_for(m), kThreads, 0, s>>>(pts, order.p, m, sorted);
+    RBF_LAUNCHED();
+}
+
+void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s, bool binning_only) {
     const int64_t n = P->n;
     bool finite = bbox_host((const float *)centers, n, 4, P->lo, P->hi, s);
     RBF_CHECK(finite, RBF_ERR_INVALID, "non-finite centre coordinate");
@@ -648,6 +661,7 @@ void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s) {
     P->pos.alloc(n, s);
     k_gather_pos<<<grid_for(n), kThreads, 0, s>>>(centers, P->perm.p, n, P->pos.p);
     RBF_LAUNCHED();
+    if (binning_only) return;
 
     // 3: k-d refinement inside each cell (runs of <= kKdMax), then source blocks,
     //    target tiles and their boxes

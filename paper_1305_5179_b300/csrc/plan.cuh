@@ -84,7 +84,12 @@ struct rbf_plan {
 };
 
 // plan.cu
-void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s);
+// binning_only: stop after the sorted positions and the cell table (no blocks, tiles
+// or pair list).
+void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s, bool binning_only = false);
+// Copy of m points (float4, w cleared) in the order of their keys on the plan's grid
+// (points outside the grid clamp to its border cells).
+void plan_sorted_copy(const rbf_plan *P, const float4 *pts, int64_t m, float4 *sorted, cudaStream_t s);
 // Pair list of target tiles given by boxes (lo, hi per tile; qlo, qhi per quarter of
 // 32 targets, 4 per tile) against the plan's source blocks.
 void build_pairlist(rbf_plan *P, const float4 *tlo, const float4 *thi, const float4 *qlo, const float4 *qhi,
@@ -152,6 +157,10 @@ void mlp_adam_step(rbf_mlp *M, float lr, cudaStream_t s);
 int64_t mlp_make_data(rbf_plan *P, float lambda, const int32_t *block_ids, const float *R, int64_t ns, float *X,
                       float *Y, cudaStream_t s);
 int64_t mlp_apply(rbf_mlp *M, rbf_plan *P, float lambda, int core, const double *vd, float *z, cudaStream_t s);
+
+// density.cu
+void density_measures(rbf_ctx *ctx, const float4 *pts, int64_t n, const float4 *probes, int64_t m, float cell,
+                      float *nn, rbf_density *out, cudaStream_t s);
 
 // fgmres.cu
 rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_params &p, double *x_caller,
