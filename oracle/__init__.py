@@ -549,3 +549,91 @@ def density_measures(X: np.ndarray, probes=None) -> dict:
     out["sigma_fill"] = out["fill"] * np.sqrt(2.0)
     out["sigma_hmax"] = out["h_max"] * np.sqrt(2.0)
     return out
+
+
+# ---------------------------------------------------------------- isosurface (Algorithm 1, step 4)
+# The paper renders P_f = 0 with MATLAB's isosurface (marching cubes).  The oracle
+# extracts the same level set by marching tetrahedra: every grid cell is cut into
+# the 6 tetrahedra around its diagonal from corner (0,0,0) to (1,1,1) (the same cut
+# in every cell, so neighbouring cells' faces match), and every tetrahedron whose
+# corners straddle the level contributes 1 or 2 triangles with corners on its edges.
+_CUBE = np.array([[(c >> 0) & 1, (c >> 1) & 1, (c >> 2) & 1] for c in range(8)])   # corner bit c -> (x, y, z)
+
+
+def _kuhn_tets():
+    """The 6 tetrahedra (corner indices) 0 -> 0 + e_a -> 0 + e_a + e_b -> 7 for the
+    orders (a, b, c) of the axes, each listed with positive orientation."""
+    import itertools
+    tets = []
+    for a, b, _ in itertools.permutations((1, 2, 4)):
+        t = [0, a, a | b, 7]
+        v = _CUBE[t].astype(np.float64)
+        if np.linalg.det(np.stack([v[1] - v[0], v[2] - v[0], v[3] - v[0]])) < 0:
+            t[2], t[3] = t[3], t[2]
+        tets.append(t)
+    return tets
+
+
+# even permutations putting a given corner (or pair of corners) first
+_FIRST = {0: (0, 1, 2, 3), 1: (1, 0, 3, 2), 2: (2, 3, 0, 1), 3: (3, 2, 1, 0)}
+_PAIR = {(0, 1): (0, 1, 2, 3), (0, 2): (0, 2, 3, 1), (0, 3): (0, 3, 1, 2),
+         (1, 2): (1, 2, 0, 3), (1, 3): (1, 3, 2, 0), (2, 3): (2, 3, 0, 1)}
+
+
+def isosurface(f: np.ndarray, lo, hi, iso: float = 0.0):
+    """Triangles (ntri, 3, 3) of the level set {f = iso} of the grid field f
+    (shape (Gz, Gy, Gx), x fastest, nodes lo + i (hi - lo)/(G - 1)), in the order
+    (cell in x-fastest order, tetrahedron, triangle); a corner is inside when
+    f < iso; an edge point is p_a + (iso - f_a)/(f_b - f_a) (p_b - p_a) with a the
+    edge's corner of smaller node index; every
+    triangle's normal (v1 - v0) x (v2 - v0) points from inside to outside (a
+    corner exactly at the level counts as outside and can give zero-area triangles).
+    Returns (triangles, per-cell triangle counts of shape (Gz-1, Gy-1, Gx-1))."""
+    f = np.asarray(f, dtype=np.float64)
+    Gz, Gy, Gx = f.shape
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    dims = np.array([Gx, Gy, Gz])
+    step = np.where(dims > 1, (hi - lo) / np.maximum(dims - 1, 1), 0.0)
+    tets = _kuhn_tets()
+    counts = np.zeros((Gz - 1, Gy - 1, Gx - 1), dtype=np.int64)
+    per_cell = {}
+    for kz in range(Gz - 1):
+        for ky in range(Gy - 1):
+            for kx in range(Gx - 1):
+                vals = np.array([f[kz + _CUBE[c, 2], ky + _CUBE[c, 1], kx + _CUBE[c, 0]] for c in range(8)])
+                inside = vals < iso
+                if inside.all() or not inside.any():
+                    continue
+                pos = lo + (np.array([kx, ky, kz]) + _CUBE) * step
+                tris = []
+                for t in tets:
+                    vin = inside[t]
+                    nin = int(vin.sum())
+                    if nin == 0 or nin == 4:
+                        continue
+
+                    def cut(i, j):
+                        # interpolated from the corner with the smaller node index, so that
+                        # an edge shared by several tetrahedra or cells yields one point
+                        a, b = min(t[i], t[j]), max(t[i], t[j])
+                        s = (iso - vals[a]) / (vals[b] - vals[a])
+                        return pos[a] + s * (pos[b] - pos[a])
+                    if nin in (1, 3):
+                        lone = [i for i in range(4) if vin[i] == (nin == 1)][0]
+                        p = _FIRST[lone]
+                        tri = [cut(p[0], p[1]), cut(p[0], p[2]), cut(p[0], p[3])]
+                        if nin == 3:          # the lone corner is outside: the normal must point to it
+                            tri = [tri[0], tri[2], tri[1]]
+                        tris.append(tri)
+                    else:
+                        pair = tuple(i for i in range(4) if vin[i])
+                        p = _PAIR[pair]
+                        e_ac, e_ad, e_bd, e_bc = cut(p[0], p[2]), cut(p[0], p[3]), cut(p[1], p[3]), cut(p[1], p[2])
+                        tris.append([e_ac, e_ad, e_bd])
+                        tris.append([e_ac, e_bd, e_bc])
+                counts[kz, ky, kx] = len(tris)
+                per_cell[(kz, ky, kx)] = tris
+    out = [tri for key in sorted(per_cell) for tri in per_cell[key]]
+    T = np.array(out, dtype=np.float64).reshape(-1, 3, 3)
+    return T, counts

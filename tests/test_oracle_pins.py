@@ -487,3 +487,75 @@ def test_density_nearest_neighbours_match_a_kd_tree():
     two = np.array([[0.0, 0.0, 0.0], [0.3, 0.4, 0.0]])
     t = oracle.density_measures(two)
     assert t["q"] == pytest.approx(0.25) and t["h_max"] == pytest.approx(0.5)
+
+
+# ---------------------------------------------------------------- Algorithm 1, step 4: the level set
+def _poly_area_clip(square, keep):
+    """Area of a convex polygon clipped by half-planes keep(p) >= 0 (linear in p),
+    Sutherland-Hodgman, for the reference area of a plane section."""
+    pts = square
+    for h in keep:
+        out = []
+        for k in range(len(pts)):
+            p, q = np.array(pts[k]), np.array(pts[(k + 1) % len(pts)])
+            hp, hq = h(p), h(q)
+            if hp >= 0:
+                out.append(p)
+            if (hp >= 0) != (hq >= 0):
+                out.append(p + (hp / (hp - hq)) * (q - p))
+        pts = out
+    x, y = np.array(pts).T
+    return 0.5 * abs(np.dot(x, np.roll(y, -1)) - np.dot(y, np.roll(x, -1)))
+
+
+def test_isosurface_of_a_linear_field_is_its_plane():
+    """For f = a.x - c the interpolation along every edge is exact: every vertex lies
+    on the plane, every normal points along a, and the triangles tile the plane's
+    section of the box (area from an independent polygon clip)."""
+    a = np.array([0.3, -0.5, 0.8])
+    c = 0.1
+    lo, hi, G = np.array([-1.0, -0.7, -0.6]), np.array([0.9, 1.1, 0.8]), (13, 11, 9)
+    xs = [np.linspace(lo[d], hi[d], G[d]) for d in range(3)]
+    Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    f = a[0] * X + a[1] * Y + a[2] * Z - c
+    T, counts = oracle.isosurface(f, lo, hi)
+    assert len(T) == counts.sum() > 0
+    assert np.abs(T @ a - c).max() <= 1e-12
+    n = np.cross(T[:, 1] - T[:, 0], T[:, 2] - T[:, 0])
+    live = np.linalg.norm(n, axis=1) > 1e-14      # nodes exactly on the plane give zero-area triangles
+    assert live.sum() > 0.9 * len(T) and np.all(n[live] @ a > 0)
+    area = 0.5 * np.linalg.norm(n, axis=1).sum()
+    # section area = area of its projection on the xy-plane (z between lo and hi) x |a| / |a_z|
+    square = [(lo[0], lo[1]), (hi[0], lo[1]), (hi[0], hi[1]), (lo[0], hi[1])]
+    zof = lambda p: (c - a[0] * p[0] - a[1] * p[1]) / a[2]
+    proj = _poly_area_clip(square, [lambda p: zof(p) - lo[2], lambda p: hi[2] - zof(p)])
+    assert area == pytest.approx(proj * np.linalg.norm(a) / abs(a[2]), rel=1e-12)
+
+
+def _mesh_topology(T, digits=9):
+    key = {}
+    V = np.round(T.reshape(-1, 3), digits)
+    ids = np.array([key.setdefault(tuple(v), len(key)) for v in V]).reshape(-1, 3)
+    edges = {}
+    for t in ids:
+        for i in range(3):
+            e = (min(t[i], t[(i + 1) % 3]), max(t[i], t[(i + 1) % 3]))
+            edges[e] = edges.get(e, 0) + 1
+    return len(key), edges, len(ids)
+
+
+@pytest.mark.parametrize("shape,chi", [("sphere", 2), ("torus", 0)])
+def test_isosurface_is_a_closed_surface(shape, chi):
+    """The level set of a signed distance to a sphere or a torus is a closed
+    2-manifold: every edge borders exactly two triangles, and the Euler
+    characteristic V - E + F is 2 for the sphere and 0 for the torus."""
+    g = np.linspace(-1.0, 1.0, 23)
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    if shape == "sphere":
+        f = np.sqrt(X ** 2 + Y ** 2 + Z ** 2) - 0.63
+    else:
+        f = np.sqrt((np.sqrt(X ** 2 + Y ** 2) - 0.55) ** 2 + Z ** 2) - 0.23
+    T, _ = oracle.isosurface(f, (-1.0,) * 3, (1.0,) * 3)
+    V, E, F = _mesh_topology(T)
+    assert all(c == 2 for c in E.values())
+    assert V - len(E) + F == chi
