@@ -48,6 +48,11 @@ WORKLOADS = {
     "density": dict(desc="density measures (Sec. IV) of the 1,000,000-point torus cloud: nearest neighbour of every "
                          "point and fill distance over 1,000,000 probe points on the noise-free torus",
                     N=1_000_000, probes=1_000_000),
+    "isosurface": dict(desc="level set P_f = 0 (Algorithm 1 step 4, triangle buffer) of the 256^3 grid field of the "
+                            "3,000,000-centre torus (weights from 20 RAS-FGMRES iterations), within 0.03 of the "
+                            "cloud (the surrounding volume M_ext^eps, eps = 3 delta)",
+                       N=1_000_000, delta=0.01, sigma=0.02, k=6.0, grid=256, core=96, block=128, shift=1.0,
+                       iters=20, m=20, precond="schwarz", band=0.03),
     "sphere1500": dict(desc="unit sphere N=1,500 -> 4,500 centres, untruncated", N=1500, delta=0.05, sigma=0.1,
                        k=0.0, grid=64, core=96, block=128, shift=1e-4, iters=50, m=50, precond="none"),
     "batch512": dict(desc="512 ellipsoids/tori, log-uniform 500-20,000 points each, delta 0.02, "
@@ -424,6 +429,77 @@ def run_density(args, wl):
     return 0
 
 
+def run_isosurface(args, wl):
+    """Row f2: rbf_isosurface (count pass, scan, emit pass) on the C2 grid field."""
+    import numpy as np
+    import torch
+    import paper_1305_5179_b300 as rbf
+
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    ctx = rbf.Context(local)
+    dev = torch.device("cuda", local)
+    cl = make_cloud(wl)
+    lo, hi = grid_box(cl.points, wl)
+    G = wl["grid"]
+    C, b, _ = rbf.build_centers(ctx, torch.from_numpy(cl.points).to(dev), torch.from_numpy(cl.normals).to(dev),
+                                delta=wl["delta"])
+    plan = rbf.Plan(ctx, C, sigma=wl["sigma"], k=wl["k"])
+    x, _ = plan.solve(b, m=wl["m"], max_it=wl["iters"], fixed_iterations=True, precond=wl["precond"],
+                      core=wl["core"], block=wl["block"], shift=wl["shift"], escalate=True)
+    f = plan.eval_grid(x, lo, hi, (G, G, G))
+    del plan
+    Xp = np.zeros((len(cl.points), 4), dtype=np.float32)
+    Xp[:, :3] = cl.points
+    Xd = torch.from_numpy(Xp).to(dev)
+    iso_kw = dict(points=Xd, band=wl["band"])
+    ntri_all = int(rbf.isosurface(ctx, f, lo, hi).shape[0])
+    for _ in range(args.warmup):
+        tri = rbf.isosurface(ctx, f, lo, hi, **iso_kw)
+    torch.cuda.synchronize()
+    steps = max(args.steps, 50)
+    l0 = rbf.launch_count()
+    with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            tri = rbf.isosurface(ctx, f, lo, hi, **iso_kw)
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    launches = rbf.launch_count() - l0
+    ntri = int(tri.shape[0])
+    cells = (G - 1) ** 3
+    # algorithmic bytes: the field read by each pass, the counts written and read back
+    # (count, scan, emit), the triangles written
+    nbytes = 2 * G ** 3 * 4 + 3 * cells * 4 + ntri * 36
+    peak = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))["hbm_gbs"]
+    fh = f.cpu()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        fd = fh.to(dev, non_blocking=True)
+        tri = rbf.isosurface(ctx, fd, lo, hi, **iso_kw)
+        th = tri.cpu()
+    ms_e2e = 1e3 * (time.perf_counter() - t0) / steps
+    if rank == 0:
+        out = {"metric": "grid cells/s (level set extraction: count, scan, emit)", "value": cells / (ms * 1e-3),
+               "unit": "cells/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic", "config": {"workload": wl["desc"], "grid": [G, G, G], "triangles": ntri,
+                                               "triangles_without_band": ntri_all, "band": wl["band"]},
+               "roofline": {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                            "frac": nbytes / (ms * 1e-3) / 1e9 / peak, "traffic": None,
+                            "bytes_per_launch_algorithmic": nbytes,
+                            "kernel": "k_iso_count + scan + k_iso_emit (one call)",
+                            "peak_basis": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth), of measured"},
+               "e2e": {"value": cells / (ms_e2e * 1e-3), "unit": "cells/s", "ms_per_step": ms_e2e,
+                       "h2d_bytes_per_step": G ** 3 * 4, "d2h_bytes_per_step": ntri * 36},
+               "gpu_launches": launches, "clocks": clk.summary()}
+        print(json.dumps(out))
+    return 0
+
+
 def run_density_reference(args, wl):
     """The oracle's brute-force nearest neighbours on a bounded sample of the queries."""
     import numpy as np
@@ -545,6 +621,8 @@ def main():
         return run_batch(args, wl)
     if args.workload == "density":
         return run_density_reference(args, wl) if args.impl == "reference" else run_density(args, wl)
+    if args.workload == "isosurface":
+        return run_isosurface(args, wl)
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_ours(args, wl)

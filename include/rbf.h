@@ -327,6 +327,27 @@ rbf_status rbf_eval_grid(rbf_ctx *ctx, const float *centers, const double *weigh
                          const rbf_plan_params *pp, const rbf_grid *g, float *f, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Step 4 of Algorithm 1 without the rendering: the level set {f = iso} of a grid
+ * field (as written by rbf_eval_grid) as a triangle buffer.  Marching tetrahedra
+ * over the six tetrahedra of each cell around its (0,0,0)-(1,1,1) diagonal;
+ * a node is inside when f < iso; an edge point is interpolated linearly from the
+ * edge's node of smaller index; each triangle (v0, v1, v2) has its normal
+ * (v1 - v0) x (v2 - v0) pointing from inside to outside; cells with a NaN node
+ * give none.  Triangles come in cell order (x fastest), then tetrahedron, then
+ * triangle.  With data points and band > 0 only cells whose centre lies within
+ * band of a data point contribute (the surrounding volume M_ext^eps of Sec.
+ * II.A.3; points = the cloud X, float4, device, 16-byte aligned).
+ *   f         : device float, dims[0] x dims[1] x dims[2], x fastest; dims >= 2
+ *   triangles : device float, 9 per triangle (x, y, z of v0, v1, v2), or NULL to
+ *               count only; capacity = triangles it can hold
+ *   ntri      : host, the number of triangles of the level set
+ * Synchronises `stream`.  Errors: RBF_ERR_INVALID (bad grid, non-finite iso,
+ * capacity below the count), RBF_ERR_OOM, RBF_ERR_CUDA. */
+rbf_status rbf_isosurface(rbf_ctx *ctx, const float *f, const rbf_grid *g, float iso, const float *points,
+                          int64_t npoints, float band, float *triangles, int64_t capacity, int64_t *ntri,
+                          void *stream);
+
+/* ------------------------------------------------------------------------
  * Learned block preconditioner (not in the paper: it stands in for the exact
  * subdomain solve of the restricted additive Schwarz method, Sec. III.A).
  * Blocks are the Schwarz subdomains of 64 centres without overlap.  Input of a

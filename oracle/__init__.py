@@ -580,14 +580,18 @@ _PAIR = {(0, 1): (0, 1, 2, 3), (0, 2): (0, 2, 3, 1), (0, 3): (0, 3, 1, 2),
          (1, 2): (1, 2, 0, 3), (1, 3): (1, 3, 2, 0), (2, 3): (2, 3, 0, 1)}
 
 
-def isosurface(f: np.ndarray, lo, hi, iso: float = 0.0):
+def isosurface(f: np.ndarray, lo, hi, iso: float = 0.0, points=None, band: float = 0.0):
     """Triangles (ntri, 3, 3) of the level set {f = iso} of the grid field f
     (shape (Gz, Gy, Gx), x fastest, nodes lo + i (hi - lo)/(G - 1)), in the order
     (cell in x-fastest order, tetrahedron, triangle); a corner is inside when
     f < iso; an edge point is p_a + (iso - f_a)/(f_b - f_a) (p_b - p_a) with a the
     edge's corner of smaller node index; every
     triangle's normal (v1 - v0) x (v2 - v0) points from inside to outside (a
-    corner exactly at the level counts as outside and can give zero-area triangles).
+    corner exactly at the level counts as outside and can give zero-area triangles;
+    a cell with a NaN node gives none).  With data points and band > 0 only cells
+    whose centre lies within `band` of a data point contribute: the surrounding
+    volume M_ext^eps = {x : d(x, M) <= eps} of Sec. II.A.3, with d(x, M) read as the
+    distance to the nearest data point.
     Returns (triangles, per-cell triangle counts of shape (Gz-1, Gy-1, Gx-1))."""
     f = np.asarray(f, dtype=np.float64)
     Gz, Gy, Gx = f.shape
@@ -596,16 +600,23 @@ def isosurface(f: np.ndarray, lo, hi, iso: float = 0.0):
     dims = np.array([Gx, Gy, Gz])
     step = np.where(dims > 1, (hi - lo) / np.maximum(dims - 1, 1), 0.0)
     tets = _kuhn_tets()
+    pts = np.asarray(points, dtype=np.float64)[:, :3] if band > 0 else None
     counts = np.zeros((Gz - 1, Gy - 1, Gx - 1), dtype=np.int64)
     per_cell = {}
     for kz in range(Gz - 1):
         for ky in range(Gy - 1):
             for kx in range(Gx - 1):
                 vals = np.array([f[kz + _CUBE[c, 2], ky + _CUBE[c, 1], kx + _CUBE[c, 0]] for c in range(8)])
+                if np.isnan(vals).any():          # a node left out of the evaluation
+                    continue
                 inside = vals < iso
                 if inside.all() or not inside.any():
                     continue
                 pos = lo + (np.array([kx, ky, kz]) + _CUBE) * step
+                if band > 0:
+                    centre = lo + (np.array([kx, ky, kz]) + 0.5) * step
+                    if ((pts - centre) ** 2).sum(1).min() > band * band:
+                        continue
                 tris = []
                 for t in tets:
                     vin = inside[t]

@@ -35,7 +35,7 @@ EXPORTS = (
     "rbf_build_centers", "rbf_plan_create", "rbf_plan_destroy", "rbf_plan_get_info", "rbf_plan_export_binning",
     "rbf_matvec", "rbf_count_pairs", "rbf_residual", "rbf_schwarz_setup", "rbf_schwarz_apply",
     "rbf_plan_solve", "rbf_solve", "rbf_plan_eval_grid", "rbf_count_grid_pairs", "rbf_eval_grid",
-    "rbf_density_measures",
+    "rbf_density_measures", "rbf_isosurface",
     "rbf_matvec_dense_noalloc",
     "rbf_batch_create", "rbf_batch_destroy", "rbf_batch_size", "rbf_batch_matvec", "rbf_batch_solve",
     "rbf_batch_autotune",
@@ -134,6 +134,7 @@ def lib() -> ctypes.CDLL:
         "rbf_launch_count": ([], I64),
         "rbf_probe_peaks": ([I, ctypes.POINTER(ProbeResult)], I),
         "rbf_density_measures": ([P, P, I64, P, I64, F, P, ctypes.POINTER(Density), P], I),
+        "rbf_isosurface": ([P, P, ctypes.POINTER(Grid), F, P, I64, F, P, I64, ctypes.POINTER(I64), P], I),
         "rbf_status_string": ([I], ctypes.c_char_p),
         "rbf_ctx_create": ([ctypes.POINTER(P), I], I),
         "rbf_ctx_destroy": ([P], I),
@@ -240,6 +241,33 @@ def probe_peaks(device: int = 0) -> dict:
     if st != RBF_OK:
         raise RbfError(st, "rbf_probe_peaks")
     return {f: getattr(r, f) for f, _ in r._fields_}
+
+
+def isosurface(ctx: Context, f, lo, hi, iso: float = 0.0, points=None, band: float = 0.0, stream=None):
+    """Step 4 without rendering: the triangles (ntri, 3, 3) of {f = iso} on the grid
+    field f of shape (Gz, Gy, Gx) with nodes lo + i (hi - lo)/(G - 1); with data
+    points (n, 4) and band > 0, only cells whose centre is within band of a point."""
+    import torch
+    _req(f, torch.float32, "f")
+    if f.dim() != 3:
+        raise ValueError("f must be (Gz, Gy, Gx)")
+    npts = 0
+    if points is not None:
+        _req(points, torch.float32, "points")
+        if points.dim() != 2 or points.shape[1] != 4:
+            raise ValueError("points must be (n, 4) float32")
+        npts = int(points.shape[0])
+    pp = _ptr(points) if npts else None
+    dims = (int(f.shape[2]), int(f.shape[1]), int(f.shape[0]))
+    g = _grid(lo, hi, dims)
+    n = ctypes.c_int64(0)
+    ctx.check(lib().rbf_isosurface(ctx._h, _ptr(f), ctypes.byref(g), float(iso), pp, npts, float(band), None, 0,
+                                   ctypes.byref(n), _stream(stream)), "rbf_isosurface")
+    tri = torch.empty((max(1, n.value), 3, 3), dtype=torch.float32, device=f.device)
+    if n.value:
+        ctx.check(lib().rbf_isosurface(ctx._h, _ptr(f), ctypes.byref(g), float(iso), pp, npts, float(band),
+                                       _ptr(tri), n.value, ctypes.byref(n), _stream(stream)), "rbf_isosurface")
+    return tri[:n.value]
 
 
 def density_measures(ctx: Context, points, probes=None, cell: float = 0.0, return_nn: bool = False, stream=None):

@@ -337,6 +337,20 @@ rbf_status rbf_count_grid_pairs(rbf_plan *P, const rbf_grid *g, int64_t *count, 
     });
 }
 
+rbf_status rbf_isosurface(rbf_ctx *ctx, const float *f, const rbf_grid *g, float iso, const float *points,
+                          int64_t npoints, float band, float *triangles, int64_t capacity, int64_t *ntri,
+                          void *stream) {
+    return guarded(ctx, [&]() {
+        RBF_CHECK(f && g && ntri, RBF_ERR_INVALID, "null pointer argument");
+        RBF_CHECK(!points || aligned16(points), RBF_ERR_INVALID, "points must be 16-byte aligned");
+        RBF_CHECK(npoints >= 0 && npoints < (1LL << 31) - 1, RBF_ERR_INVALID, "npoints out of range");
+        *ntri = isosurface(ctx, f, *g, iso, (const float4 *)points, npoints, band, triangles, capacity, S(stream));
+        RBF_CHECK(!triangles || *ntri <= capacity, RBF_ERR_INVALID, "triangle buffer holds %lld, the level set has %lld",
+                  (long long)capacity, (long long)*ntri);
+        return RBF_OK;
+    });
+}
+
 rbf_status rbf_density_measures(rbf_ctx *ctx, const float *points, int64_t n, const float *probes, int64_t m,
                                 float cell, float *nn, rbf_density *out, void *stream) {
     return guarded(ctx, [&]() {

@@ -158,6 +158,11 @@ int64_t mlp_make_data(rbf_plan *P, float lambda, const int32_t *block_ids, const
                       float *Y, cudaStream_t s);
 int64_t mlp_apply(rbf_mlp *M, rbf_plan *P, float lambda, int core, const double *vd, float *z, cudaStream_t s);
 
+// isosurface.cu: returns the triangle count; writes the triangles when tri != nullptr
+// and capacity is enough
+int64_t isosurface(rbf_ctx *ctx, const float *f, const rbf_grid &g, float iso, const float4 *pts, int64_t npts,
+                   float band, float *tri, int64_t capacity, cudaStream_t s);
+
 // density.cu
 void density_measures(rbf_ctx *ctx, const float4 *pts, int64_t n, const float4 *probes, int64_t m, float cell,
                       float *nn, rbf_density *out, cudaStream_t s);

@@ -559,3 +559,24 @@ def test_isosurface_is_a_closed_surface(shape, chi):
     V, E, F = _mesh_topology(T)
     assert all(c == 2 for c in E.values())
     assert V - len(E) + F == chi
+
+
+def test_isosurface_band_keeps_only_cells_near_the_data():
+    """With a band, a cell contributes only when its centre is within the band of a
+    data point: a plane's level set restricted to a disc of data points keeps
+    exactly the cells whose centres are within the band, and the full level set's
+    cells are kept when the band exceeds the box diagonal."""
+    lo, hi, G = np.array([-1.0, -1.0, -1.0]), np.array([1.0, 1.0, 1.0]), 17
+    g = np.linspace(-1, 1, G)
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    f = Z - 0.03
+    T_all, c_all = oracle.isosurface(f, lo, hi)
+    pts = np.array([[0.0, 0.0, 0.03]])                     # one data point on the plane
+    T_b, c_b = oracle.isosurface(f, lo, hi, points=pts, band=0.3)
+    step = (hi - lo) / (G - 1)
+    kz, ky, kx = np.nonzero(c_all)
+    centres = lo + (np.stack([kx, ky, kz], 1) + 0.5) * step
+    near = ((centres - pts[0]) ** 2).sum(1) <= 0.09
+    assert np.array_equal(c_b[kz, ky, kx] > 0, near) and 0 < near.sum() < len(near)
+    T_w, c_w = oracle.isosurface(f, lo, hi, points=pts, band=4.0)
+    assert np.array_equal(c_w, c_all)
