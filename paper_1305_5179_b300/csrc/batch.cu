@@ -469,6 +469,7 @@ rbf_batch *batch_create(rbf_ctx *ctx, rbf_plan *const *plans, int nplans, cudaSt
             v.tiles = P->tiles.p;
             v.blk = P->blk.p;
             v.ent = P->pl.ent.p;
+            v.ebi = P->pl.ebi.p;
             v.seg = Bt->bseg[b].p;
             v.tile_seg = Bt->btile_seg[b].p;
             v.perm = P->perm.p;

@@ -10,6 +10,7 @@ struct PlanView {
     const int2 *tiles;
     const int2 *blk;
     const int32_t *ent;
+    const int2 *ebi;       // per entry (block start, count | quarter codes << 8)
     const int4 *seg;
     const int32_t *tile_seg;
     const int32_t *perm;

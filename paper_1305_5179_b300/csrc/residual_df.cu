@@ -107,11 +107,15 @@ __device__ __forceinline__ df block_terms(float px, float py, float pz, const fl
     return acc;
 }
 
-// One segment of one problem: acc over the segment's blocks for target thread.
+// One segment of one problem: acc over the segment's blocks for target thread.  Warp
+// w holds the tile's targets 32w .. 32w + 31, so it skips a block whose pair-list
+// code for that quarter says no pair is within the cut-off (those terms are zero).
 __device__ __forceinline__ double resid_segment(const float4 *__restrict__ pos, const int2 tl, const double *__restrict__ x,
                                                 const int2 *__restrict__ blk, const int32_t *__restrict__ ent,
-                                                const int4 sg, const DfConst &kc, float4 *s_p, float2 *s_w,
-                                                const float2 *s_tab, bool &valid, int64_t &i) {
+                                                const int2 *__restrict__ ebi, const int4 sg, const DfConst &kc,
+                                                float4 *s_p, float2 *s_w, const float2 *s_tab, bool &valid,
+                                                int64_t &i) {
+    const int quarter_shift = 8 + 2 * (int)(threadIdx.x >> 5);
     i = (int64_t)tl.x + threadIdx.x;
     valid = (int)threadIdx.x < tl.y;
     float4 p = valid ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -126,6 +130,7 @@ __device__ __forceinline__ double resid_segment(const float4 *__restrict__ pos, 
             s_w[threadIdx.x] = make_float2(xh, (float)(xv - (double)xh));
         }
         __syncthreads();
+        if (ebi && ((ebi[e].y >> quarter_shift) & 3) == 0) continue;
         df a = block_terms(p.x, p.y, p.z, s_p, s_w, bi.y, kc, s_tab);
         acc += (double)a.h + (double)a.l;
     }
@@ -135,7 +140,8 @@ __device__ __forceinline__ double resid_segment(const float4 *__restrict__ pos, 
 __global__ void __launch_bounds__(kT) k_resid_df(const float4 *__restrict__ pos, const int2 *__restrict__ tiles,
                                                  const double *__restrict__ x,
                                                  const int2 *__restrict__ blk, const int32_t *__restrict__ ent,
-                                                 const int4 *__restrict__ seg, int64_t n, DfConst kc,
+                                                 const int2 *__restrict__ ebi, const int4 *__restrict__ seg,
+                                                 int64_t n, DfConst kc,
                                                  const float *__restrict__ b, double *__restrict__ out,
                                                  double *__restrict__ part) {
     __shared__ float4 s_p[kBlk];
@@ -145,7 +151,7 @@ __global__ void __launch_bounds__(kT) k_resid_df(const float4 *__restrict__ pos,
     const int4 sg = seg[blockIdx.x];
     bool valid;
     int64_t i;
-    double acc = resid_segment(pos, tiles[sg.x], x, blk, ent, sg, kc, s_p, s_w, s_tab, valid, i);
+    double acc = resid_segment(pos, tiles[sg.x], x, blk, ent, ebi, sg, kc, s_p, s_w, s_tab, valid, i);
     if (sg.w) {
         if (valid) out[i] = (double)b[i] - acc;
     } else {
@@ -191,7 +197,8 @@ __global__ void __launch_bounds__(kT) k_resid_df_batched(const PlanView *__restr
     kc.Ll = Ll;
     bool valid;
     int64_t i;
-    double acc = resid_segment(v.pos, v.tiles[sg.x], xs + v.off, v.blk, v.ent, sg, kc, s_p, s_w, s_tab, valid, i);
+    double acc = resid_segment(v.pos, v.tiles[sg.x], xs + v.off, v.blk, v.ent, v.ebi, sg, kc, s_p, s_w, s_tab, valid,
+                               i);
     if (sg.w) {
         if (valid) rs[v.off + i] = (double)bs[v.off + i] - acc;
     } else {
@@ -265,8 +272,8 @@ void residual_binned_df(rbf_plan *P, const float *bs, const double *xs, double *
     DevBuf<double> part;
     if (pl.any_split) part.alloc((size_t)pl.nseg * kChunk, s);
     if (pl.nseg > 0) {
-        k_resid_df<<<(unsigned)pl.nseg, kT, 0, s>>>(P->pos.p, P->tiles.p, xs, P->blk.p, pl.ent.p, pl.seg.p, P->n, kc,
-                                                    bs, rs, part.p);
+        k_resid_df<<<(unsigned)pl.nseg, kT, 0, s>>>(P->pos.p, P->tiles.p, xs, P->blk.p, pl.ent.p, pl.ebi.p, pl.seg.p,
+                                                    P->n, kc, bs, rs, part.p);
         RBF_LAUNCHED();
     }
     if (pl.any_split) {
