@@ -58,6 +58,10 @@ WORKLOADS = {
                               "a 150^3 grid (M = 3,375,000) over [-1.2, 1.2]^3",
                          N=8012, delta=0.05, sigma=0.157, k=0.0, grid=150, iters=50, m=50,
                          paper_eval_s=7.9468, paper_solve_s=815.09),
+    "assembled": dict(desc="assembled truncated matrix (Algorithm 2, CSR float32 values, int32 columns) against the "
+                           "matrix-free product, on the sector 0 <= theta < 0.6 of the 1,000,000-point torus "
+                           "(95,492 points -> 286,476 centres)",
+                      N=95_492, theta=0.6, delta=0.01, sigma=0.02, k=6.0),
     "sphere1500": dict(desc="unit sphere N=1,500 -> 4,500 centres, untruncated", N=1500, delta=0.05, sigma=0.1,
                        k=0.0, grid=64, core=96, block=128, shift=1e-4, iters=50, m=50, precond="none"),
     "batch512": dict(desc="512 ellipsoids/tori, log-uniform 500-20,000 points each, delta 0.02, "
@@ -377,6 +381,102 @@ def run_ours(args, wl):
     return 0
 
 
+def run_assembled(args, wl):
+    """Row f3: the truncated matrix assembled entry by entry (rbf_plan_assemble) and its
+    CSR product (rbf_spmv), timed beside the matrix-free product (rbf_matvec) on the
+    same plan.  The CSR product streams 8 bytes per stored entry: HBM-bound."""
+    import numpy as np
+    import torch
+    import paper_1305_5179_b300 as rbf
+
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = rbf.Context(local)
+    stream = torch.cuda.current_stream()
+    if args.theta:   # a smaller sector of the same density (profiling captures)
+        wl = dict(wl, theta=args.theta, N=int(1_000_000 * args.theta / (2 * math.pi)),
+                  desc=wl["desc"].split(", on the sector")[0] + f", on the sector 0 <= theta < {args.theta}")
+    cl = make_cloud(wl)
+    C, b, _ = rbf.build_centers(ctx, torch.from_numpy(cl.points).to(dev), torch.from_numpy(cl.normals).to(dev),
+                                delta=wl["delta"])
+    plan = rbf.Plan(ctx, C, sigma=wl["sigma"], k=wl["k"])
+    n = plan.n
+    pairs = plan.count_pairs()
+
+    def timed(fn, reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    nnz, stored = plan.assemble()                   # untimed first build (allocation of the matrix)
+    plan.release_csr()
+    ms_asm = timed(lambda: plan.assemble(), 1)
+    csr_bytes = stored * 8 + (n + 1) * 8
+    z_h = torch.from_numpy(np.random.default_rng(0).standard_normal(n).astype(np.float32)).pin_memory()
+    y_h = torch.empty(n, dtype=torch.float32).pin_memory()
+    z = z_h.to(dev)
+    y = torch.empty_like(z)
+    for _ in range(args.warmup):
+        plan.spmv(z, out=y)
+        plan.matvec(z, out=y)
+    steps = max(args.steps, 300)     # a product lasts a few ms: enough of them for the clock samples
+    l0 = rbf.launch_count()
+    with ClockSampler(local) as clk:
+        ms_spmv = timed(lambda: plan.spmv(z, out=y), steps)
+        ms_mv = timed(lambda: plan.matvec(z, out=y), steps)
+    launches = rbf.launch_count() - l0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        zz = z_h.to(dev, non_blocking=True)
+        plan.spmv(zz, out=y)
+        y_h.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+    ms_e2e = 1e3 * (time.perf_counter() - t0) / steps
+    peak = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))["hbm_gbs"]
+    # algorithmic bytes of one CSR product: columns and values of every stored entry, row_ptr,
+    # z read once, y written once (binned order; the permutations add 2 x 12 n bytes)
+    alg = stored * 8 + (n + 1) * 8 + n * 8
+    achieved = alg / (ms_spmv * 1e-3) / 1e9
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle as orc
+        Cc, _ = orc.build_centers(cl.points, cl.normals, wl["delta"])
+        Cc = Cc.astype(np.float32).astype(np.float64)
+        rate, cnt, dt = oracle_rate(Cc, wl, min(args.cpu_rows, 20000))
+        cpu = {"value": rate, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+               "sample": f"{min(args.cpu_rows, 20000)} sampled rows of the {len(Cc):,}-centre truncated operator "
+                         f"({cnt:,} pairs, {dt:.1f} s), float64 row sums over a bucket list"}
+    if rank == 0:
+        out = {"metric": "RBF pair-evals/s through the assembled CSR matrix (Algorithm 2) per product",
+               "value": nnz / (ms_spmv * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+               "ms_per_step": ms_spmv, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32", "data": "synthetic",
+               "config": {"workload": wl["desc"], "sigma": wl["sigma"], "k": wl["k"], "centres": n,
+                          "l2": f"the CSR matrix ({csr_bytes / 1e9:.1f} GB) streams past L2 every product"},
+               "assembled": {"nnz": nnz, "stored": stored, "bytes": csr_bytes, "ms_assemble": ms_asm,
+                             "ms_spmv": ms_spmv, "pairs_per_s": nnz / (ms_spmv * 1e-3)},
+               "matrix_free": {"pairs": pairs, "ms_matvec": ms_mv, "pairs_per_s": pairs / (ms_mv * 1e-3),
+                               "speedup_over_assembled": ms_spmv / ms_mv},
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": None,
+                            "kernel": "k_spmv_csr (one warp per row, 16-byte streaming loads)",
+                            "peak_basis": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth), of measured",
+                            "algorithmic_bytes": alg},
+               "cpu_baseline": cpu,
+               "e2e": {"value": nnz / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
+                       "h2d_bytes_per_step": n * 4, "d2h_bytes_per_step": n * 4},
+               "gpu_launches": launches, "clocks": clk.summary()}
+        print(json.dumps(out))
+    return 0
+
+
 def run_density(args, wl):
     """Row f1: the density measures that choose sigma (rbf_density_measures) on the C2
     cloud: N nearest-neighbour queries plus M probe queries per step."""
@@ -679,6 +779,7 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=20000)
     ap.add_argument("--ref-rows", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--theta", type=float, default=0.0, help="assembled workload: sector angle (default 0.6)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.workload == "batch512":
@@ -689,6 +790,8 @@ def main():
         return run_isosurface(args, wl)
     if args.workload == "paper_tables":
         return run_paper_tables(args, wl)
+    if args.workload == "assembled" and args.impl != "reference":
+        return run_assembled(args, wl)
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_ours(args, wl)

@@ -191,6 +191,44 @@ rbf_status rbf_residual(rbf_plan *plan, const float *b, const double *x, double 
                         void *stream);
 
 /* ------------------------------------------------------------------------
+ * Assembled truncated matrix (Algorithm 2, Sec. III.B): the matrix of the
+ * plan built entry by entry and kept as CSR, for comparison with the
+ * matrix-free product.  The plan owns it until rbf_plan_release_csr or
+ * rbf_plan_destroy.
+ *
+ * Layout (device, binned order: row p and column c are binned positions; the
+ * caller index of position p is perm[p] from rbf_plan_export_binning):
+ *   row_ptr : n + 1 int64, row p is entries [row_ptr[p], row_ptr[p+1]);
+ *             every row_ptr[p] is a multiple of 4 (rows are padded)
+ *   col     : stored int32 column positions
+ *   val     : stored float32 values
+ * Entries: every pair with |c_i - c_j| < k sigma (decided as rbf_count_pairs
+ * decides, so nnz equals that count); for an untruncated plan (k = 0), every
+ * pair closer than 13 sigma (the others are below 2.2e-37).  Values
+ * exp(-|c_i - c_j|^2 / (2 sigma^2)) = 2^-t in float32, from the float32 squared
+ * distance (relative error of t below 7 x 2^-24) through ex2.approx: relative
+ * error below 2^-21 + 7 x 2^-24 ln(2) t; no 1/(sqrt(2 pi) sigma) prefactor.  Columns of a row are grouped by
+ * source block (ascending inside a block), not sorted.  Padding entries have
+ * the row's own position as column and value 0; a row holds each real column
+ * once.
+ *
+ * rbf_plan_assemble: builds the matrix, replacing a previous one.  nnz, stored
+ * (host, both required): entries within the cut-off and with the padding; set
+ * even when the call fails for size.  max_bytes > 0 caps the matrix's size
+ * (8 (stored + n + 1) bytes); RBF_ERR_OOM when that cap, or the device's free
+ * memory less 2 GiB, is exceeded (then nothing is kept).  Synchronises `stream`.
+ * Errors: RBF_ERR_INVALID (null pointers), RBF_ERR_OOM, RBF_ERR_CUDA. */
+rbf_status rbf_plan_assemble(rbf_plan *plan, int64_t max_bytes, int64_t *nnz, int64_t *stored, void *stream);
+/* Free the assembled matrix (no-op without one). */
+rbf_status rbf_plan_release_csr(rbf_plan *plan);
+/* Copy the assembled matrix out: row_ptr n + 1 int64, col `stored` int32, val
+ * `stored` float (device; any may be NULL).  RBF_ERR_INVALID without a matrix. */
+rbf_status rbf_plan_export_csr(rbf_plan *plan, int64_t *row_ptr, int32_t *col, float *val, void *stream);
+/* y = A~ z through the assembled matrix (float32, caller order; z and y n
+ * floats, distinct).  RBF_ERR_INVALID without a matrix. */
+rbf_status rbf_spmv(rbf_plan *plan, const float *z, float *y, void *stream);
+
+/* ------------------------------------------------------------------------
  * Restricted additive Schwarz preconditioner (Sec. III.A, RASM).
  * Subdomains are defined on the binned order: cores are consecutive runs of
  * `core` positions; subdomain i is the run of exactly min(block, n) positions
@@ -242,6 +280,9 @@ typedef struct {
     rbf_mlp *mlp;           /* RBF_PRECOND_MLP: the trained network */
     float mlp_lambda;       /* RBF_PRECOND_MLP: the shift the network was trained for */
     int mlp_initial_guess;  /* RBF_PRECOND_MLP: start from x0 = network(b) instead of 0 */
+    int assembled;          /* non-zero: the float32 products use the plan's assembled matrix
+                               (rbf_plan_assemble; RBF_ERR_INVALID without one); the float64
+                               true residuals stay matrix-free */
 } rbf_solve_params;
 
 typedef struct {

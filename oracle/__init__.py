@@ -170,6 +170,31 @@ def kernel_rows(C: np.ndarray, z: np.ndarray, sigma: float, k: float, rows=None)
     return y, int(cnt.value)
 
 
+def truncated_entries(C: np.ndarray, sigma: float, k: float, rows, radius_sigmas: float = 0.0):
+    """Nonzero entries of the chosen rows of the truncated matrix (Algorithm 2: for
+    each point, each point of its truncation area, A_ij = phi(|x_i - x_j|)).
+
+    Row r holds every j with |c_r - c_j| < k sigma (``k <= 0``: every j, or every j
+    closer than ``radius_sigmas`` sigma when that is > 0), value
+    exp(-|c_r - c_j|^2 / (2 sigma^2)).  Brute force over all centres, float64.
+    Returns a list of (columns ascending int64, values float64), one per row."""
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    s2 = float(sigma) * float(sigma)
+    if k > 0:
+        lim = (float(k) * float(sigma)) ** 2
+    elif radius_sigmas > 0:
+        lim = (float(radius_sigmas) * float(sigma)) ** 2
+    else:
+        lim = np.inf
+    out = []
+    for r in np.asarray(rows, dtype=np.int64):
+        d = C - C[r]
+        d2 = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]
+        cols = np.nonzero(d2 < lim)[0]
+        out.append((cols.astype(np.int64), np.exp(-d2[cols] / (2.0 * s2))))
+    return out
+
+
 def residual_rows(C, b, x, sigma, k, rows=None):
     """r_i = b_i - (A~ x)_i on ``rows`` (all rows by default)."""
     y, _ = kernel_rows(C, x, sigma, k, rows)

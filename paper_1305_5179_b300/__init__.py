@@ -33,7 +33,9 @@ RESIDUAL = {"df": 0, "f64": 1}
 EXPORTS = (
     "rbf_version", "rbf_launch_count", "rbf_probe_peaks", "rbf_status_string", "rbf_ctx_create", "rbf_ctx_destroy", "rbf_last_error",
     "rbf_build_centers", "rbf_plan_create", "rbf_plan_destroy", "rbf_plan_get_info", "rbf_plan_export_binning",
-    "rbf_matvec", "rbf_count_pairs", "rbf_residual", "rbf_schwarz_setup", "rbf_schwarz_apply",
+    "rbf_matvec", "rbf_count_pairs", "rbf_residual",
+    "rbf_plan_assemble", "rbf_plan_release_csr", "rbf_plan_export_csr", "rbf_spmv",
+    "rbf_schwarz_setup", "rbf_schwarz_apply",
     "rbf_plan_solve", "rbf_solve", "rbf_plan_eval_grid", "rbf_count_grid_pairs", "rbf_eval_grid",
     "rbf_density_measures", "rbf_isosurface",
     "rbf_matvec_dense_noalloc",
@@ -75,7 +77,8 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("max_it", ctypes.c_int), ("tol", ctypes.c_double), ("precond", ctypes.c_int),
                 ("schwarz", SchwarzParams), ("fixed_iterations", ctypes.c_int),
                 ("true_residual_each_restart", ctypes.c_int), ("residual_mode", ctypes.c_int),
-                ("mlp", ctypes.c_void_p), ("mlp_lambda", ctypes.c_float), ("mlp_initial_guess", ctypes.c_int)]
+                ("mlp", ctypes.c_void_p), ("mlp_lambda", ctypes.c_float), ("mlp_initial_guess", ctypes.c_int),
+                ("assembled", ctypes.c_int)]
 
 
 class TrainParams(ctypes.Structure):
@@ -169,6 +172,10 @@ def lib() -> ctypes.CDLL:
         "rbf_batch_solve": ([P, P, ctypes.POINTER(SolveParams), P, P, ctypes.POINTER(BatchStats), P], I),
         "rbf_batch_autotune": ([P, P, ctypes.POINTER(SolveParams), P, I, ctypes.POINTER(I), P, P], I),
         "rbf_eval_grid": ([P, P, P, I64, ctypes.POINTER(PlanParams), ctypes.POINTER(Grid), P, P], I),
+        "rbf_plan_assemble": ([P, I64, ctypes.POINTER(I64), ctypes.POINTER(I64), P], I),
+        "rbf_plan_release_csr": ([P], I),
+        "rbf_plan_export_csr": ([P, P, P, P, P], I),
+        "rbf_spmv": ([P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -320,7 +327,8 @@ def _grid(lo, hi, dims) -> Grid:
 
 def _solve_params(m=50, max_it=500, tol=1e-6, precond="none", core=96, block=128, shift=1e-4, restricted=True,
                   escalate=True, fixed_iterations=False, true_residual_each_restart=True,
-                  residual="df", mlp=None, mlp_lambda=1e-2, mlp_initial_guess=False) -> SolveParams:
+                  residual="df", mlp=None, mlp_lambda=1e-2, mlp_initial_guess=False,
+                  assembled=False) -> SolveParams:
     sp = SolveParams()
     sp.m, sp.max_it, sp.tol = int(m), int(max_it), float(tol)
     sp.precond = PRECOND[precond] if isinstance(precond, str) else int(precond)
@@ -331,6 +339,7 @@ def _solve_params(m=50, max_it=500, tol=1e-6, precond="none", core=96, block=128
     sp.mlp = mlp._h.value if mlp is not None else None
     sp.mlp_lambda = float(mlp_lambda)
     sp.mlp_initial_guess = int(bool(mlp_initial_guess))
+    sp.assembled = int(bool(assembled))
     return sp
 
 
@@ -391,6 +400,45 @@ class Plan:
         c = ctypes.c_int64(0)
         self.ctx.check(lib().rbf_count_pairs(self._h, ctypes.byref(c), _stream(stream)), "rbf_count_pairs")
         return int(c.value)
+
+    def assemble(self, max_bytes: int = 0, stream=None):
+        """Build the assembled matrix (Algorithm 2, CSR in binned order, kept by the plan).
+        Returns (nnz, stored); raises RbfError (RBF_ERR_OOM) when it would not fit, with
+        ``.nnz`` / ``.stored`` set on the exception."""
+        nnz, stored = ctypes.c_int64(0), ctypes.c_int64(0)
+        st = lib().rbf_plan_assemble(self._h, int(max_bytes), ctypes.byref(nnz), ctypes.byref(stored),
+                                     _stream(stream))
+        try:
+            self.ctx.check(st, "rbf_plan_assemble")
+        except RbfError as e:
+            e.nnz, e.stored = int(nnz.value), int(stored.value)
+            raise
+        self.csr_stored = int(stored.value)
+        return int(nnz.value), int(stored.value)
+
+    def release_csr(self):
+        self.ctx.check(lib().rbf_plan_release_csr(self._h), "rbf_plan_release_csr")
+
+    def export_csr(self, stream=None):
+        """(row_ptr int64 n+1, col int32, val float32) of the assembled matrix, binned order."""
+        import torch
+        stored = getattr(self, "csr_stored", None)
+        if stored is None:
+            raise RbfError(1, "the plan has no assembled matrix")
+        rp = torch.empty(self.n + 1, dtype=torch.int64, device=self.device)
+        col = torch.empty(stored, dtype=torch.int32, device=self.device)
+        val = torch.empty(stored, dtype=torch.float32, device=self.device)
+        self.ctx.check(lib().rbf_plan_export_csr(self._h, _ptr(rp), _ptr(col), _ptr(val), _stream(stream)),
+                       "rbf_plan_export_csr")
+        return rp, col, val
+
+    def spmv(self, z, out=None, stream=None):
+        """y = A~ z through the assembled matrix (caller order)."""
+        import torch
+        _req(z, torch.float32, "z", self.n)
+        y = torch.empty_like(z) if out is None else _req(out, torch.float32, "out", self.n)
+        self.ctx.check(lib().rbf_spmv(self._h, _ptr(z), _ptr(y), _stream(stream)), "rbf_spmv")
+        return y
 
     def residual(self, b, x, mode="df", stream=None):
         """True residual b - A~ x (float64); mode "df" (double-float) or "f64" (native)."""

@@ -261,6 +261,54 @@ rbf_status rbf_residual(rbf_plan *P, const float *b, const double *x, double *r,
     });
 }
 
+rbf_status rbf_plan_assemble(rbf_plan *P, int64_t max_bytes, int64_t *nnz, int64_t *stored, void *stream) {
+    if (!P) return RBF_ERR_INVALID;
+    return guarded(P->ctx, [&]() {
+        RBF_CHECK(nnz && stored, RBF_ERR_INVALID, "nnz and stored are required");
+        *nnz = 0;
+        *stored = 0;
+        assemble_csr(P, max_bytes, nnz, stored, S(stream));
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_plan_release_csr(rbf_plan *P) {
+    if (!P) return RBF_ERR_INVALID;
+    return guarded(P->ctx, [&]() {
+        P->csr.release();
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_plan_export_csr(rbf_plan *P, int64_t *row_ptr, int32_t *col, float *val, void *stream) {
+    if (!P) return RBF_ERR_INVALID;
+    return guarded(P->ctx, [&]() {
+        const CsrData &M = P->csr;
+        RBF_CHECK(M.ready, RBF_ERR_INVALID, "the plan has no assembled matrix");
+        cudaStream_t s = S(stream);
+        if (row_ptr)
+            RBF_CUDA(cudaMemcpyAsync(row_ptr, M.row_ptr.p, (P->n + 1) * 8, cudaMemcpyDeviceToDevice, s));
+        if (col) RBF_CUDA(cudaMemcpyAsync(col, M.col.p, M.stored * 4, cudaMemcpyDeviceToDevice, s));
+        if (val) RBF_CUDA(cudaMemcpyAsync(val, M.val.p, M.stored * 4, cudaMemcpyDeviceToDevice, s));
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_spmv(rbf_plan *P, const float *z, float *y, void *stream) {
+    if (!P) return RBF_ERR_INVALID;
+    return guarded(P->ctx, [&]() {
+        RBF_CHECK(z && y && z != y, RBF_ERR_INVALID, "z and y must be distinct device pointers");
+        RBF_CHECK(P->csr.ready, RBF_ERR_INVALID, "the plan has no assembled matrix (call rbf_plan_assemble first)");
+        cudaStream_t s = S(stream);
+        P->zs.ensure(P->n, s);
+        P->ys.ensure(P->n, s);
+        permute_to_binned_f32(P, z, P->zs.p, s);
+        spmv_binned(P, P->zs.p, P->ys.p, s);
+        permute_from_binned_f32(P, P->ys.p, y, s);
+        return RBF_OK;
+    });
+}
+
 rbf_status rbf_schwarz_setup(rbf_plan *P, const rbf_schwarz_params *p, int64_t *failed, void *stream) {
     if (!P) return RBF_ERR_INVALID;
     return guarded(P->ctx, [&]() {

@@ -668,6 +668,7 @@ rbf_status batch_solve(rbf_batch *Bt, const float *b, const rbf_solve_params &p,
     const int max_it = p.max_it > 0 ? p.max_it : 500;
     RBF_CHECK(m <= 64, RBF_ERR_UNSUPPORTED, "batched restart length %d > 64", m);
     RBF_CHECK(p.precond == RBF_PRECOND_NONE || p.precond == RBF_PRECOND_SCHWARZ, RBF_ERR_INVALID, "unknown preconditioner");
+    RBF_CHECK(!p.assembled, RBF_ERR_UNSUPPORTED, "the batched solve has no assembled operator");
     const bool pc = p.precond == RBF_PRECOND_SCHWARZ;
     cudaEvent_t e0, e1, e2;
     RBF_CUDA(cudaEventCreate(&e0));

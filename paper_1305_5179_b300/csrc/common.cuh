@@ -156,6 +156,7 @@ __host__ __device__ __forceinline__ uint32_t morton_host_dev(uint32_t x, uint32_
 // ------------------------------------------------------------------ primitives (scan.cu, sort.cu)
 // out[i] = sum_{t<i} in[t] for i in [0, n]; out has n+1 entries (out[n] = total).
 void scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
 // Stable LSD radix sort of (key, val) pairs on the low `bits` bits of key.
 // keys/vals are sorted in place (ping-pong buffers allocated internally).
 void radix_sort_pairs(uint32_t *keys, int32_t *vals, int64_t n, int bits, cudaStream_t s);

@@ -196,6 +196,13 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
     RBF_CHECK(m <= 512, RBF_ERR_INVALID, "restart length %d > 512", m);
     const bool each_restart = p.true_residual_each_restart != 0;
     const int G = std::max(1, std::min<int>(4 * P->ctx->num_sms, (int)ceil_div(n, kThreads)));
+    RBF_CHECK(!p.assembled || P->csr.ready, RBF_ERR_INVALID,
+              "assembled operator requested but the plan has no assembled matrix");
+    // the float32 operator: matrix-free product, or the assembled matrix (Algorithm 2)
+    auto op = [&](const float *in, float *out) {
+        if (p.assembled) spmv_binned(P, in, out, s);
+        else matvec_binned(P, in, out, s);
+    };
 
     rbf_report R{};
     Timer tm_setup, tm_solve;
@@ -269,7 +276,7 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
                 // float32 product for the restart vector; the float64 residual runs once at the end
                 k_to_f32<<<g1(n), kThreads, 0, s>>>(x.p, w32.p, n);
                 RBF_LAUNCHED();
-                matvec_binned(P, w32.p, Z.p, s);
+                op(w32.p, Z.p);
                 k_b_minus<<<g1(n), kThreads, 0, s>>>(bs.p, Z.p, r.p, n);
                 RBF_LAUNCHED();
             }
@@ -310,7 +317,7 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
                 RBF_LAUNCHED();
             }
             t_mv.begin(s);
-            matvec_binned(P, Zj, w32.p, s);
+            op(Zj, w32.p);
             t_mv.end(s);
             const int nv = j + 1;
             // pass 1

@@ -41,6 +41,23 @@ struct GridCache {
     PairList pl;
 };
 
+// Assembled truncated matrix (CSR in binned order, rows padded to multiples of 4 entries).
+struct CsrData {
+    bool ready = false;
+    int64_t nnz = 0;             // entries within the cut-off
+    int64_t stored = 0;          // with the padding (row_ptr[n])
+    PBuf<int64_t> row_ptr;       // n + 1
+    PBuf<int32_t> col;           // stored
+    PBuf<float> val;             // stored
+    void release() {
+        ready = false;
+        nnz = stored = 0;
+        row_ptr.release();
+        col.release();
+        val.release();
+    }
+};
+
 struct rbf_plan {
     rbf_ctx *ctx = nullptr;
     int64_t n = 0;
@@ -78,6 +95,7 @@ struct rbf_plan {
 
     SchwarzData sz;
     GridCache grid;
+    CsrData csr;
     // learned preconditioner work space
     PBuf<float> mlp_x, mlp_y, mlp_n;
     PBuf<int32_t> mlp_bad;
@@ -126,6 +144,12 @@ inline void residual_binned(rbf_plan *P, int mode, const float *bs, const double
 void schwarz_setup(rbf_plan *P, const rbf_schwarz_params &p, int64_t *failed_host, cudaStream_t s);
 // z = M^-1 v, binned order; v given as float64 (vd) or float32 (vf), exactly one non-null.
 void schwarz_apply_binned(rbf_plan *P, const double *vd, const float *vf, float *z, cudaStream_t s);
+
+// assemble.cu: the truncated matrix as CSR (Algorithm 2) and its product.  Sets *nnz and
+// *stored before any size check fails (RBF_ERR_OOM when the matrix exceeds max_bytes > 0
+// or the device's free memory less 2 GiB).
+void assemble_csr(rbf_plan *P, int64_t max_bytes, int64_t *nnz, int64_t *stored, cudaStream_t s);
+void spmv_binned(rbf_plan *P, const float *zs, float *ys, cudaStream_t s);
 
 // grid.cu
 void eval_grid(rbf_plan *P, const double *weights, const rbf_grid &g, float *f, cudaStream_t s);

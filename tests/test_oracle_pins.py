@@ -126,6 +126,53 @@ def test_kernel_rows_match_brute_force_loops():
 
 
 # --------------------------------------------------------------- Cholesky / solve
+def test_truncated_entries_on_a_lattice_count_ball_offsets():
+    """Algorithm 2 on the 7^3 unit lattice, sigma 0.5, k 3 (cut-off 1.5): a row keeps the
+    integer offsets (a, b, c) with a^2 + b^2 + c^2 < 2.25 that stay on the lattice,
+    value exp(-2 (a^2 + b^2 + c^2)); counted here by enumerating the offsets."""
+    m = 7
+    C = synth.lattice(m, 1.0)
+    idx = lambda x, y, z: x + m * (y + m * z)
+    for (x, y, z) in [(3, 3, 3), (0, 0, 0), (6, 3, 0), (1, 5, 6)]:
+        want = {}
+        for a in range(-2, 3):
+            for b in range(-2, 3):
+                for c in range(-2, 3):
+                    q = a * a + b * b + c * c
+                    if q < 2.25 and 0 <= x + a < m and 0 <= y + b < m and 0 <= z + c < m:
+                        want[idx(x + a, y + b, z + c)] = math.exp(-2.0 * q)
+        cols, vals = oracle.truncated_entries(C, 0.5, 3.0, [idx(x, y, z)])[0]
+        assert sorted(want) == list(cols)
+        np.testing.assert_allclose(vals, [want[j] for j in cols], rtol=1e-15)
+    # interior row: 1 + 6 + 12 offsets of squared length 0, 1, 2
+    assert len(oracle.truncated_entries(C, 0.5, 3.0, [idx(3, 3, 3)])[0][0]) == 19
+
+
+def test_truncated_entries_agree_with_the_c_product_and_are_symmetric():
+    """Rows of the numpy entry list against the C row product (an independent code):
+    sum_j A_rj z_j and the pair count; and A_rj = A_jr."""
+    cl = synth.torus(3000, noise=1e-3, seed=5)
+    C = oracle.build_centers(cl.points, cl.normals, 0.02)[0]
+    sigma, k = 0.05, 4.0
+    rng = np.random.default_rng(1)
+    z = rng.standard_normal(len(C))
+    rows = rng.choice(len(C), 40, replace=False)
+    ent = oracle.truncated_entries(C, sigma, k, rows)
+    y, pairs = oracle.kernel_rows(C, z, sigma, k, rows)
+    np.testing.assert_allclose([v @ z[c] for c, v in ent], y, rtol=1e-12, atol=1e-13)
+    assert sum(len(c) for c, _ in ent) == pairs
+    for r, (cols, vals) in zip(rows, ent):
+        for j, v in zip(cols[:5], vals[:5]):
+            cj, vj = oracle.truncated_entries(C, sigma, k, [j])[0]
+            assert v == vj[np.searchsorted(cj, r)] and r in cj
+    # k = 0 with a radius: the full dense rows less the entries beyond it
+    A = oracle.dense_matrix(C[:500], sigma)
+    e0 = oracle.truncated_entries(C[:500], sigma, 0.0, [7], radius_sigmas=13.0)[0]
+    d = np.linalg.norm(C[:500] - C[7], axis=1)
+    assert list(e0[0]) == list(np.nonzero(d < 13 * sigma)[0])
+    np.testing.assert_allclose(e0[1], A[7, e0[0]], rtol=1e-13)   # exponents up to 84.5: 84.5 x 2^-52 x a few
+
+
 def test_cholesky_reconstructs_and_matches_lapack():
     cl = synth.sphere(80, seed=2)
     C, _ = oracle.build_centers(cl.points, cl.normals, 0.05)
