@@ -195,6 +195,63 @@ def truncated_entries(C: np.ndarray, sigma: float, k: float, rows, radius_sigmas
     return out
 
 
+# --------------------------------------------------------------------------
+# Table I: the inverse multiquadric (1 + |x - x_j|^2)^(-beta), here with the
+# length scale sigma: phi(r) = (1 + r^2 / sigma^2)^(-beta) (Table I is sigma = 1).
+# Dense numpy, for the small systems this variant is used on.
+# --------------------------------------------------------------------------
+def imq_phi(r2, sigma: float, beta: float):
+    """(1 + r^2/sigma^2)^(-beta) for squared distances r2."""
+    return (1.0 + np.asarray(r2, dtype=np.float64) / (float(sigma) ** 2)) ** (-float(beta))
+
+
+def _imq_block(Ci: np.ndarray, Cj: np.ndarray, sigma: float, beta: float, k: float) -> np.ndarray:
+    d2 = ((Ci[:, None, :] - Cj[None, :, :]) ** 2).sum(-1)
+    A = imq_phi(d2, sigma, beta)
+    if k > 0:
+        A[~(d2 < (float(k) * float(sigma)) ** 2)] = 0.0
+    return A
+
+
+def imq_matrix(C: np.ndarray, sigma: float, beta: float, k: float = 0.0) -> np.ndarray:
+    """A_ij = phi(|c_i - c_j|), zero where |c_i - c_j| >= k sigma (k > 0)."""
+    C = np.ascontiguousarray(C, dtype=np.float64)[:, :3]
+    return _imq_block(C, C, sigma, beta, k)
+
+
+def imq_rows(C: np.ndarray, z: np.ndarray, sigma: float, beta: float, k: float = 0.0, rows=None) -> np.ndarray:
+    """y_r = sum_j A_rj z_j on the chosen rows (all by default), 256 rows at a time."""
+    C = np.ascontiguousarray(C, dtype=np.float64)[:, :3]
+    z = np.asarray(z, dtype=np.float64)
+    rows = np.arange(len(C)) if rows is None else np.asarray(rows, dtype=np.int64)
+    y = np.empty(len(rows))
+    for a in range(0, len(rows), 256):
+        y[a:a + 256] = _imq_block(C[rows[a:a + 256]], C, sigma, beta, k) @ z
+    return y
+
+
+def imq_eval_points(C: np.ndarray, w: np.ndarray, sigma: float, beta: float, k: float, P: np.ndarray) -> np.ndarray:
+    """P_f(p) = sum_j w_j phi(|p - c_j|) at the rows of P."""
+    C = np.ascontiguousarray(C, dtype=np.float64)[:, :3]
+    P = np.ascontiguousarray(P, dtype=np.float64)[:, :3]
+    w = np.asarray(w, dtype=np.float64)
+    f = np.empty(len(P))
+    for a in range(0, len(P), 256):
+        f[a:a + 256] = _imq_block(P[a:a + 256], C, sigma, beta, k) @ w
+    return f
+
+
+def imq_solve_dense(C: np.ndarray, b: np.ndarray, sigma: float, beta: float):
+    """Solve A c = b for the untruncated IMQ matrix by the oracle's Cholesky (A is
+    positive definite for every beta > 0: phi is completely monotone in r^2).
+    Returns (c, relative residual)."""
+    A = imq_matrix(C, sigma, beta)
+    L = cholesky(A)
+    x = chol_solve(L, np.asarray(b, dtype=np.float64))
+    r = np.asarray(b, dtype=np.float64) - A @ x
+    return x, float(np.linalg.norm(r) / np.linalg.norm(b))
+
+
 def residual_rows(C, b, x, sigma, k, rows=None):
     """r_i = b_i - (A~ x)_i on ``rows`` (all rows by default)."""
     y, _ = kernel_rows(C, x, sigma, k, rows)

@@ -247,6 +247,19 @@ def batch(nclouds: int = 512, nmin: int = 500, nmax: int = 20000, seed: int = 0,
     return clouds
 
 
+def fibonacci_sphere(n: int, radius: float = 1.0) -> Cloud:
+    """``n`` quasi-uniform points on the sphere: the golden-angle spiral, point i at
+    height z_i = 1 - (2 i + 1)/n and longitude i pi (3 - sqrt 5).  Normals are the
+    positions.  A scan-like cloud whose gaps are all about the spacing (unlike
+    random samples, whose largest gaps set the fill distance)."""
+    i = np.arange(n, dtype=np.float64) + 0.5
+    z = 1.0 - 2.0 * i / n
+    lon = math.pi * (3.0 - math.sqrt(5.0)) * i
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    u = np.stack([r * np.cos(lon), r * np.sin(lon), z], 1)
+    return Cloud(_f32(radius * u), _f32(u), {"kind": "fibonacci_sphere", "n": n, "radius": radius})
+
+
 def lattice(m: int, h: float, origin=(0.0, 0.0, 0.0)) -> np.ndarray:
     """The m^3 regular lattice of spacing ``h`` (float64, x fastest)."""
     i = np.arange(m, dtype=np.float64) * h

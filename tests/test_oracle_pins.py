@@ -173,6 +173,38 @@ def test_truncated_entries_agree_with_the_c_product_and_are_symmetric():
     np.testing.assert_allclose(e0[1], A[7, e0[0]], rtol=1e-13)   # exponents up to 84.5: 84.5 x 2^-52 x a few
 
 
+def test_imq_interpolant_matches_scipy():
+    """Table I's inverse multiquadric with beta = 1/2 is SciPy's 'inverse_multiquadric'
+    kernel 1/sqrt(1 + (eps r)^2) with eps = 1/sigma; with no polynomial part the two
+    interpolants of the same data agree (an independent library routine)."""
+    from scipy.interpolate import RBFInterpolator
+    cl = synth.sphere(150, seed=11)
+    C, b = oracle.build_centers(cl.points, cl.normals, 0.05)
+    sigma = 0.3
+    x, res = oracle.imq_solve_dense(C, b, sigma, 0.5)
+    assert res < 1e-10
+    P = np.random.default_rng(4).uniform(-1.2, 1.2, (500, 3))
+    ours = oracle.imq_eval_points(C, x, sigma, 0.5, 0.0, P)
+    ref = RBFInterpolator(C, b, kernel="inverse_multiquadric", epsilon=1.0 / sigma, degree=-1)(P)
+    assert np.abs(ours - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_imq_matrix_positive_definite_truncation_bound_and_rows():
+    cl = synth.sphere(200, seed=12)
+    C, _ = oracle.build_centers(cl.points, cl.normals, 0.05)
+    for beta in (0.5, 1.5, 2.5):
+        assert np.linalg.eigvalsh(oracle.imq_matrix(C, 0.2, beta)).min() > 0
+    A = oracle.imq_matrix(C, 0.1, 2.0)
+    At = oracle.imq_matrix(C, 0.1, 2.0, k=6.0)
+    assert np.abs(A - At).max() <= (1 + 36.0) ** -2.0
+    assert A[0, 0] == 1.0 and np.allclose(np.diag(A), 1.0)
+    d2 = ((C[3] - C[17]) ** 2).sum()
+    assert A[3, 17] == pytest.approx(1.0 / (1.0 + d2 / 0.01) ** 2, rel=1e-14)
+    z = np.random.default_rng(5).standard_normal(len(C))
+    np.testing.assert_allclose(oracle.imq_rows(C, z, 0.1, 2.0, 6.0, [3, 17, 500]), (At @ z)[[3, 17, 500]],
+                               rtol=1e-12)
+
+
 def test_cholesky_reconstructs_and_matches_lapack():
     cl = synth.sphere(80, seed=2)
     C, _ = oracle.build_centers(cl.points, cl.normals, 0.05)
@@ -537,6 +569,26 @@ def test_density_nearest_neighbours_match_a_kd_tree():
 
 
 # ---------------------------------------------------------------- Algorithm 1, step 4: the level set
+def test_density_hemisphere_fill_closed_form_and_subset_monotone():
+    """Data on the upper unit hemisphere: the distance from the south pole to (x, y, z)
+    on the sphere is sqrt(2 + 2 z), so with the pole among the probes the fill distance
+    over the whole sphere is sqrt(2 + 2 z_min) (the paper's sqrt 2 when points reach the
+    equator), and it cannot be below that; removing points never lowers a fill distance."""
+    Xf = synth.fibonacci_sphere(1120).points.astype(np.float64)
+    Xf /= np.linalg.norm(Xf, axis=1, keepdims=True)          # exactly on the sphere (up to float64)
+    Xu = Xf[Xf[:, 2] >= 0]
+    u = np.random.default_rng(2).standard_normal((20000, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    pole = np.array([[0.0, 0.0, -1.0]])
+    zmin = Xu[:, 2].min()
+    assert oracle.fill_distance(Xu, pole) == pytest.approx(math.sqrt(2 + 2 * zmin), rel=1e-14)
+    assert oracle.fill_distance(Xu, np.vstack([u, pole])) == pytest.approx(math.sqrt(2 + 2 * zmin), rel=1e-14)
+    eq = np.array([[math.cos(a), math.sin(a), 0.0] for a in (0.3, 2.4, 4.5)])
+    assert oracle.fill_distance(np.vstack([Xu, eq]), pole) == pytest.approx(math.sqrt(2.0), rel=1e-15)
+    sub = Xf[np.random.default_rng(3).choice(len(Xf), len(Xf) // 2, replace=False)]
+    assert oracle.fill_distance(sub, u) >= oracle.fill_distance(Xf, u)
+
+
 def _poly_area_clip(square, keep):
     """Area of a convex polygon clipped by half-planes keep(p) >= 0 (linear in p),
     Sutherland-Hodgman, for the reference area of a plane section."""
