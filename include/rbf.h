@@ -74,7 +74,9 @@ int64_t rbf_launch_count(void);
 const char *rbf_status_string(rbf_status s);
 
 /* Create a context on CUDA device `device` (made current for every call on the
- * context).  *ctx receives a host-owned handle; destroy it with rbf_ctx_destroy. */
+ * context).  *ctx receives a host-owned handle; destroy it with rbf_ctx_destroy,
+ * after the plans, batches and networks made on it (their destroy functions do
+ * not touch the context; every other call on them does). */
 rbf_status rbf_ctx_create(rbf_ctx **ctx, int device);
 rbf_status rbf_ctx_destroy(rbf_ctx *ctx);
 
@@ -107,7 +109,8 @@ rbf_status rbf_build_centers(rbf_ctx *ctx, const float *pts, const float *nrm, i
  * Binning is a definition shared with the tests:
  *   lo = componentwise minimum of the centres, ext = hi - lo (float32);
  *   cell edge hc = k sigma / cells_per_cutoff (k > 0), or
- *   max(min(max(ext)/8, 3 sigma), max(ext)/128) in double (k = 0; 1 if ext is 0); fine cells hf = hc / 2^levels; inv = (float)(2^levels / hc)
+ *   max(min(max(ext)/8, 3 sigma), max(ext)/128) in double (k = 0, Gaussian), max(ext)/8
+ *   (k = 0, inverse multiquadric); 1 if ext is 0; fine cells hf = hc / 2^levels; inv = (float)(2^levels / hc)
  *   computed in double; q_d = floor((c_d - lo_d) * inv) in float32;
  *   key = Morton interleave (x in bit 0) of q; cell = key >> (3 levels);
  *   centres are ordered by a stable sort on key.  At most 1024 fine cells per
@@ -120,7 +123,21 @@ typedef struct {
     int levels;             /* fine levels per cell (0..7); -1 selects 3 */
     int product;            /* kernel of the float32 product and grid evaluation: RBF_PRODUCT_TC (0) or
                                RBF_PRODUCT_SIMT (1); both compute the same sum (see rbf_matvec) */
+    int kernel;             /* radial function: RBF_KERNEL_GAUSSIAN (0, the paper's choice) or
+                               RBF_KERNEL_IMQ (1), see below */
+    float beta;             /* RBF_KERNEL_IMQ: exponent, 0 < beta <= 16 */
 } rbf_plan_params;
+
+/* Radial functions (Table I).  The Gaussian exp(-r^2 / (2 sigma^2)) is the
+ * method's; the inverse multiquadric (1 + r^2 / sigma^2)^(-beta) is Table I's
+ * (1 + r^2)^(-beta) with the length scale sigma (positive definite for every
+ * beta > 0).  IMQ plans: the products and the grid evaluation run a direct
+ * float32 kernel (one thread per target; the `product` choice does not apply),
+ * true residuals are native float64 whatever the residual mode, k > 0 truncates
+ * at k sigma with entry error (1 + k^2)^(-beta) (large: IMQ decays
+ * algebraically), k = 0 keeps every pair; the learned preconditioner and the
+ * batched solve take Gaussian plans only (RBF_ERR_UNSUPPORTED). */
+enum { RBF_KERNEL_GAUSSIAN = 0, RBF_KERNEL_IMQ = 1 };
 
 enum {
     RBF_PRODUCT_TC = 0,     /* exponents -|u - v|^2 of a 128 x 32 tile by tcgen05.mma (tf32 head + tail

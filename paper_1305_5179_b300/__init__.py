@@ -55,7 +55,16 @@ class RbfError(RuntimeError):
 
 class PlanParams(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_float), ("k", ctypes.c_float), ("cells_per_cutoff", ctypes.c_int),
-                ("levels", ctypes.c_int), ("product", ctypes.c_int)]
+                ("levels", ctypes.c_int), ("product", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("beta", ctypes.c_float)]
+
+
+KERNELS = {"gaussian": 0, "imq": 1}
+
+
+def _plan_params(sigma, k, cells_per_cutoff=1, levels=3, product="tc", kernel="gaussian", beta=0.0):
+    return PlanParams(float(sigma), float(k), int(cells_per_cutoff), int(levels), PRODUCTS[product],
+                      KERNELS[kernel], float(beta))
 
 
 PRODUCTS = {"tc": 0, "simt": 1}
@@ -212,7 +221,9 @@ class Context:
     """A library context bound to one CUDA device."""
 
     def __init__(self, device: int = 0):
+        import weakref
         self._h = ctypes.c_void_p()
+        self._dependents = weakref.WeakSet()    # plans, batches, networks: closed before the context
         st = lib().rbf_ctx_create(ctypes.byref(self._h), int(device))
         if st != RBF_OK:
             raise RbfError(st, f"rbf_ctx_create(device={device}) failed")
@@ -226,6 +237,8 @@ class Context:
 
     def close(self):
         if self._h:
+            for d in list(getattr(self, "_dependents", ())):
+                d.close()
             lib().rbf_ctx_destroy(self._h)
             self._h = ctypes.c_void_p()
 
@@ -347,7 +360,8 @@ class Plan:
     """The matrix-free truncated Gaussian operator over a fixed set of centres."""
 
     def __init__(self, ctx: Context, centers, sigma: float, k: float = 0.0, cells_per_cutoff: int = 1,
-                 levels: int = 3, product: str = "tc", stream=None):
+                 levels: int = 3, product: str = "tc", kernel: str = "gaussian", beta: float = 0.0, stream=None):
+        """kernel "gaussian" (exp(-r^2/(2 sigma^2))) or "imq" ((1 + r^2/sigma^2)^-beta, Table I)."""
         import torch
         _req(centers, torch.float32, "centers")
         if centers.dim() != 2 or centers.shape[1] != 4:
@@ -355,10 +369,11 @@ class Plan:
         self.ctx = ctx
         self.n = int(centers.shape[0])
         self.device = centers.device
-        self.params = PlanParams(float(sigma), float(k), int(cells_per_cutoff), int(levels), PRODUCTS[product])
+        self.params = _plan_params(sigma, k, cells_per_cutoff, levels, product, kernel, beta)
         self._h = ctypes.c_void_p()
         ctx.check(lib().rbf_plan_create(ctx._h, _ptr(centers), self.n, ctypes.byref(self.params),
                                         ctypes.byref(self._h), _stream(stream)), "rbf_plan_create")
+        ctx._dependents.add(self)
 
     def close(self):
         if self._h:
@@ -498,13 +513,14 @@ class Plan:
         return f
 
 
-def solve(ctx: Context, centers, targets, sigma: float, k: float = 0.0, product: str = "tc", stream=None, **kw):
+def solve(ctx: Context, centers, targets, sigma: float, k: float = 0.0, product: str = "tc", kernel: str = "gaussian",
+          beta: float = 0.0, stream=None, **kw):
     """One-shot step 2 (plan + FGMRES + free)."""
     import torch
     _req(centers, torch.float32, "centers")
     n = centers.shape[0]
     _req(targets, torch.float32, "targets", n)
-    pp = PlanParams(float(sigma), float(k), 1, 3, PRODUCTS[product])
+    pp = _plan_params(sigma, k, product=product, kernel=kernel, beta=beta)
     x = torch.empty(n, dtype=torch.float64, device=centers.device)
     rep = Report()
     sp = _solve_params(**kw)
@@ -517,13 +533,13 @@ def solve(ctx: Context, centers, targets, sigma: float, k: float = 0.0, product:
 
 
 def eval_grid(ctx: Context, centers, weights, sigma: float, k: float, lo, hi, dims, product: str = "tc",
-              stream=None):
+              kernel: str = "gaussian", beta: float = 0.0, stream=None):
     """One-shot step 3."""
     import torch
     _req(centers, torch.float32, "centers")
     n = centers.shape[0]
     _req(weights, torch.float64, "weights", n)
-    pp = PlanParams(float(sigma), float(k), 1, 3, PRODUCTS[product])
+    pp = _plan_params(sigma, k, product=product, kernel=kernel, beta=beta)
     f = torch.empty((int(dims[2]), int(dims[1]), int(dims[0])), dtype=torch.float32, device=centers.device)
     g = _grid(lo, hi, dims)
     ctx.check(lib().rbf_eval_grid(ctx._h, _ptr(centers), _ptr(weights), n, ctypes.byref(pp), ctypes.byref(g), _ptr(f),
@@ -559,6 +575,7 @@ class Batch:
         self._h = ctypes.c_void_p()
         ctx.check(lib().rbf_batch_create(ctx._h, arr, len(self.plans), ctypes.byref(self._h), _stream(stream)),
                   "rbf_batch_create")
+        ctx._dependents.add(self)
         self.n = int(lib().rbf_batch_size(self._h))
         self.device = self.plans[0].device
 
@@ -616,6 +633,7 @@ class MLP:
         self._h = ctypes.c_void_p()
         ctx.check(lib().rbf_mlp_create(ctx._h, p.ctypes.data_as(ctypes.c_void_p), ctypes.byref(self._h)),
                   "rbf_mlp_create")
+        ctx._dependents.add(self)
 
     def close(self):
         if self._h:

@@ -19,6 +19,7 @@ rbf_status guarded(rbf_ctx *ctx, F &&f) {
     if (!ctx) return RBF_ERR_INVALID;
     try {
         ctx->last_error.clear();
+        (void)cudaGetLastError();   // a stale (non-sticky) error of earlier, unrelated work is not this call's
         cudaError_t e = cudaSetDevice(ctx->device);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
@@ -50,6 +51,10 @@ void check_plan_params(const rbf_plan_params *p) {
     RBF_CHECK(p->levels >= -1 && p->levels <= 7, RBF_ERR_INVALID, "levels in -1..7");
     RBF_CHECK(p->product == RBF_PRODUCT_TC || p->product == RBF_PRODUCT_SIMT, RBF_ERR_INVALID,
               "product must be RBF_PRODUCT_TC or RBF_PRODUCT_SIMT");
+    RBF_CHECK(p->kernel == RBF_KERNEL_GAUSSIAN || p->kernel == RBF_KERNEL_IMQ, RBF_ERR_INVALID,
+              "kernel must be RBF_KERNEL_GAUSSIAN or RBF_KERNEL_IMQ");
+    RBF_CHECK(p->kernel != RBF_KERNEL_IMQ || (std::isfinite(p->beta) && p->beta > 0.f && p->beta <= 16.f),
+              RBF_ERR_INVALID, "inverse multiquadric beta must be in (0, 16]");
 }
 
 }  // namespace
@@ -72,12 +77,15 @@ rbf_plan *make_plan(rbf_ctx *ctx, const float *centers, int64_t n, const rbf_pla
     rbf_plan *P = new rbf_plan();
     try {
         P->ctx = ctx;
+        P->device = ctx->device;
         P->n = n;
         P->sigma = p->sigma;
         P->k = p->k;
         P->cells_per_cutoff = p->cells_per_cutoff > 0 ? p->cells_per_cutoff : 1;
         P->levels = p->levels >= 0 ? p->levels : 3;
         P->product = p->product;
+        P->kernel = p->kernel;
+        P->beta = p->kernel == RBF_KERNEL_IMQ ? p->beta : 0.f;
         plan_build(P, (const float4 *)centers, s);
     } catch (...) {
         delete P;
@@ -167,8 +175,12 @@ rbf_status rbf_plan_create(rbf_ctx *ctx, const float *centers, int64_t n, const 
 
 rbf_status rbf_plan_destroy(rbf_plan *plan) {
     if (!plan) return RBF_OK;
-    cudaSetDevice(plan->ctx->device);
+    int cur = 0;
+    const bool have = cudaGetDevice(&cur) == cudaSuccess;
+    cudaSetDevice(plan->device);     // its buffers belong to this device
     delete plan;
+    if (have) cudaSetDevice(cur);
+    (void)cudaGetLastError();        // leave no error behind for the caller's next check
     return RBF_OK;
 }
 
@@ -457,6 +469,8 @@ rbf_status rbf_mlp_make_data(rbf_plan *plan, float lambda, const int32_t *block_
     if (!plan) return RBF_ERR_INVALID;
     return guarded(plan->ctx, [&]() {
         RBF_CHECK(block_ids && R && X && Y && ns >= 0, RBF_ERR_INVALID, "null pointer argument");
+        RBF_CHECK(plan->kernel == RBF_KERNEL_GAUSSIAN, RBF_ERR_UNSUPPORTED,
+                  "the learned preconditioner is trained on Gaussian blocks");
         int64_t f = mlp_make_data(plan, lambda, block_ids, R, ns, X, Y, S(stream));
         if (failed) *failed = f;
         return RBF_OK;

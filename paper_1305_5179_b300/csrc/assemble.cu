@@ -18,10 +18,12 @@
 //
 // Stored entries: pairs with |x_i - x_j| < k sigma, decided in float32 and
 // repeated in float64 within 1e-5 (relative) of the cut-off, the decision of the
-// pair count; for an untruncated plan, pairs closer than 13 sigma (every other
-// entry is below exp(-84.5) < 2.2e-37).  Values exp(-|x_i - x_j|^2 / (2 sigma^2))
-// from the float32 squared distance through ex2.approx; columns of a row appear in
-// the order of the tile's source blocks, ascending within a block.
+// pair count; for an untruncated Gaussian plan, pairs closer than 13 sigma (every
+// other entry is below exp(-84.5) < 2.2e-37), for an untruncated inverse
+// multiquadric plan every pair.  Values exp(-|x_i - x_j|^2 / (2 sigma^2)), or
+// (1 + |x_i - x_j|^2 / sigma^2)^-beta, from the float32 squared distance through
+// ex2.approx (and lg2.approx); columns of a row appear in the order of the tile's
+// source blocks, ascending within a block.
 //
 // The product (one warp per row, 16-byte streaming loads of columns and values,
 // z gathered through L1) moves 8 bytes per stored entry from HBM; the matrix-free
@@ -39,8 +41,13 @@ constexpr int kSpmvWarps = 8;
 struct Cut {
     double rc2;        // float64 squared cut-off
     float lo, hi;      // float32 band around it where the test is repeated in float64
-    float c;           // log2(e) / (2 sigma^2)
+    float c;           // Gaussian: log2(e) / (2 sigma^2); inverse multiquadric: 1 / sigma^2
+    float beta;        // inverse multiquadric exponent (0: Gaussian)
 };
+
+__device__ __forceinline__ float entry(const Cut &k, float r2) {
+    return k.beta > 0.f ? ex2_approx(-k.beta * __log2f(fmaf(r2, k.c, 1.f))) : ex2_approx(-(r2 * k.c));
+}
 
 __device__ __forceinline__ bool within(const Cut &k, float px, float py, float pz, float qx, float qy, float qz,
                                        float &r2) {
@@ -153,7 +160,7 @@ __global__ void __launch_bounds__(kT) k_asm_fill(const float4 *__restrict__ pos,
                 const int64_t at = base + __popc(m & lt);
                 if (at < lim) {
                     __stcs(col + at, bi.x + lane);
-                    __stcs(val + at, ex2_approx(-(r2 * cut.c)));
+                    __stcs(val + at, entry(cut, r2));
                 }
             }
             if (lane == r) next += __popc(m);
@@ -214,11 +221,13 @@ __global__ void __launch_bounds__(kSpmvWarps * 32) k_spmv_csr(const int64_t *__r
 Cut make_cut(const rbf_plan *P) {
     Cut k;
     const double s = (double)P->sigma;
-    k.rc2 = P->rc2_64 > 0.0 ? P->rc2_64 : (13.0 * s) * (13.0 * s);
+    const bool imq = P->kernel == RBF_KERNEL_IMQ;
+    k.rc2 = P->rc2_64 > 0.0 ? P->rc2_64 : imq ? (double)INFINITY : (13.0 * s) * (13.0 * s);
     const float f = (float)k.rc2;
     k.lo = f * (1.f - 1e-5f);
     k.hi = f * (1.f + 1e-5f);
-    k.c = (float)(1.4426950408889634 / (2.0 * s * s));
+    k.c = imq ? (float)(1.0 / (s * s)) : (float)(1.4426950408889634 / (2.0 * s * s));
+    k.beta = imq ? P->beta : 0.f;
     return k;
 }
 

@@ -423,6 +423,8 @@ rbf_batch *batch_create(rbf_ctx *ctx, rbf_plan *const *plans, int nplans, cudaSt
         int64_t total_len = 0, total_tiles = 0;
         for (int b = 0; b < nplans; ++b) {
             RBF_CHECK(plans[b] && plans[b]->ctx == ctx, RBF_ERR_INVALID, "plan %d is null or from another context", b);
+            RBF_CHECK(plans[b]->kernel == RBF_KERNEL_GAUSSIAN, RBF_ERR_UNSUPPORTED,
+                      "plan %d: the batched solve takes Gaussian plans only", b);
             Bt->off[b + 1] = Bt->off[b] + plans[b]->n;
             total_len += plans[b]->pl.len;
             total_tiles += plans[b]->pl.ntiles;

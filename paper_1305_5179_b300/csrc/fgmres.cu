@@ -212,6 +212,8 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
         schwarz_setup(P, p.schwarz, &failed, s);
         R.precond_failed_blocks = (int)failed;
     } else if (p.precond == RBF_PRECOND_MLP) {
+        RBF_CHECK(P->kernel == RBF_KERNEL_GAUSSIAN, RBF_ERR_UNSUPPORTED,
+                  "the learned preconditioner is trained on Gaussian blocks");
         RBF_CHECK(p.mlp && p.mlp_lambda > 0.f, RBF_ERR_INVALID, "MLP preconditioner needs a network and lambda > 0");
         rbf_schwarz_params fb{};
         fb.core = 64;

@@ -22,6 +22,12 @@
 //
 // float64 kernel (true residual): one thread per target, all arithmetic in
 // double precision, cut-off decided as |x_i - x_j|^2 < (k sigma)^2 in double.
+//
+// Inverse multiquadric plans (Table I, phi = (1 + r^2 / sigma^2)^(-beta)) have no
+// such factorisation: their float32 product is direct, one thread per target,
+// phi = 2^(-beta log2(1 + r^2 / sigma^2)) (two MUFU operations per pair), blocks
+// staged in shared memory; entries flagged for the cut-off test keep
+// r^2 < (k sigma)^2 (float32).
 #include <cmath>
 
 #include "plan.cuh"
@@ -55,6 +61,40 @@ __global__ void k_reduce_segments(MvArgs a, const int32_t *__restrict__ tile_seg
     }
 }
 
+// Inverse multiquadric product (direct).  One CTA of kChunk threads per segment.
+template <bool kGrid>
+__global__ void __launch_bounds__(kChunk) k_matvec_imq(MvArgs a) {
+    __shared__ float4 s_p[kBlk];
+    const int4 sg = a.seg[blockIdx.x];
+    float px, py, pz;
+    int64_t oi;
+    const bool valid = target_xyz<kGrid>(a, sg.x, threadIdx.x, px, py, pz, oi);
+    float acc = 0.f;
+    for (int e = sg.y; e < sg.z; ++e) {
+        const int v = a.ent[e];
+        const int2 bi = a.blk[v & 0x7fffffff];
+        __syncthreads();
+        if ((int)threadIdx.x < bi.y) {
+            const float4 q = a.pos[bi.x + threadIdx.x];
+            s_p[threadIdx.x] = make_float4(q.x, q.y, q.z, a.w[bi.x + threadIdx.x]);
+        }
+        __syncthreads();
+        const float lim = v < 0 ? a.rc2f : INFINITY;
+        for (int j = 0; j < bi.y; ++j) {
+            const float4 q = s_p[j];
+            const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float phi = ex2_approx(-a.imq_beta * __log2f(fmaf(r2, a.imq_ic, 1.f)));
+            acc = fmaf(r2 < lim ? q.w : 0.f, phi, acc);
+        }
+    }
+    if (sg.w) {
+        if (valid) a.out[oi] = acc;
+    } else {
+        a.partial[(int64_t)blockIdx.x * kChunk + threadIdx.x] = acc;
+    }
+}
+
 // ---------------------------------------------------------------- float64
 constexpr int kT64 = kChunk;   // one thread per target
 
@@ -62,6 +102,7 @@ __global__ void __launch_bounds__(kT64) k_resid_f64(const float4 *__restrict__ p
                                                    const double *__restrict__ x,
                                                    const int2 *__restrict__ blk, const int32_t *__restrict__ ent,
                                                    const int4 *__restrict__ seg, int64_t n, double rc2, double inv2s2,
+                                                   int imq, double imq_ic, double imq_beta,
                                                    const float *__restrict__ b, double *__restrict__ out,
                                                    double *__restrict__ part, unsigned long long *__restrict__ cnt) {
     __shared__ double s_x[kBlk], s_y[kBlk], s_z[kBlk], s_w[kBlk];
@@ -93,7 +134,7 @@ __global__ void __launch_bounds__(kT64) k_resid_f64(const float4 *__restrict__ p
             double dx = px - s_x[j], dy = py - s_y[j], dz = pz - s_z[j];
             double r2 = dx * dx + dy * dy + dz * dz;
             if (rc2 <= 0.0 || r2 < rc2) {
-                acc += s_w[j] * exp(-r2 * inv2s2);
+                acc += s_w[j] * (imq ? pow(1.0 + r2 * imq_ic, -imq_beta) : exp(-r2 * inv2s2));
                 ++c;
             }
         }
@@ -145,6 +186,9 @@ MvArgs base_args(const rbf_plan *P, const PairList &pl, const float *w, float *o
     a.n = P->n;
     a.scl = P->scl;
     a.R = P->R;
+    a.imq_ic = (float)(1.0 / ((double)P->sigma * (double)P->sigma));
+    a.imq_beta = P->beta;
+    a.rc2f = P->rc2_64 > 0.0 ? (float)P->rc2_64 : INFINITY;
     a.out = out;
     a.partial = partial;
     return a;
@@ -157,7 +201,12 @@ void matvec_binned(rbf_plan *P, const float *zs, float *ys, cudaStream_t s) {
     if (pl.any_split) P->partial.ensure((size_t)pl.nseg * kChunk, s);
     MvArgs a = base_args(P, pl, zs, ys, P->partial.p);
     ctx_check_device_error(P->ctx);
-    if (P->product == RBF_PRODUCT_TC) {
+    if (P->kernel == RBF_KERNEL_IMQ) {
+        if (pl.nseg > 0) {
+            k_matvec_imq<false><<<(unsigned)pl.nseg, kChunk, 0, s>>>(a);
+            RBF_LAUNCHED();
+        }
+    } else if (P->product == RBF_PRODUCT_TC) {
         product_tc_launch(P, pl, a, false, s);
     } else if (pl.nseg > 0) {
         k_matvec_f32<false><<<(unsigned)pl.nseg, kWarps * 32, 0, s>>>(a);
@@ -175,8 +224,10 @@ void residual_binned_f64(rbf_plan *P, const float *bs, const double *xs, double 
     DevBuf<double> part;
     if (pl.any_split) part.alloc((size_t)pl.nseg * kChunk, s);
     if (pl.nseg > 0) {
+        const int imq = P->kernel == RBF_KERNEL_IMQ;
         k_resid_f64<<<(unsigned)pl.nseg, kT64, 0, s>>>(P->pos.p, P->tiles.p, xs, P->blk.p, pl.ent.p, pl.seg.p, P->n,
-                                                       P->rc2_64, P->inv2s2_64, bs, rs, part.p, cnt);
+                                                       P->rc2_64, P->inv2s2_64, imq, 2.0 * P->inv2s2_64,
+                                                       (double)P->beta, bs, rs, part.p, cnt);
         RBF_LAUNCHED();
     }
     if (pl.any_split) {
@@ -197,7 +248,12 @@ void matvec_grid_launch(rbf_plan *P, const PairList &pl, const float *ws, const 
         a.bdim[d] = (int)bricks[d];
     }
     ctx_check_device_error(P->ctx);
-    if (P->product == RBF_PRODUCT_TC) {
+    if (P->kernel == RBF_KERNEL_IMQ) {
+        if (pl.nseg > 0) {
+            k_matvec_imq<true><<<(unsigned)pl.nseg, kChunk, 0, s>>>(a);
+            RBF_LAUNCHED();
+        }
+    } else if (P->product == RBF_PRODUCT_TC) {
         product_tc_launch(P, pl, a, true, s);
     } else if (pl.nseg > 0) {
         k_matvec_f32<true><<<(unsigned)pl.nseg, kWarps * 32, 0, s>>>(a);

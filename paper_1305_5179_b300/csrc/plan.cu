@@ -612,6 +612,10 @@ void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s, bool binning
     double hc;
     if (P->k > 0.f) {
         hc = (double)P->k * (double)P->sigma / (double)P->cells_per_cutoff;
+    } else if (P->kernel == RBF_KERNEL_IMQ) {
+        // untruncated inverse multiquadric: every pair is evaluated, 8 cells per axis suffice
+        double m = std::max({(double)ext[0], (double)ext[1], (double)ext[2]});
+        hc = m > 0 ? m / 8.0 : 1.0;
     } else {
         // untruncated: cells of at most 3 sigma keep blocks compact in scaled units, at least
         // max(ext)/128 keeps the fine grid within 1024 cells per axis
@@ -637,6 +641,13 @@ void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s, bool binning
         P->rc = P->k * P->sigma;
         P->rc2_64 = ((double)P->k * (double)P->sigma) * ((double)P->k * (double)P->sigma);
         P->R = (float)((double)P->k * (double)P->k * 1.4426950408889634 / 2.0);
+    } else if (P->kernel == RBF_KERNEL_IMQ) {
+        // untruncated inverse multiquadric: an infinite culling radius keeps every block for
+        // every target, grid nodes outside the centres' box included (the cell ranges clamp
+        // before converting to integers)
+        P->rc = INFINITY;
+        P->rc2_64 = 0.0;
+        P->R = INFINITY;
     } else {
         // untruncated: blocks further than 14 sigma contribute < 3e-43 per unit weight, below
         // float32's normal range, and are skipped

@@ -60,10 +60,13 @@ struct CsrData {
 
 struct rbf_plan {
     rbf_ctx *ctx = nullptr;
+    int device = 0;               // the context's device (release does not read the context)
     int64_t n = 0;
     float sigma = 0.f, k = 0.f;
     int cells_per_cutoff = 1, levels = 3, nbits = 0;
     int product = RBF_PRODUCT_TC;   // kernel of the float32 product and grid evaluation
+    int kernel = RBF_KERNEL_GAUSSIAN;
+    float beta = 0.f;               // inverse multiquadric exponent
     float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     float inv = 0.f;          // fine cells per unit length
     int cdim = 0;             // cells per axis in the cell table (2^(nbits - levels))
@@ -133,8 +136,9 @@ void residual_binned_f64(rbf_plan *P, const float *bs, const double *xs, double 
 // residual_df.cu: the same residual in double-float arithmetic on the float32 pipes.
 void residual_binned_df(rbf_plan *P, const float *bs, const double *xs, double *rs, cudaStream_t s);
 // dispatch on rbf_residual_mode
+// (inverse multiquadric plans always take the float64 kernel)
 inline void residual_binned(rbf_plan *P, int mode, const float *bs, const double *xs, double *rs, cudaStream_t s) {
-    if (mode == RBF_RESIDUAL_F64)
+    if (mode == RBF_RESIDUAL_F64 || P->kernel == RBF_KERNEL_IMQ)
         residual_binned_f64(P, bs, xs, rs, nullptr, s);
     else
         residual_binned_df(P, bs, xs, rs, s);

@@ -53,6 +53,8 @@ struct MvArgs {
     float glo[3], gstep[3];
     int gdim[3];
     int bdim[3];
+    // inverse multiquadric plans (direct kernel): 1 / sigma^2, beta, squared cut-off (k sigma)^2
+    float imq_ic, imq_beta, rc2f;
 };
 
 // Target slot q (0..kChunk-1) of tile t: coordinates and validity.

@@ -32,7 +32,8 @@ __device__ __forceinline__ void dom_of(int64_t blkid, int core, int B, int64_t n
 }
 
 __global__ void __launch_bounds__(kSetupThreads) k_schwarz_setup(const float4 *__restrict__ pos, int64_t n, int core,
-                                                                 int B, float scl, float shift, int escalate,
+                                                                 int B, float scl, float imq_beta, float shift,
+                                                                 int escalate,
                                                                  float *__restrict__ Lout, float *__restrict__ shift_used,
                                                                  int32_t *__restrict__ failed) {
     extern __shared__ float sm[];
@@ -51,7 +52,10 @@ __global__ void __launch_bounds__(kSetupThreads) k_schwarz_setup(const float4 *_
             if (j > i) continue;
             float4 pi = pos[d0 + i], pj = pos[d0 + j];   // difference before scaling keeps it exact-ish
             float dx = (pi.x - pj.x) * scl, dy = (pi.y - pj.y) * scl, dz = (pi.z - pj.z) * scl;
-            float v = ex2_approx(-(dx * dx + dy * dy + dz * dz));
+            const float t = dx * dx + dy * dy + dz * dz;   // |d|^2 log2(e) / (2 sigma^2)
+            // Gaussian 2^-t; inverse multiquadric (1 + |d|^2 / sigma^2)^-beta, |d|^2 / sigma^2 = 2 ln(2) t
+            float v = imq_beta > 0.f ? ex2_approx(-imq_beta * __log2f(fmaf(t, 1.3862943611198906f, 1.f)))
+                                     : ex2_approx(-t);
             A[i * ld + j] = (i == j) ? 1.f + lam : v;
         }
         if (threadIdx.x == 0) s_fail = 0;
@@ -178,8 +182,10 @@ void schwarz_setup(rbf_plan *P, const rbf_schwarz_params &p, int64_t *failed_hos
     S.failed.alloc(S.nblocks, s);
     size_t smem = (size_t)B * (B + 1) * sizeof(float);
     RBF_CUDA(cudaFuncSetAttribute(k_schwarz_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_schwarz_setup<<<(unsigned)S.nblocks, kSetupThreads, smem, s>>>(P->pos.p, P->n, S.core, B, P->scl, p.shift,
-                                                                     p.escalate, S.L.p, S.shift_used.p, S.failed.p);
+    const float imq_beta = P->kernel == RBF_KERNEL_IMQ ? P->beta : 0.f;
+    k_schwarz_setup<<<(unsigned)S.nblocks, kSetupThreads, smem, s>>>(P->pos.p, P->n, S.core, B, P->scl, imq_beta,
+                                                                     p.shift, p.escalate, S.L.p, S.shift_used.p,
+                                                                     S.failed.p);
     RBF_LAUNCHED();
     if (failed_host) {
         std::vector<int32_t> f(S.nblocks);
