@@ -73,22 +73,33 @@ WORKLOADS = {
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_product_tc launch on the
 # 3,000,000-centre torus, from one ncu capture (profiles/k_product_tc_torus_sector.md gives the
 # command); valid only while the kernel sources hash to the values it was taken with.
-PRODUCT_TRAFFIC = {"torus1m": (156.64e6 + 9.10e6, {
-    "paper_1305_5179_b300/csrc/product_tc.cu": "7b1c29d5c5703c35308666b6511ff095d8634c978a1696da5ed8eff6e4430cf6",
-    "paper_1305_5179_b300/csrc/tcgen05.cuh": "eb1c4ef3c7182b1729de9e68052cb52ca5850d77a3c93fff07681ddd33baa43f"})}
+PRODUCT_TRAFFIC = {"torus1m": (157.304320e6 + 9.154560e6, {
+    "paper_1305_5179_b300/csrc/product_tc.cu": "31437d231516bf8177bae16a276df4690f11f9fc230ff1e71209644a1a4bad16",
+    "paper_1305_5179_b300/csrc/tcgen05.cuh": "b0f1821451b34e230cdc5000e9e34c3b6ce5dd95aef3f1df5a956d533ea2386e"})}
+
+# DRAM bytes of one k_spmv_csr launch per byte of its algorithmic traffic, from one ncu capture on
+# the 0.05-radian sector (23,871 centres, 514 MB of CSR; profiles/k_spmv_csr_torus_sector.md):
+# 524.3 MB measured / 514.2 MB algorithmic.  The product streams the matrix once, so the ratio
+# carries to larger sectors; valid while the kernel source hashes to the value it was taken with.
+SPMV_TRAFFIC_RATIO = (524.297984e6 / 514.242360e6, {
+    "paper_1305_5179_b300/csrc/assemble.cu": "5cb9c1615f631d9b1972ead40cb0f036a3f5ac5a334fed4155fc7c988e27d693"})
 
 
-def product_traffic(name):
+def sources_unchanged(hashes):
     import hashlib
-    if name not in PRODUCT_TRAFFIC:
-        return None
-    nbytes, hashes = PRODUCT_TRAFFIC[name]
     here = os.path.dirname(os.path.abspath(__file__))
     for rel, h in hashes.items():
         with open(os.path.join(here, rel), "rb") as fh:
             if hashlib.sha256(fh.read()).hexdigest() != h:
-                return None
-    return nbytes
+                return False
+    return True
+
+
+def product_traffic(name):
+    if name not in PRODUCT_TRAFFIC:
+        return None
+    nbytes, hashes = PRODUCT_TRAFFIC[name]
+    return nbytes if sources_unchanged(hashes) else None
 
 
 def make_cloud(wl):
@@ -465,7 +476,11 @@ def run_assembled(args, wl):
                "matrix_free": {"pairs": pairs, "ms_matvec": ms_mv, "pairs_per_s": pairs / (ms_mv * 1e-3),
                                "speedup_over_assembled": ms_spmv / ms_mv},
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                            "frac": achieved / peak, "traffic": None,
+                            "frac": achieved / peak,
+                            "traffic": (alg * SPMV_TRAFFIC_RATIO[0] if sources_unchanged(SPMV_TRAFFIC_RATIO[1])
+                                        else None),
+                            "traffic_basis": "bytes per launch: measured DRAM bytes per algorithmic byte on the "
+                                             "0.05-radian sector x this launch's algorithmic bytes",
                             "kernel": "k_spmv_csr (one warp per row, 16-byte streaming loads)",
                             "peak_basis": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth), of measured",
                             "algorithmic_bytes": alg},
