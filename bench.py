@@ -797,6 +797,13 @@ def main():
     ap.add_argument("--theta", type=float, default=0.0, help="assembled workload: sector angle (default 0.6)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
+    if args.impl == "reference" and args.workload in ("batch512", "isosurface", "paper_tables"):
+        # these workloads time GPU-only stages (the batched graph, the level set, the paper's
+        # table shapes); the oracle leg is the row-sum oracle of the default workload
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps({"impl": "reference", "workload": args.workload,
+                              "unavailable": "no oracle leg for this workload; run --workload torus1m"}))
+        return 0
     if args.workload == "batch512":
         return run_batch(args, wl)
     if args.workload == "density":
