@@ -49,7 +49,8 @@ struct DfConst {
 
 __constant__ float2 c_tab[64];   // 2^(-j/64) as (hi, lo)
 
-// sum over one staged block of w_j 2^(-t_ij) for the target (px, py, pz)
+// sum over one staged block of w_j 2^(-t_ij) for the target (px, py, pz); called by
+// every lane of a warp with the same cnt
 __device__ __forceinline__ df block_terms(float px, float py, float pz, const float4 *__restrict__ sp,
                                           const float2 *__restrict__ sw, int cnt, const DfConst &k,
                                           const float2 *__restrict__ tab) {
@@ -70,6 +71,9 @@ __device__ __forceinline__ df block_terms(float px, float py, float pz, const fl
         r2.l = __fadd_rn(r2.l, __fadd_rn(s.l, sz.l));
         r2 = two_sum(r2.h, r2.l);
         const bool in = (r2.h < k.Rh) || (r2.h == k.Rh && r2.l < k.Rl);
+        // a source beyond the cut-off for every target of the warp adds nothing: skip its
+        // exponential (the loop runs over the same sources on every lane, so the vote is uniform)
+        if (!__any_sync(0xffffffffu, in)) continue;
         // t = r2 * C
         df t = two_prod(r2.h, k.Ch);
         t.l = __fadd_rn(t.l, __fmaf_rn(r2.h, k.Cl, __fmul_rn(r2.l, k.Ch)));
