@@ -282,6 +282,7 @@ def run_ours(args, wl):
     # untimed: pair counts of the products and of the grid evaluation
     plan0, x0, f0, rep0 = step(pts, nrm)
     pairs_mv = plan0.count_pairs()
+    candidates_mv = plan0.count_candidate_pairs()
     pairs_grid = grid_pairs(plan0, wl, lo, hi, dims)
     n = plan0.n
     info = plan0.info()
@@ -365,6 +366,7 @@ def run_ours(args, wl):
                        "centres": n, "grid": list(dims), "fgmres_iterations": wl["iters"], "restart": wl["m"],
                        "precond": f"{wl['precond']} core {wl['core']} block {wl['block']} shift {wl['shift']}",
                        "pairs_per_matvec": pairs_mv, "pairs_grid": pairs_grid, "pairs_per_step": pairs_step,
+                       "candidate_pairs_per_matvec": candidates_mv, "waste_ratio": candidates_mv / pairs_mv,
                        "l2": "working set > L2 (FGMRES basis alone is "
                              f"{(wl['m'] + 1) * n * 8 / 1e9:.2f} GB)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",

@@ -149,7 +149,7 @@ typedef struct {
     int64_t n;              /* centres */
     int64_t ncells;         /* entries of the dense cell table (2^(3(nbits-levels))) */
     int64_t nblocks;        /* source blocks (runs of <= 32 centres inside one cell) */
-    int64_t nchunks;        /* target tiles (runs of 256 consecutive binned centres) */
+    int64_t nchunks;        /* target tiles (runs of <= 128 consecutive binned centres of one cell) */
     int64_t pairlist_len;   /* (tile, block) entries that survive the box test */
     int64_t nsegments;      /* work items of the product kernels */
     int nbits;              /* Morton bits per axis */
@@ -193,6 +193,14 @@ rbf_status rbf_matvec(rbf_plan *plan, const float *z, float *y, void *stream);
  * (all n^2 when k = 0), decided in double precision.  `count` is host memory.
  * Costs about one double-precision product. */
 rbf_status rbf_count_pairs(rbf_plan *plan, int64_t *count, void *stream);
+
+/* Number of (target, source) pairs the tensor-core product evaluates: for every
+ * pair-list entry, each quarter of 32 targets of its tile whose box test does not
+ * exclude the block, times the block's sources (pairs beyond the cut-off inside
+ * such quarter-block combinations are evaluated and masked).  Divided by
+ * rbf_count_pairs it is the product's waste ratio (>= 1; n^2 / n^2 = 1 when every
+ * pair is kept).  `count` is host memory; synchronises `stream`. */
+rbf_status rbf_count_candidate_pairs(rbf_plan *plan, int64_t *count, void *stream);
 
 /* True residual r = b - A~ x with float64-class accuracy, caller order.
  *   mode  : RBF_RESIDUAL_DF (default, 0): double-float arithmetic (pairs of

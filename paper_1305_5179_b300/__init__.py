@@ -33,7 +33,7 @@ RESIDUAL = {"df": 0, "f64": 1}
 EXPORTS = (
     "rbf_version", "rbf_launch_count", "rbf_probe_peaks", "rbf_status_string", "rbf_ctx_create", "rbf_ctx_destroy", "rbf_last_error",
     "rbf_build_centers", "rbf_plan_create", "rbf_plan_destroy", "rbf_plan_get_info", "rbf_plan_export_binning",
-    "rbf_matvec", "rbf_count_pairs", "rbf_residual",
+    "rbf_matvec", "rbf_count_pairs", "rbf_count_candidate_pairs", "rbf_residual",
     "rbf_plan_assemble", "rbf_plan_release_csr", "rbf_plan_export_csr", "rbf_spmv",
     "rbf_schwarz_setup", "rbf_schwarz_apply",
     "rbf_plan_solve", "rbf_solve", "rbf_plan_eval_grid", "rbf_count_grid_pairs", "rbf_eval_grid",
@@ -182,6 +182,7 @@ def lib() -> ctypes.CDLL:
         "rbf_batch_autotune": ([P, P, ctypes.POINTER(SolveParams), P, I, ctypes.POINTER(I), P, P], I),
         "rbf_eval_grid": ([P, P, P, I64, ctypes.POINTER(PlanParams), ctypes.POINTER(Grid), P, P], I),
         "rbf_plan_assemble": ([P, I64, ctypes.POINTER(I64), ctypes.POINTER(I64), P], I),
+        "rbf_count_candidate_pairs": ([P, ctypes.POINTER(I64), P], I),
         "rbf_plan_release_csr": ([P], I),
         "rbf_plan_export_csr": ([P, P, P, P, P], I),
         "rbf_spmv": ([P, P, P, P], I),
@@ -454,6 +455,13 @@ class Plan:
         y = torch.empty_like(z) if out is None else _req(out, torch.float32, "out", self.n)
         self.ctx.check(lib().rbf_spmv(self._h, _ptr(z), _ptr(y), _stream(stream)), "rbf_spmv")
         return y
+
+    def count_candidate_pairs(self, stream=None) -> int:
+        """Pairs the tensor-core product evaluates (the waste ratio's numerator)."""
+        c = ctypes.c_int64(0)
+        self.ctx.check(lib().rbf_count_candidate_pairs(self._h, ctypes.byref(c), _stream(stream)),
+                       "rbf_count_candidate_pairs")
+        return int(c.value)
 
     def residual(self, b, x, mode="df", stream=None):
         """True residual b - A~ x (float64); mode "df" (double-float) or "f64" (native)."""

@@ -238,6 +238,15 @@ rbf_status rbf_count_pairs(rbf_plan *P, int64_t *count, void *stream) {
     });
 }
 
+rbf_status rbf_count_candidate_pairs(rbf_plan *P, int64_t *count, void *stream) {
+    if (!P) return RBF_ERR_INVALID;
+    return guarded(P->ctx, [&]() {
+        RBF_CHECK(count, RBF_ERR_INVALID, "null count");
+        *count = count_candidates(P, S(stream));
+        return RBF_OK;
+    });
+}
+
 rbf_status rbf_residual(rbf_plan *P, const float *b, const double *x, double *r, double *norms, int mode,
                         void *stream) {
     if (!P) return RBF_ERR_INVALID;

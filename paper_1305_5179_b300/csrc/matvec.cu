@@ -381,6 +381,45 @@ int64_t count_grid_pairs_launch(rbf_plan *P, const PairList &pl, const rbf_grid 
     return (int64_t)h;
 }
 
+namespace {
+// Pairs the tensor-core product evaluates: per list entry, every quarter of 32 targets
+// whose code is not 0 times the block's sources.  One warp per tile.
+__global__ void k_count_candidates(const int32_t *__restrict__ off, const int2 *__restrict__ ebi,
+                                   const int2 *__restrict__ tiles, int64_t ntiles,
+                                   unsigned long long *__restrict__ cnt) {
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= ntiles) return;
+    const int nt = tiles[t].y;
+    unsigned long long c = 0;
+    for (int e = off[t] + lane; e < off[t + 1]; e += 32) {
+        const int w = ebi[e].y;
+        for (int q = 0; q < 4; ++q) {
+            const int tq = min(32, max(0, nt - 32 * q));
+            if ((w >> (8 + 2 * q)) & 3) c += (unsigned long long)tq * (unsigned long long)(w & 0xff);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0 && c) atomicAdd(cnt, c);
+}
+}  // namespace
+
+int64_t count_candidates(rbf_plan *P, cudaStream_t s) {
+    DevBuf<unsigned long long> c;
+    c.alloc(1, s);
+    c.zero(s);
+    const PairList &pl = P->pl;
+    if (pl.ntiles > 0 && pl.len > 0) {
+        k_count_candidates<<<(unsigned)ceil_div(pl.ntiles * 32, 256), 256, 0, s>>>(pl.off.p, pl.ebi.p, P->tiles.p,
+                                                                                 pl.ntiles, c.p);
+        RBF_LAUNCHED();
+    }
+    unsigned long long h = 0;
+    RBF_CUDA(cudaMemcpyAsync(&h, c.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(cudaStreamSynchronize(s));
+    return (int64_t)h;
+}
+
 int64_t count_pairs(rbf_plan *P, cudaStream_t s) {
     if (P->pairs >= 0) return P->pairs;
     if (P->k <= 0.f) {

@@ -130,6 +130,8 @@ void permute_from_binned_f64(const rbf_plan *P, const double *in, double *out, c
 void matvec_binned(rbf_plan *P, const float *zs, float *ys, cudaStream_t s);
 // Algorithmic pair count (cached on the plan).
 int64_t count_pairs(rbf_plan *P, cudaStream_t s);
+// Pairs the tensor-core product evaluates (see rbf_count_candidate_pairs).
+int64_t count_candidates(rbf_plan *P, cudaStream_t s);
 // r = b - A~ x in float64 (binned order); counts pairs when cnt != nullptr (device int64).
 void residual_binned_f64(rbf_plan *P, const float *bs, const double *xs, double *rs,
                          unsigned long long *cnt, cudaStream_t s);

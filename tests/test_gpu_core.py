@@ -243,6 +243,25 @@ def test_residual_modes_agree_dense(ctx, rbf, sphere_c1):
     assert np.abs(rd.cpu().numpy() - r64).max() <= 1e-12 * scale.max()
 
 
+def test_candidate_pairs_bound_the_algorithmic_ones(ctx, rbf, sphere_c1):
+    """The product's evaluated pairs: n^2 when every pair is kept (cut-off beyond the
+    cloud's diameter, or the untruncated inverse multiquadric), otherwise between the
+    algorithmic pairs and 4096 per list entry."""
+    C, _ = oracle.build_centers(sphere_c1.points, sphere_c1.normals, 0.05)
+    Cd, _ = c4(C)
+    n = len(C)
+    wide = rbf.Plan(ctx, Cd, sigma=0.2, k=12.0)              # 2.4 > the diameter 2.1
+    assert wide.count_pairs() == n * n and wide.count_candidate_pairs() == n * n
+    imq = rbf.Plan(ctx, Cd, sigma=0.1, k=0.0, kernel="imq", beta=2.0)
+    assert imq.count_candidate_pairs() == n * n
+    _, Ct, _ = torus_patch(theta=0.05)
+    Ctd, _ = c4(Ct)
+    plan = rbf.Plan(ctx, Ctd, sigma=0.02, k=6.0)
+    cand, pairs = plan.count_candidate_pairs(), plan.count_pairs()
+    assert pairs < cand <= 4096 * plan.info()["pairlist_len"]
+    assert cand < 2.5 * pairs          # measured 1.47 on the full torus
+
+
 # ---------------------------------------------------------------------- Schwarz
 def _schwarz_tol(Cs, sigma, parts, shift):
     """4 sqrt(B) eps32 kappa_max: forward error of float32 Cholesky solves."""
