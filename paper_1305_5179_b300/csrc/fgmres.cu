@@ -39,20 +39,43 @@ __device__ double block_sum_d(double v, double *sh) {
     return t;   // valid in thread 0
 }
 
-// partial[k * G + g] = sum over CTA g's range of V[k][i] * w[i], k < nv
+// partial[k * G + g] = sum over CTA g's range of V[k][i] * w[i], k < nv.  Eight vectors
+// per sweep of the range (eight independent loads in flight per element); each thread
+// sums its elements in index order and the block reduces as block_sum_d does.
+constexpr int kDotGroup = 8;
 template <typename Tw>
 __global__ void __launch_bounds__(kThreads) k_mdot(const double *__restrict__ V, int64_t ldv, int nv,
                                                    const Tw *__restrict__ w, int64_t n, double *__restrict__ partial) {
-    __shared__ double sh[kThreads / 32];
-    int G = gridDim.x;
-    int64_t per = (n + G - 1) / G;
-    int64_t i0 = blockIdx.x * per, i1 = min(n, i0 + per);
-    for (int k = 0; k < nv; ++k) {
-        const double *vk = V + k * ldv;
-        double s = 0.0;
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += kThreads) s += vk[i] * ld(w, i);
-        double t = block_sum_d(s, sh);
-        if (threadIdx.x == 0) partial[(int64_t)k * G + blockIdx.x] = t;
+    __shared__ double sh[kDotGroup][kThreads / 32];
+    const int G = gridDim.x;
+    const int64_t per = (n + G - 1) / G;
+    const int64_t i0 = blockIdx.x * per, i1 = min(n, i0 + per);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k0 = 0; k0 < nv; k0 += kDotGroup) {
+        const int kn = min(kDotGroup, nv - k0);
+        const double *v0 = V + (int64_t)k0 * ldv;
+        double s[kDotGroup];
+#pragma unroll
+        for (int q = 0; q < kDotGroup; ++q) s[q] = 0.0;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += kThreads) {
+            const double wi = ld(w, i);
+#pragma unroll
+            for (int q = 0; q < kDotGroup; ++q)
+                if (q < kn) s[q] += v0[q * ldv + i] * wi;
+        }
+#pragma unroll
+        for (int q = 0; q < kDotGroup; ++q) {
+            double v = s[q];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) sh[q][warp] = v;
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < kn) {
+            double t = 0.0;
+            for (int u = 0; u < kThreads / 32; ++u) t += sh[threadIdx.x][u];
+            partial[(int64_t)(k0 + threadIdx.x) * G + blockIdx.x] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -81,6 +104,7 @@ __global__ void __launch_bounds__(kThreads) k_maxpy(const double *__restrict__ V
     double sq = 0.0;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += kThreads) {
         double v = ld(win, i);
+#pragma unroll 8
         for (int k = 0; k < nv; ++k) v -= hs[k] * V[k * ldv + i];
         wout[i] = v;
         sq += v * v;
