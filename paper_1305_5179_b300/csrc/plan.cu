@@ -493,6 +493,67 @@ __global__ void k_pl_expand(CellGridArgs g, const int32_t *__restrict__ off, int
 }
 }  // namespace
 
+namespace {
+// Exact quarter codes for the plan's own tiles.  The box tests leave a (quarter, block)
+// undecided (code 1) when the boxes straddle the cut-off; here the smallest and largest
+// squared distance between the quarter's targets and the block's sources decide it: 0
+// when every pair lies beyond rc^2 (1 + 1e-5), 2 when every pair lies within rc^2 (1 - 1e-5),
+// else 1.  The margins exceed the float32 distance error and the tensor-core exponent's,
+// so a pair's contribution does not change: only the work to find it does.  The pairwise
+// loop stops as soon as the warp has seen a pair inside and a pair outside (the quarter
+// stays undecided), so only quarters that turn out uniform pay the full 32 x 32 test.
+// One warp per tile; the tile's targets are staged in shared memory.
+constexpr int kRefWarps = 8;
+__global__ void __launch_bounds__(kRefWarps * 32) k_pl_refine(const float4 *__restrict__ pos,
+                                                              const int2 *__restrict__ tiles,
+                                                              const int32_t *__restrict__ off, int64_t ntiles,
+                                                              float lo2, float hi2, int2 *__restrict__ ebi) {
+    __shared__ float4 s_t[kRefWarps][kChunk];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * kRefWarps + warp;
+    if (t >= ntiles) return;
+    const int2 tl = tiles[t];
+    for (int q = lane; q < kChunk; q += 32)
+        s_t[warp][q] = q < tl.y ? pos[tl.x + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+    for (int e = off[t]; e < off[t + 1]; ++e) {
+        const int2 w = ebi[e];
+        const int codes = (w.y >> 8) & 0xff;
+        if (((codes & 0x55) & ~(codes >> 1)) == 0) continue;     // no quarter with code 1
+        const int cnt = w.y & 0xff;
+        const float4 src = lane < cnt ? pos[w.x + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        int nc = codes;
+        for (int q = 0; q < 4; ++q) {
+            if (((codes >> (2 * q)) & 3) != 1) continue;
+            const int nq = min(32, tl.y - 32 * q);
+            float mn = INFINITY, mx = 0.f;
+            bool mixed = false;
+            for (int r0 = 0; r0 < nq && !mixed; r0 += 8) {
+                for (int r = r0; r < min(nq, r0 + 8); ++r) {
+                    const float4 p = s_t[warp][32 * q + r];
+                    const float dx = p.x - src.x, dy = p.y - src.y, dz = p.z - src.z;
+                    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    if (lane < cnt) {
+                        mn = fminf(mn, d2);
+                        mx = fmaxf(mx, d2);
+                    }
+                }
+                mixed = __any_sync(0xffffffffu, mn <= hi2) && __any_sync(0xffffffffu, mx >= lo2);
+            }
+            if (mixed) continue;     // stays 1
+            for (int o = 16; o > 0; o >>= 1) {
+                mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            }
+            const int c = mn > hi2 ? 0 : (mx < lo2 ? 2 : 1);
+            nc = (nc & ~(3 << (2 * q))) | (c << (2 * q));
+        }
+        if (lane == 0 && nc != codes) ebi[e].y = (w.y & ~(0xff << 8)) | (nc << 8);
+        __syncwarp();
+    }
+}
+}  // namespace
+
 void build_pairlist(rbf_plan *P, const float4 *tlo, const float4 *thi, const float4 *qlo, const float4 *qhi,
                     int64_t ntiles, PairList &pl, cudaStream_t s) {
     CellGridArgs g;
@@ -705,4 +766,10 @@ void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s, bool binning
                                                               P->chk_hi.p, qlo.p, qhi.p);
     RBF_LAUNCHED();
     build_pairlist(P, P->chk_lo.p, P->chk_hi.p, qlo.p, qhi.p, P->nchk, P->pl, s);
+    if (P->k > 0.f && P->pl.len > 0) {
+        const float rc2 = P->rc * P->rc;
+        k_pl_refine<<<(unsigned)ceil_div(P->nchk, kRefWarps), kRefWarps * 32, 0, s>>>(
+            P->pos.p, P->tiles.p, P->pl.off.p, P->nchk, rc2 * (1.f - 1e-5f), rc2 * (1.f + 1e-5f), P->pl.ebi.p);
+        RBF_LAUNCHED();
+    }
 }
