@@ -1,7 +1,8 @@
 // Step 3 of Algorithm 1 (Eq. matxvet): P_f on the nodes of a structured grid.
 //
 // The grid is cut into bricks of 8 x 4 x 4 nodes (128 targets, one tile of the
-// product kernel); each brick gets a box and a pair list against the source
+// product kernel; its four quarters of 32 nodes are blocks of 4 x 2 x 4); each brick
+// gets a box and a pair list against the source
 // blocks exactly like the tiles of centres, so bricks far from every centre
 // cost nothing.  The pair list is cached on the plan for repeated grids.
 #include <cmath>
@@ -15,8 +16,9 @@ int64_t count_grid_pairs_launch(rbf_plan *P, const PairList &pl, const rbf_grid 
 
 namespace {
 
-// Brick boxes, and the boxes of its four quarters of 32 nodes (the z layers of the
-// brick; a layer outside the grid gets lo > hi).
+// Brick boxes, and the boxes of its four quarters of 32 nodes (blocks of 4 x 2 x 4
+// nodes, quarter u at x offset 4 (u & 1) and y offset 2 (u >> 1); a quarter entirely
+// outside the grid gets lo > hi).
 __global__ void k_brick_boxes(int64_t nb, int bx, int by, int gx, int gy, int gz, float lox, float loy, float loz,
                               float sx, float sy, float sz, float4 *__restrict__ lo, float4 *__restrict__ hi,
                               float4 *__restrict__ qlo, float4 *__restrict__ qhi) {
@@ -27,14 +29,15 @@ __global__ void k_brick_boxes(int64_t nb, int bx, int by, int gx, int gy, int gz
     int x1 = min(x0 + 7, gx - 1), y1 = min(y0 + 3, gy - 1), z1 = min(z0 + 3, gz - 1);
     const float X0 = fmaf((float)x0, sx, lox), Y0 = fmaf((float)y0, sy, loy);
     const float X1 = fmaf((float)x1, sx, lox), Y1 = fmaf((float)y1, sy, loy);
-    lo[t] = make_float4(X0, Y0, fmaf((float)z0, sz, loz), 0.f);
-    hi[t] = make_float4(X1, Y1, fmaf((float)z1, sz, loz), 0.f);
+    const float Z0 = fmaf((float)z0, sz, loz), Z1 = fmaf((float)z1, sz, loz);
+    lo[t] = make_float4(X0, Y0, Z0, 0.f);
+    hi[t] = make_float4(X1, Y1, Z1, 0.f);
     for (int u = 0; u < 4; ++u) {
-        const int zu = z0 + u;
-        const float Z = fmaf((float)zu, sz, loz);
-        if (zu < gz) {
-            qlo[4 * t + u] = make_float4(X0, Y0, Z, 0.f);
-            qhi[4 * t + u] = make_float4(X1, Y1, Z, 0.f);
+        const int xa = x0 + 4 * (u & 1), ya = y0 + 2 * (u >> 1);
+        if (xa < gx && ya < gy) {
+            const int xb = min(xa + 3, gx - 1), yb = min(ya + 1, gy - 1);
+            qlo[4 * t + u] = make_float4(fmaf((float)xa, sx, lox), fmaf((float)ya, sy, loy), Z0, 0.f);
+            qhi[4 * t + u] = make_float4(fmaf((float)xb, sx, lox), fmaf((float)yb, sy, loy), Z1, 0.f);
         } else {
             qlo[4 * t + u] = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
             qhi[4 * t + u] = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);

@@ -74,8 +74,12 @@ __device__ __forceinline__ bool target_xyz(const MvArgs &a, int64_t t, int q, fl
         outidx = -1;
         return false;
     } else {
+        // brick of 8 x 4 x 4 nodes; quarter u = q / 32 is its (u & 1, u >> 1) block of 4 x 2 x 4 nodes
+        // (compact, so that the quarter box tests of the pair list are tight)
         int64_t bx = t % a.bdim[0], by = (t / a.bdim[0]) % a.bdim[1], bz = t / ((int64_t)a.bdim[0] * a.bdim[1]);
-        int ix = (int)bx * 8 + (q & 7), iy = (int)by * 4 + ((q >> 3) & 3), iz = (int)bz * 4 + (q >> 5);
+        const int u = q >> 5, l = q & 31;
+        int ix = (int)bx * 8 + 4 * (u & 1) + (l & 3), iy = (int)by * 4 + 2 * (u >> 1) + ((l >> 2) & 1),
+            iz = (int)bz * 4 + (l >> 3);
         bool v = ix < a.gdim[0] && iy < a.gdim[1] && iz < a.gdim[2];
         x = fmaf((float)ix, a.gstep[0], a.glo[0]);
         y = fmaf((float)iy, a.gstep[1], a.glo[1]);
