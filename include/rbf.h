@@ -471,9 +471,10 @@ rbf_status rbf_mlp_train(rbf_mlp *mlp, const float *X, const float *T, int64_t n
  * Batched solve of many independent problems (for example many clouds of
  * uneven size, each with its own sigma): one plan per problem, solved together
  * by flexible GMRES in lockstep with every step on the device, so that a whole
- * solve is a single CUDA graph launch.  The product is a persistent kernel
- * whose CTAs take (problem, segment) work items, longest first, from an atomic
- * counter; the Arnoldi reductions are segmented per problem; the Givens
+ * solve is a single CUDA graph launch.  The product runs one CTA per
+ * (problem, segment) work item, longest first: the tensor-core kernel when every
+ * plan takes RBF_PRODUCT_TC, else a persistent CUDA-core kernel whose CTAs take
+ * items from an atomic counter; the Arnoldi reductions are segmented per problem; the Givens
  * rotations and the triangular solve run on the device.  The iteration count
  * is fixed (max_it, restarted every m <= 64), as in the paper's timing protocol
  * (Table II); each problem reports its own float64-class true residual.
@@ -485,7 +486,7 @@ typedef struct {
     double ms_solve;            /* gather, graph launch, scatter, milliseconds (CUDA events) */
     int64_t graph_nodes;        /* nodes of the captured solve (0 when it was replayed) */
     int recaptured;             /* 1 if this call captured the graph */
-    int persistent_ctas;        /* CTAs of the persistent product */
+    int persistent_ctas;        /* CTAs of the persistent CUDA-core product (unused by the tensor-core one) */
     int64_t work_items;         /* (problem, segment) items per product */
     int converged;              /* problems whose true residual met tol */
     double worst_residual;      /* largest relative true residual over the problems */

@@ -553,6 +553,7 @@ rbf_status rbf_batch_matvec(rbf_batch *batch, const float *z, float *y, void *st
         RBF_CHECK(z && y && z != y, RBF_ERR_INVALID, "z and y must be distinct device pointers");
         cudaStream_t s = S(stream);
         const int64_t N = batch_size(batch);
+        ctx_check_device_error(ctx);
         DevBuf<float> zs, ys;
         zs.alloc(N, s);
         ys.alloc(N, s);

@@ -47,6 +47,7 @@ struct rbf_batch {
     PBuf<int64_t> part_off_d;
     PBuf<unsigned int> counter;
     int persistent_ctas = 0;
+    bool tc = false;              // every plan takes the tensor-core product
     int schwarz_block = 0;        // block size of the current Schwarz set-up (0 = none)
     // solve state
     int m_alloc = 0;
@@ -532,6 +533,9 @@ rbf_batch *batch_create(rbf_ctx *ctx, rbf_plan *const *plans, int nplans, cudaSt
         RBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bmatvec, kWarps * 32, 0));
         Bt->persistent_ctas = std::max(1, per_sm) * ctx->num_sms;
         residual_df_prepare(ctx->device, s);
+        Bt->tc = true;
+        for (int b = 0; b < nplans; ++b) Bt->tc = Bt->tc && plans[b]->product == RBF_PRODUCT_TC;
+        if (Bt->tc) product_tc_prepare(ctx->device);
         batch_refresh_views(Bt, s);
     } catch (...) {
         delete Bt;
@@ -571,10 +575,16 @@ static void batch_alloc(rbf_batch *Bt, int m, cudaStream_t s) {
 }
 
 void batch_matvec_binned(rbf_batch *Bt, const float *z, float *y, cudaStream_t s) {
-    RBF_CUDA(cudaMemsetAsync(Bt->counter.p, 0, sizeof(unsigned int), s));
-    const int grid = (int)std::min<int64_t>(Bt->persistent_ctas, std::max<int64_t>(Bt->nseg_items, 1));
-    k_bmatvec<<<grid, kWarps * 32, 0, s>>>(Bt->views.p, Bt->seg_items.p, (int)Bt->nseg_items, Bt->counter.p, z, y);
-    RBF_LAUNCHED();
+    if (Bt->tc) {
+        product_tc_batched_launch(Bt->views.p, Bt->seg_items.p, Bt->nseg_items, z, y, ctx_error_word(Bt->ctx),
+                                  Bt->ctx->device, s);
+    } else {
+        RBF_CUDA(cudaMemsetAsync(Bt->counter.p, 0, sizeof(unsigned int), s));
+        const int grid = (int)std::min<int64_t>(Bt->persistent_ctas, std::max<int64_t>(Bt->nseg_items, 1));
+        k_bmatvec<<<grid, kWarps * 32, 0, s>>>(Bt->views.p, Bt->seg_items.p, (int)Bt->nseg_items, Bt->counter.p, z,
+                                               y);
+        RBF_LAUNCHED();
+    }
     if (Bt->nsplit > 0) {
         k_breduce_split<<<(unsigned)Bt->nsplit, kChunk, 0, s>>>(Bt->views.p, Bt->split_tiles.p, y);
         RBF_LAUNCHED();
@@ -743,6 +753,7 @@ rbf_status batch_solve(rbf_batch *Bt, const float *b, const rbf_solve_params &p,
         RBF_CUDA(cudaMemcpyAsync(bn.data(), Bt->bn2.p, Bt->nb * sizeof(double), cudaMemcpyDeviceToHost, s));
         RBF_CUDA(cudaMemcpyAsync(es.data(), Bt->est.p, Bt->nb * sizeof(double), cudaMemcpyDeviceToHost, s));
         RBF_CUDA(cudaStreamSynchronize(s));
+        ctx_check_device_error(Bt->ctx);     // a tensor-core product that gave up on a wait
         float msa = 0, msb = 0;
         cudaEventElapsedTime(&msa, e0, e1);
         cudaEventElapsedTime(&msb, e1, e2);

@@ -27,6 +27,13 @@ struct PlanView {
     int64_t nsub;
 };
 
+// Tensor-core product of every problem of a batch (product_tc.cu): one CTA per
+// (problem, segment) item; split tiles' partial sums go to each view's `partial`.
+void product_tc_batched_launch(const PlanView *views, const int2 *items, int64_t nitems, const float *z, float *y,
+                               unsigned *err, int device, cudaStream_t s);
+// Sets the product kernels' shared-memory attribute on `device` (call before any capture).
+void product_tc_prepare(int device);
+
 // Uploads the exp2 table once per device (synchronises; call before any capture).
 void residual_df_prepare(int device, cudaStream_t s);
 

@@ -32,6 +32,7 @@
 // tensor memory.
 #include <cmath>
 
+#include "batch.cuh"
 #include "plan.cuh"
 #include "product.cuh"
 #include "tcgen05.cuh"
@@ -108,12 +109,13 @@ __device__ __forceinline__ void raise_error(TcSmem &S, unsigned *err) {
     if (err) atomicOr(err, 1u);
 }
 
+// One segment sg of a pair list; `slot` indexes its row of partial sums when its tile
+// has more than one segment.  Run by a whole CTA of kThreadsTc threads.
 template <bool kGrid>
-__global__ void __launch_bounds__(kThreadsTc, 4) k_product_tc(MvArgs a, unsigned *err) {
+__device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, int64_t slot, unsigned *err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     TcSmem &S = *reinterpret_cast<TcSmem *>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int4 sg = a.seg[blockIdx.x];
     const int64_t t = sg.x;
     const int nb = sg.z - sg.y;
 
@@ -371,7 +373,7 @@ __global__ void __launch_bounds__(kThreadsTc, 4) k_product_tc(MvArgs a, unsigned
         if (sg.w) {
             if (valid) a.out[oi] = y;
         } else {
-            a.partial[(int64_t)blockIdx.x * kChunk + threadIdx.x] = y;
+            a.partial[slot * kChunk + threadIdx.x] = y;
         }
     }
 
@@ -384,6 +386,36 @@ __global__ void __launch_bounds__(kThreadsTc, 4) k_product_tc(MvArgs a, unsigned
 }
 
 template <bool kGrid>
+__global__ void __launch_bounds__(kThreadsTc, 4) k_product_tc(MvArgs a, unsigned *err) {
+    product_tc_body<kGrid>(a, a.seg[blockIdx.x], blockIdx.x, err);
+}
+
+// Many problems at once: CTA = one (problem, segment) item of a batch.
+__global__ void __launch_bounds__(kThreadsTc, 4) k_bproduct_tc(const PlanView *__restrict__ views,
+                                                              const int2 *__restrict__ items,
+                                                              const float *__restrict__ z, float *__restrict__ y,
+                                                              unsigned *err) {
+    const int2 ci = items[blockIdx.x];
+    const PlanView &v = views[ci.x];
+    MvArgs a{};
+    a.pos = v.pos;
+    a.tiles = v.tiles;
+    a.src = v.src;
+    a.w = z + v.off;
+    a.blk = v.blk;
+    a.blk_c = v.blk_c;
+    a.ent = v.ent;
+    a.ebi = v.ebi;
+    a.seg = v.seg;
+    a.n = v.n;
+    a.scl = v.scl;
+    a.R = v.R;
+    a.out = y + v.off;
+    a.partial = v.partial;
+    product_tc_body<false>(a, v.seg[ci.y], ci.y, err);
+}
+
+template <bool kGrid>
 void set_smem_attr(int device) {
     static bool done[64] = {};
     if (device >= 0 && device < 64 && !done[device]) {
@@ -393,6 +425,24 @@ void set_smem_attr(int device) {
 }
 
 }  // namespace
+
+void product_tc_prepare(int device) {
+    set_smem_attr<false>(device);
+    set_smem_attr<true>(device);
+    static bool done[64] = {};
+    if (device >= 0 && device < 64 && !done[device]) {
+        RBF_CUDA(cudaFuncSetAttribute(k_bproduct_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTc));
+        done[device] = true;
+    }
+}
+
+void product_tc_batched_launch(const PlanView *views, const int2 *items, int64_t nitems, const float *z, float *y,
+                               unsigned *err, int device, cudaStream_t s) {
+    if (nitems <= 0) return;
+    product_tc_prepare(device);
+    k_bproduct_tc<<<(unsigned)nitems, kThreadsTc, kSmemTc, s>>>(views, items, z, y, err);
+    RBF_LAUNCHED();
+}
 
 // The product over a pair list with the tensor-core exponent (see the top of this file).
 void product_tc_launch(const rbf_plan *P, const PairList &pl, const rbfk::MvArgs &a, bool grid, cudaStream_t s) {
