@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "batch.cuh"
+#include "schwarz.cuh"
 #include "product.cuh"
 
 using rbfk::kWarps;
@@ -143,40 +144,7 @@ __global__ void k_bschwarz_apply(const PlanView *__restrict__ views, const int2 
         int k = lane + 32 * q;
         yv[q] = k < B ? (float)vv[d0 + k] : 0.f;
     }
-    for (int j = 0; j < B; ++j) {
-        const float *row = L + (int64_t)j * B;
-        float acc = 0.f;
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            int k = lane + 32 * q;
-            if (32 * q < j && k < j) acc = fmaf(row[k], yv[q], acc);
-        }
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        float ljj = row[j];
-        if (lane == (j & 31)) {
-#pragma unroll
-            for (int q = 0; q < Q; ++q)
-                if (q == (j >> 5)) yv[q] = (yv[q] - acc) / ljj;
-        }
-    }
-    for (int j = B - 1; j >= 0; --j) {
-        const float *row = L + (int64_t)j * B;
-        float yj = 0.f;
-#pragma unroll
-        for (int q = 0; q < Q; ++q)
-            if (q == (j >> 5)) yj = yv[q];
-        float xj = __shfl_sync(0xffffffffu, yj, j & 31) / row[j];
-        if (lane == (j & 31)) {
-#pragma unroll
-            for (int q = 0; q < Q; ++q)
-                if (q == (j >> 5)) yv[q] = xj;
-        }
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            int k = lane + 32 * q;
-            if (32 * q < j && k < j) yv[q] = fmaf(-row[k], xj, yv[q]);
-        }
-    }
+    ras::solve_block(L, B, yv, lane);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         int k = lane + 32 * q;

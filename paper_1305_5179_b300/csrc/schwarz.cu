@@ -12,6 +12,7 @@
 #include <cmath>
 
 #include "plan.cuh"
+#include "schwarz.cuh"
 
 namespace {
 
@@ -113,43 +114,7 @@ __global__ void k_schwarz_apply(const Tin *__restrict__ v, int64_t n, int core, 
         int k = lane + 32 * q;
         y[q] = k < B ? (float)v[d0 + k] : 0.f;
     }
-    // forward: y_j = (v_j - sum_{k<j} L_jk y_k) / L_jj
-    for (int j = 0; j < B; ++j) {
-        const float *row = L + (int64_t)j * B;
-        float s = 0.f;
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            int k = lane + 32 * q;
-            if (32 * q < j && k < j) s = fmaf(row[k], y[q], s);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        float ljj = row[j];
-        if (lane == (j & 31)) {
-#pragma unroll
-            for (int q = 0; q < Q; ++q)
-                if (q == (j >> 5)) y[q] = (y[q] - s) / ljj;
-        }
-    }
-    // backward: x_j = y_j / L_jj; y_k -= L_jk x_j for k < j
-    for (int j = B - 1; j >= 0; --j) {
-        const float *row = L + (int64_t)j * B;
-        float yj = 0.f;
-#pragma unroll
-        for (int q = 0; q < Q; ++q)
-            if (q == (j >> 5)) yj = y[q];
-        float xj = __shfl_sync(0xffffffffu, yj, j & 31) / row[j];
-        if (lane == (j & 31)) {
-#pragma unroll
-            for (int q = 0; q < Q; ++q)
-                if (q == (j >> 5)) y[q] = xj;
-        }
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            int k = lane + 32 * q;
-            if (32 * q < j && k < j) y[q] = fmaf(-row[k], xj, y[q]);
-        }
-    }
+    ras::solve_block(L, B, y, lane);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         int k = lane + 32 * q;
