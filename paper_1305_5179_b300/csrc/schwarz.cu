@@ -4,11 +4,10 @@
 // [s_i, s_i + core) (B = min(block, n), d0_i = clamp(s_i - (block - core)/2, 0,
 // n - B)).  Set-up: one CTA per subdomain assembles the untruncated Gaussian
 // block A_i + shift I in shared memory (float32, exp2 on the SFU) and factorises
-// it in place by a right-looking Cholesky (one thread per column); a failed
+// it in place by a blocked right-looking Cholesky on 32 x 32 tiles; a failed
 // pivot retries with a 10x larger shift when escalation is on.  Apply: one warp
-// per subdomain gathers v, solves L y = v (row dots, warp reductions) and
-// L^T x = y (row updates), and writes the core entries (restricted) or adds
-// the whole local solution (additive).
+// per subdomain gathers v, solves L y = v and L^T x = y tile by tile (ras::solve_block),
+// and writes the core entries (restricted) or adds the whole local solution (additive).
 #include <cmath>
 
 #include "plan.cuh"
@@ -32,49 +31,116 @@ __device__ __forceinline__ void dom_of(int64_t blkid, int core, int B, int64_t n
     cl = (int)(e - s);
 }
 
+// Blocked Cholesky of the padded matrix (Bp = B rounded up to 32, identity beyond B) in
+// shared memory, tiles of 32 x 32, right-looking: the diagonal tile by all threads (per
+// column: pivot, scaled column, the tile's trailing triangle), the panel below it by one
+// thread per row (substitution against the diagonal tile), the trailing tiles by the
+// four warps (each lane one column of a tile, the panel rows broadcast from shared
+// memory).  A pivot that is not positive and finite fails the attempt.
 __global__ void __launch_bounds__(kSetupThreads) k_schwarz_setup(const float4 *__restrict__ pos, int64_t n, int core,
                                                                  int B, float scl, float imq_beta, float shift,
                                                                  int escalate,
                                                                  float *__restrict__ Lout, float *__restrict__ shift_used,
                                                                  int32_t *__restrict__ failed) {
     extern __shared__ float sm[];
-    const int ld = B + 1;
-    float *A = sm;                                  // B x (B + 1), padded rows
+    const int Bp = (B + 31) & ~31, T = Bp >> 5, ld = Bp + 1;
+    float *A = sm;                                  // Bp x (Bp + 1), padded rows
+    float4 *P = reinterpret_cast<float4 *>(sm + Bp * ld);   // the block's positions
     __shared__ int s_fail;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t d0, c0;
     int cl;
     dom_of(blockIdx.x, core, B, n, d0, c0, cl);
+    for (int i = threadIdx.x; i < B; i += blockDim.x) P[i] = pos[d0 + i];
+    __syncthreads();
     float lam = shift;
     int attempts = escalate ? 5 : 1;
     int ok = 0;
     for (int att = 0; att < attempts && !ok; ++att, lam *= 10.f) {
-        for (int idx = threadIdx.x; idx < B * B; idx += blockDim.x) {
-            int i = idx / B, j = idx % B;
+        for (int idx = threadIdx.x; idx < Bp * Bp; idx += blockDim.x) {
+            const int i = idx / Bp, j = idx % Bp;
             if (j > i) continue;
-            float4 pi = pos[d0 + i], pj = pos[d0 + j];   // difference before scaling keeps it exact-ish
-            float dx = (pi.x - pj.x) * scl, dy = (pi.y - pj.y) * scl, dz = (pi.z - pj.z) * scl;
-            const float t = dx * dx + dy * dy + dz * dz;   // |d|^2 log2(e) / (2 sigma^2)
-            // Gaussian 2^-t; inverse multiquadric (1 + |d|^2 / sigma^2)^-beta, |d|^2 / sigma^2 = 2 ln(2) t
-            float v = imq_beta > 0.f ? ex2_approx(-imq_beta * __log2f(fmaf(t, 1.3862943611198906f, 1.f)))
-                                     : ex2_approx(-t);
-            A[i * ld + j] = (i == j) ? 1.f + lam : v;
+            float v;
+            if (i >= B) {
+                v = i == j ? 1.f : 0.f;                 // padding: identity
+            } else if (i == j) {
+                v = 1.f + lam;
+            } else {
+                const float4 pi = P[i], pj = P[j];   // difference before scaling keeps it exact-ish
+                float dx = (pi.x - pj.x) * scl, dy = (pi.y - pj.y) * scl, dz = (pi.z - pj.z) * scl;
+                const float t = dx * dx + dy * dy + dz * dz;   // |d|^2 log2(e) / (2 sigma^2)
+                // Gaussian 2^-t; inverse multiquadric (1 + |d|^2 / sigma^2)^-beta, |d|^2 / sigma^2 = 2 ln(2) t
+                v = imq_beta > 0.f ? ex2_approx(-imq_beta * __log2f(fmaf(t, 1.3862943611198906f, 1.f)))
+                                   : ex2_approx(-t);
+            }
+            A[i * ld + j] = v;
         }
         if (threadIdx.x == 0) s_fail = 0;
         __syncthreads();
-        for (int j = 0; j < B; ++j) {
-            if (threadIdx.x == 0) {
-                float d = A[j * ld + j];
-                if (!(d > 0.f) || !isfinite(d)) s_fail = 1;
-                A[j * ld + j] = sqrtf(fmaxf(d, 1e-30f));
+        for (int k = 0; k < T; ++k) {
+            const int k0 = 32 * k;
+            // 1. diagonal tile, in shared memory: per column jj the pivot, the column scaled by
+            //    it, then the tile's remaining lower triangle updated (32 x 32 elements spread
+            //    over the CTA's threads)
+            for (int jj = 0; jj < 32; ++jj) {
+                const int j = k0 + jj;
+                const float d = A[j * ld + j];
+                if (threadIdx.x == 0 && (!(d > 0.f) || !isfinite(d))) s_fail = 1;
+                const float ljj = sqrtf(fmaxf(d, 1e-30f));
+                __syncthreads();
+                if (threadIdx.x < 32) {
+                    const int r = k0 + threadIdx.x;
+                    if (threadIdx.x == jj) A[j * ld + j] = ljj;
+                    else if ((int)threadIdx.x > jj) A[r * ld + j] /= ljj;
+                }
+                __syncthreads();
+                for (int e = threadIdx.x; e < 32 * 32; e += kSetupThreads) {
+                    const int rr = e >> 5, cc = e & 31;
+                    if (cc > jj && rr >= cc)
+                        A[(k0 + rr) * ld + k0 + cc] =
+                            fmaf(-A[(k0 + rr) * ld + j], A[(k0 + cc) * ld + j], A[(k0 + rr) * ld + k0 + cc]);
+                }
+                __syncthreads();     // the next pivot is written by this update
             }
             __syncthreads();
             if (s_fail) break;
-            float ljj = A[j * ld + j];
-            for (int i = j + 1 + threadIdx.x; i < B; i += blockDim.x) A[i * ld + j] /= ljj;
+            // 2. panel: rows below the diagonal tile, X = A_ik L_kk^-T
+            const int r = k0 + 32 + threadIdx.x;
+            if (r < Bp) {
+                float x[32];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) x[c] = A[r * ld + k0 + c];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    float acc = x[c];
+#pragma unroll
+                    for (int m = 0; m < c; ++m) acc = fmaf(-x[m], A[(k0 + c) * ld + k0 + m], acc);
+                    x[c] = acc / A[(k0 + c) * ld + k0 + c];
+                }
+#pragma unroll
+                for (int c = 0; c < 32; ++c) A[r * ld + k0 + c] = x[c];
+            }
             __syncthreads();
-            for (int c = j + 1 + threadIdx.x; c < B; c += blockDim.x) {
-                float lcj = A[c * ld + j];
-                for (int i = c; i < B; ++i) A[i * ld + c] = fmaf(-A[i * ld + j], lcj, A[i * ld + c]);
+            // 3. trailing tiles (i, l), k < l <= i: A_il -= X_i X_l^T
+            const int Tr = T - 1 - k;
+            const int ntiles = Tr * (Tr + 1) / 2;
+            for (int q = warp; q < ntiles; q += kSetupThreads / 32) {
+                int i = 0, l = q;                        // q -> (i, l) with l <= i over the trailing tiles
+                while (l > i) {
+                    l -= i + 1;
+                    ++i;
+                }
+                const int ri = k0 + 32 + 32 * i, cl0 = k0 + 32 + 32 * l;
+                float xl[32];
+#pragma unroll
+                for (int m = 0; m < 32; ++m) xl[m] = A[(cl0 + lane) * ld + k0 + m];
+                for (int rr = 0; rr < 32; ++rr) {
+                    const float *xi = A + (ri + rr) * ld + k0;
+                    float acc = 0.f;
+#pragma unroll
+                    for (int m = 0; m < 32; ++m) acc = fmaf(xi[m], xl[m], acc);
+                    A[(ri + rr) * ld + cl0 + lane] -= acc;
+                }
             }
             __syncthreads();
         }
@@ -145,7 +211,8 @@ void schwarz_setup(rbf_plan *P, const rbf_schwarz_params &p, int64_t *failed_hos
     S.L.alloc((size_t)S.nblocks * B * B, s);
     S.shift_used.alloc(S.nblocks, s);
     S.failed.alloc(S.nblocks, s);
-    size_t smem = (size_t)B * (B + 1) * sizeof(float);
+    const int Bp = (B + 31) & ~31;
+    size_t smem = (size_t)Bp * (Bp + 1) * sizeof(float) + (size_t)Bp * sizeof(float4);
     RBF_CUDA(cudaFuncSetAttribute(k_schwarz_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const float imq_beta = P->kernel == RBF_KERNEL_IMQ ? P->beta : 0.f;
     k_schwarz_setup<<<(unsigned)S.nblocks, kSetupThreads, smem, s>>>(P->pos.p, P->n, S.core, B, P->scl, imq_beta,
