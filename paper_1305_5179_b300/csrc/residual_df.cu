@@ -36,6 +36,14 @@ __device__ __forceinline__ df two_sum(float a, float b) {
     return {s, e};
 }
 
+// The same sum and error as two_sum when |a| >= |b| (Dekker's Fast2Sum).
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// two_sum of two non-negative numbers, ordered first (the sum is the same either way).
+__device__ __forceinline__ df two_sum_pos(float a, float b) { return fast_two_sum(fmaxf(a, b), fminf(a, b)); }
+
 __device__ __forceinline__ df two_prod(float a, float b) {
     float p = __fmul_rn(a, b);
     return {p, __fmaf_rn(a, b, -p)};
@@ -65,9 +73,9 @@ __device__ __forceinline__ df block_terms(float px, float py, float pz, const fl
         sx.l = __fmaf_rn(2.f * dx.h, dx.l, sx.l);
         sy.l = __fmaf_rn(2.f * dy.h, dy.l, sy.l);
         sz.l = __fmaf_rn(2.f * dz.h, dz.l, sz.l);
-        df s = two_sum(sx.h, sy.h);
+        df s = two_sum_pos(sx.h, sy.h);
         s.l = __fadd_rn(s.l, __fadd_rn(sx.l, sy.l));
-        df r2 = two_sum(s.h, sz.h);
+        df r2 = two_sum_pos(s.h, sz.h);
         r2.l = __fadd_rn(r2.l, __fadd_rn(s.l, sz.l));
         r2 = two_sum(r2.h, r2.l);
         const bool in = (r2.h < k.Rh) || (r2.h == k.Rh && r2.l < k.Rl);
@@ -88,12 +96,12 @@ __device__ __forceinline__ df block_terms(float px, float py, float pz, const fl
         g2.l = __fmaf_rn(2.f * g.h, g.l, g2.l);
         float rest = __fmul_rn(__fmul_rn(g2.h, g.h),
                                __fmaf_rn(g.h, __fmaf_rn(g.h, -1.f / 120.f, 1.f / 24.f), -1.f / 6.f));
-        df D = two_sum(-g.h, 0.5f * g2.h);
+        df D = fast_two_sum(-g.h, 0.5f * g2.h);   // |g| < 2, so |g| >= g^2 / 2
         D.l = __fadd_rn(D.l, __fadd_rn(__fmaf_rn(0.5f, g2.l, -g.l), rest));
         // E = T_j (1 + D)
         const float2 T = tab[m & 63];
         df p = two_prod(T.x, D.h);
-        df E = two_sum(T.x, p.h);
+        df E = fast_two_sum(T.x, p.h);            // T in [1/2, 1], |p| < 0.01
         E.l = __fadd_rn(E.l, __fadd_rn(p.l, __fmaf_rn(T.x, D.l, __fmaf_rn(T.y, D.h, T.y))));
         // 2^-e
         int e = m >> 6;
