@@ -120,30 +120,36 @@ __device__ __forceinline__ df block_terms(float px, float py, float pz, const fl
 }
 
 // One segment of one problem: acc over the segment's blocks for target thread.  Warp
-// w holds the tile's targets 32w .. 32w + 31, so it skips a block whose pair-list
-// code for that quarter says no pair is within the cut-off (those terms are zero).
+// w holds the tile's targets 32w .. 32w + 31 and walks the segment on its own: it
+// skips a block whose pair-list code for that quarter says no pair is within the
+// cut-off (those terms are zero) and stages the others in its own slice of shared
+// memory (one source per lane), so warps never wait for each other.  s_p and s_w
+// hold 32 entries per warp of the CTA.
 __device__ __forceinline__ double resid_segment(const float4 *__restrict__ pos, const int2 tl, const double *__restrict__ x,
                                                 const int2 *__restrict__ blk, const int32_t *__restrict__ ent,
                                                 const int2 *__restrict__ ebi, const int4 sg, const DfConst &kc,
                                                 float4 *s_p, float2 *s_w, const float2 *s_tab, bool &valid,
                                                 int64_t &i) {
-    const int quarter_shift = 8 + 2 * (int)(threadIdx.x >> 5);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quarter_shift = 8 + 2 * warp;
+    float4 *wp = s_p + 32 * warp;
+    float2 *ww = s_w + 32 * warp;
     i = (int64_t)tl.x + threadIdx.x;
     valid = (int)threadIdx.x < tl.y;
     float4 p = valid ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     double acc = 0.0;
     for (int e = sg.y; e < sg.z; ++e) {
-        int2 bi = blk[ent[e] & 0x7fffffff];
-        __syncthreads();
-        if ((int)threadIdx.x < bi.y) {
-            s_p[threadIdx.x] = pos[bi.x + threadIdx.x];
-            double xv = x[bi.x + threadIdx.x];
-            float xh = (float)xv;
-            s_w[threadIdx.x] = make_float2(xh, (float)(xv - (double)xh));
-        }
-        __syncthreads();
         if (ebi && ((ebi[e].y >> quarter_shift) & 3) == 0) continue;
-        df a = block_terms(p.x, p.y, p.z, s_p, s_w, bi.y, kc, s_tab);
+        const int2 bi = blk[ent[e] & 0x7fffffff];
+        __syncwarp();
+        if (lane < bi.y) {
+            wp[lane] = pos[bi.x + lane];
+            const double xv = x[bi.x + lane];
+            const float xh = (float)xv;
+            ww[lane] = make_float2(xh, (float)(xv - (double)xh));
+        }
+        __syncwarp();
+        df a = block_terms(p.x, p.y, p.z, wp, ww, bi.y, kc, s_tab);
         acc += (double)a.h + (double)a.l;
     }
     return acc;
@@ -156,10 +162,11 @@ __global__ void __launch_bounds__(kT) k_resid_df(const float4 *__restrict__ pos,
                                                  int64_t n, DfConst kc,
                                                  const float *__restrict__ b, double *__restrict__ out,
                                                  double *__restrict__ part) {
-    __shared__ float4 s_p[kBlk];
-    __shared__ float2 s_w[kBlk];
+    __shared__ float4 s_p[kT];
+    __shared__ float2 s_w[kT];
     __shared__ float2 s_tab[64];
     if (threadIdx.x < 64) s_tab[threadIdx.x] = c_tab[threadIdx.x];
+    __syncthreads();
     const int4 sg = seg[blockIdx.x];
     bool valid;
     int64_t i;
@@ -193,10 +200,11 @@ __global__ void __launch_bounds__(kT) k_resid_df_batched(const PlanView *__restr
                                                          const float *__restrict__ bs, const double *__restrict__ xs,
                                                          double *__restrict__ rs, double *__restrict__ pool,
                                                          const int64_t *__restrict__ poff) {
-    __shared__ float4 s_p[kBlk];
-    __shared__ float2 s_w[kBlk];
+    __shared__ float4 s_p[kT];
+    __shared__ float2 s_w[kT];
     __shared__ float2 s_tab[64];
     if (threadIdx.x < 64) s_tab[threadIdx.x] = c_tab[threadIdx.x];
+    __syncthreads();
     const int2 it = items[blockIdx.x];
     const PlanView &v = views[it.x];
     const int4 sg = v.seg[it.y];
