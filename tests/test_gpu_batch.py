@@ -66,6 +66,26 @@ def test_batched_product_matches_plans_and_oracle(batch, clouds):
         o += n
 
 
+@pytest.mark.parametrize("products", [("simt",) * 7, ("tc", "simt") * 3 + ("tc",)])
+def test_batched_cuda_core_path(rbf, ctx, batch, clouds, products):
+    """A batch whose plans are not all tensor-core plans takes the persistent CUDA-core
+    product: the same operator as the tensor-core batch and the oracle."""
+    plans = [rbf.Plan(ctx, torch.from_numpy(C).cuda(), sigma=s, k=6.0, product=pr)
+             for (C, _, s), pr in zip(clouds, products)]
+    other = rbf.Batch(ctx, plans)
+    z = np.random.default_rng(1).standard_normal(batch.n).astype(np.float32)
+    zt = torch.from_numpy(z).cuda()
+    y_tc = batch.matvec(zt).cpu().numpy().astype(np.float64)
+    y = other.matvec(zt).cpu().numpy().astype(np.float64)
+    assert rel2(y, y_tc) <= 3e-6
+    o = 0
+    for C, _, s in clouds:
+        n = len(C)
+        y64, _ = oracle.kernel_rows(C[:, :3].astype(np.float64), z[o:o + n].astype(np.float64), s, 6.0)
+        assert rel2(y[o:o + n], y64) <= 1e-5
+        o += n
+
+
 def test_batched_solve_matches_single_solves(batch, clouds):
     b = np.concatenate([c[1] for c in clouds])
     x, reps, st = batch.solve(torch.from_numpy(b).cuda(), m=15, max_it=30)
