@@ -105,3 +105,24 @@ def test_invalid_inputs(rbf, ctx):
         rbf.density_measures(ctx, f4(bad))
     with pytest.raises(rbf.RbfError):
         rbf.density_measures(ctx, f4(np.random.default_rng(0).uniform(0, 1, (10, 3))), f4(bad))
+
+
+def test_benchmark_size_sampled(rbf, ctx):
+    """The benchmark's cloud (the 1,000,000-point torus, noise 1e-3, seed 0): sampled
+    nearest-neighbour distances by brute force over all points, the separation and
+    h_max against the extremes of the GPU's own per-point distances, and the fill
+    distance over a 2,000-probe subset of the noise-free torus against the oracle."""
+    X = synth.torus(1_000_000, noise=1e-3, seed=0).points.astype(np.float32).astype(np.float64)
+    Pr = synth.torus(1_000_000, noise=0.0, seed=1).points.astype(np.float32).astype(np.float64)
+    d, nn = rbf.density_measures(ctx, f4(X), f4(Pr), return_nn=True)
+    nn = nn.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(3)
+    rows = np.concatenate([rng.choice(len(X), 300, replace=False), [int(nn.argmin()), int(nn.argmax())]])
+    o = oracle.nn_distances(X, rows)
+    assert np.abs(nn[rows] - o).max() <= 2e-6 * o.max() + 1e-9
+    assert d["q"] == pytest.approx(0.5 * nn.min(), rel=1e-7) and d["h_max"] == pytest.approx(nn.max(), rel=1e-7)
+    assert d["mean_nn"] == pytest.approx(nn.mean(), rel=1e-6)
+    sub = Pr[rng.choice(len(Pr), 2000, replace=False)]
+    ds = rbf.density_measures(ctx, f4(X), f4(sub))
+    assert ds["fill"] == pytest.approx(oracle.fill_distance(X, sub), rel=2e-6)
+    assert d["fill"] >= ds["fill"]
