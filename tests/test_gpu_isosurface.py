@@ -116,3 +116,38 @@ def test_band_matches_oracle(rbf, ctx):
     To, counts = oracle.isosurface(f.astype(np.float64), (-1.0,) * 3, (1.0,) * 3, points=P, band=band)
     assert len(T) == len(To) and 0 < len(To) < len(oracle.isosurface(f.astype(np.float64), (-1.0,) * 3, (1.0,) * 3)[0])
     assert np.abs(T - To).max() <= 2e-6
+
+
+def test_benchmark_size_field(rbf, ctx):
+    """The benchmark's level set: the 256^3 grid field of the 3,000,000-centre torus (20
+    RAS-FGMRES iterations).  A 24^3 crop through the surface gives the oracle's triangles
+    exactly; over the whole grid, with the band of 0.03, every sampled vertex lies within
+    the band plus half a cell diagonal of a cloud point."""
+    from scipy.spatial import cKDTree
+    cl = synth.torus(1_000_000, noise=1e-3, seed=0)
+    C, b, _ = rbf.build_centers(ctx, torch.from_numpy(cl.points).cuda(), torch.from_numpy(cl.normals).cuda(),
+                                delta=0.01)
+    plan = rbf.Plan(ctx, C, sigma=0.02, k=6.0)
+    x, _ = plan.solve(b, m=20, max_it=20, fixed_iterations=True, precond="schwarz", core=96, block=128, shift=1.0,
+                      escalate=True)
+    pad = 0.01 + 3 * 0.02
+    lo = tuple(cl.points.min(0).astype(np.float64) - pad)
+    hi = tuple(cl.points.max(0).astype(np.float64) + pad)
+    G = 256
+    f = plan.eval_grid(x, lo, hi, (G, G, G))
+    step = (np.asarray(hi) - np.asarray(lo)) / (G - 1)
+    # crop around the node nearest to a surface point on the outer equator, (1.35, 0, 0)
+    c = np.round((np.array([1.35, 0.0, 0.0]) - np.asarray(lo)) / step).astype(int)
+    i0 = np.clip(c - 12, 0, G - 24)
+    fc = f[i0[2]:i0[2] + 24, i0[1]:i0[1] + 24, i0[0]:i0[0] + 24].cpu().numpy().copy()
+    clo = tuple(float(np.float32(lo[d])) + i0[d] * float(np.float32(step[d])) for d in range(3))
+    chi = tuple(clo[d] + 23 * float(np.float32(step[d])) for d in range(3))
+    T, To = _compare(rbf, ctx, fc, clo, chi)
+    assert len(T) > 500
+    P = np.zeros((len(cl.points), 4), dtype=np.float32)
+    P[:, :3] = cl.points
+    Tb = rbf.isosurface(ctx, f, lo, hi, 0.0, torch.from_numpy(P).cuda(), 0.03).cpu().numpy().astype(np.float64)
+    assert len(Tb) > 1_000_000
+    V = Tb.reshape(-1, 3)[np.random.default_rng(0).choice(len(Tb) * 3, 20000, replace=False)]
+    dist, _ = cKDTree(cl.points.astype(np.float64)).query(V)
+    assert dist.max() <= 0.03 + 0.5 * np.linalg.norm(step) + 1e-6
