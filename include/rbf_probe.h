@@ -35,6 +35,15 @@ typedef struct {
  * its waits are bounded at 100 ms). */
 rbf_status rbf_probe_peaks(int device, rbf_probe_result *r);
 
+/* Failure-detection check of the bounded waits (no fault involved): one thread
+ * waits, with the wait the tensor-core kernels use, for an mbarrier phase that
+ * nothing completes; after limit_ns (clamped to [1 us, 1 s]) the wait gives up,
+ * raises the context's device error word and the kernel returns.  The call then
+ * synchronises `stream` and reports what a product launch that gave up would:
+ * RBF_ERR_TIMEOUT, with rbf_last_error set and the word cleared; the context
+ * stays usable.  Returns RBF_OK only if the phase completed (it cannot). */
+rbf_status rbf_probe_wait_expiry(rbf_ctx *ctx, uint64_t limit_ns, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

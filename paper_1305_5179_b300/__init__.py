@@ -31,7 +31,7 @@ RESIDUAL = {"df": 0, "f64": 1}
 
 # every entry point declared in include/rbf.h
 EXPORTS = (
-    "rbf_version", "rbf_launch_count", "rbf_probe_peaks", "rbf_status_string", "rbf_ctx_create", "rbf_ctx_destroy", "rbf_last_error",
+    "rbf_version", "rbf_launch_count", "rbf_probe_peaks", "rbf_probe_wait_expiry", "rbf_status_string", "rbf_ctx_create", "rbf_ctx_destroy", "rbf_last_error",
     "rbf_build_centers", "rbf_plan_create", "rbf_plan_destroy", "rbf_plan_get_info", "rbf_plan_export_binning",
     "rbf_matvec", "rbf_count_pairs", "rbf_count_candidate_pairs", "rbf_residual",
     "rbf_plan_assemble", "rbf_plan_release_csr", "rbf_plan_export_csr", "rbf_spmv",
@@ -183,6 +183,7 @@ def lib() -> ctypes.CDLL:
         "rbf_eval_grid": ([P, P, P, I64, ctypes.POINTER(PlanParams), ctypes.POINTER(Grid), P, P], I),
         "rbf_plan_assemble": ([P, I64, ctypes.POINTER(I64), ctypes.POINTER(I64), P], I),
         "rbf_count_candidate_pairs": ([P, ctypes.POINTER(I64), P], I),
+        "rbf_probe_wait_expiry": ([P, ctypes.c_uint64, P], I),
         "rbf_plan_release_csr": ([P], I),
         "rbf_plan_export_csr": ([P, P, P, P, P], I),
         "rbf_spmv": ([P, P, P, P], I),

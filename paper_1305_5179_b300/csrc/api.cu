@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 
+#include "../../include/rbf_probe.h"
 #include "centers.cuh"
 #include "plan.cuh"
 
@@ -234,6 +235,16 @@ rbf_status rbf_count_pairs(rbf_plan *P, int64_t *count, void *stream) {
     return guarded(P->ctx, [&]() {
         RBF_CHECK(count, RBF_ERR_INVALID, "null count");
         *count = count_pairs(P, S(stream));
+        return RBF_OK;
+    });
+}
+
+rbf_status rbf_probe_wait_expiry(rbf_ctx *ctx, uint64_t limit_ns, void *stream) {
+    return guarded(ctx, [&]() {
+        cudaStream_t s = S(stream);
+        launch_expiring_wait(ctx_error_word(ctx), limit_ns, s);
+        RBF_CUDA(cudaStreamSynchronize(s));
+        ctx_check_device_error(ctx);
         return RBF_OK;
     });
 }

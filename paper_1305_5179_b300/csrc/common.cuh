@@ -25,6 +25,8 @@ struct rbf_ctx {
 // turns a raised word into RBF_ERR_TIMEOUT (clearing it).
 unsigned *ctx_error_word(rbf_ctx *ctx);
 void ctx_check_device_error(rbf_ctx *ctx);
+// probe.cu: one bounded wait that expires and raises *err (failure-detection check).
+void launch_expiring_wait(unsigned *err, uint64_t limit_ns, cudaStream_t s);
 
 // ------------------------------------------------------------------ errors
 struct RbfError {

@@ -160,6 +160,19 @@ double run_probe(int num_sms, double ops_per_iter_per_thread, double *mhz, cudaS
     return per_s / ((double)num_sms * f * 1e6);   // per SM per clock
 }
 
+// A wait that nothing completes (see rbf_probe_wait_expiry).
+__global__ void k_expiring_wait(unsigned *err, unsigned long long limit_ns) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        tc5::mbar_init(&bar, 1);
+        tc5::mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !tc5::mbar_wait(&bar, 0u, &abort_flag, limit_ns)) atomicOr(err, 1u);
+}
+
 }  // namespace
 
 extern "C" rbf_status rbf_probe_peaks(int device, rbf_probe_result *r) {
@@ -180,4 +193,10 @@ extern "C" rbf_status rbf_probe_peaks(int device, rbf_probe_result *r) {
     } catch (const RbfError &e) {
         return e.status;
     }
+}
+
+void launch_expiring_wait(unsigned *err, uint64_t limit_ns, cudaStream_t s) {
+    const uint64_t lim = limit_ns < 1000ull ? 1000ull : (limit_ns > 1000000000ull ? 1000000000ull : limit_ns);
+    k_expiring_wait<<<1, 32, 0, s>>>(err, (unsigned long long)lim);
+    RBF_LAUNCHED();
 }
