@@ -3,27 +3,35 @@
 // B300's FP64 units run at a small fraction of its FP32 rate, so the residual
 // product (one per restart of the refinement loop) is evaluated in
 // double-float arithmetic: every quantity is an unevaluated sum hi + lo of two
-// float32, combined with the error-free transformations TwoSum (Knuth) and
-// TwoProd (via FMA).  Per pair:
+// float32, combined with the error-free transformations TwoSum (Knuth),
+// Fast2Sum (Dekker; where the larger operand is known) and TwoProd (via FMA).
+// Per pair:
 //   d = p - q exactly (TwoSum per axis; p, q are float32),
-//   r2 = |d|^2 to ~2^-47 relative,
+//   r2 = |d|^2 to ~2^-46 relative (left unnormalised),
 //   cut-off  r2 < (k sigma)^2 against a double-float constant,
 //   t = r2 log2(e)/(2 sigma^2),
 //   2^-t by the table-driven method of P. T. P. Tang (ACM TOMS 15(2), 1989):
-//     t = e + j/64 + f with |f| <= 1/128, 2^-t = 2^-e 2^(-j/64) exp(-f ln 2),
-//     2^(-j/64) from a 64-entry double-float table built on the host,
-//     exp(-g), |g| <= ln2/128, by its Taylor series to g^5 (truncation < 4e-17),
+//     t = e + j/1024 + f with |f| <= 1/2048, 2^-t = 2^-e 2^(-j/1024) exp(-f ln 2),
+//     2^(-j/1024) from a 1024-entry double-float table built on the host,
+//     exp(-g) - 1, |g| <= ln2/2048 + t 2^-23, as -g (double-float) plus
+//     g^2/2 - g^3/6 in float32 of the rounded g (the dropped g^4/24 is below 1e-15;
+//     the float32 rounding of g^2/2 below 4e-15),
 //   product with x_j (double-float split of the float64 weight) and
 //   accumulation of each block's <= 32 terms in double-float, added to a float64
 //   accumulator once per block.
-// Per-term relative error is of order 1e-14.
+// Per-term relative error is of order 1e-14.  Pairs beyond the cut-off get a zero
+// scale 2^-e, so their terms are exactly zero; every intermediate stays finite for
+// t below 1e20.
 #include <cmath>
+#include <vector>
 
 #include "batch.cuh"
 
 namespace {
 
 constexpr int kT = kChunk;   // one thread per target
+constexpr int kTabBits = 10;
+constexpr int kTab = 1 << kTabBits;
 
 struct df {
     float h, l;
@@ -55,7 +63,12 @@ struct DfConst {
     float Lh, Ll;     // ln 2
 };
 
-__constant__ float2 c_tab[64];   // 2^(-j/64) as (hi, lo)
+__device__ float2 d_tab[kTab];   // 2^(-j/1024) as (hi, lo)
+
+// copies the table into shared memory; the caller synchronises the CTA afterwards
+__device__ __forceinline__ void load_table(float2 *s_tab) {
+    for (int j = threadIdx.x; j < kTab; j += blockDim.x) s_tab[j] = d_tab[j];
+}
 
 // sum over one staged block of w_j 2^(-t_ij) for the target (px, py, pz); called by
 // every lane of a warp with the same cnt
@@ -67,52 +80,52 @@ __device__ __forceinline__ df block_terms(float px, float py, float pz, const fl
     for (int j = 0; j < cnt; ++j) {
         const float4 q = sp[j];
         const float2 w = sw[j];
-        df dx = two_sum(px, -q.x), dy = two_sum(py, -q.y), dz = two_sum(pz, -q.z);
-        // squares: dh^2 + 2 dh dl (dl^2 < 2^-48 dh^2 is dropped)
-        df sx = two_prod(dx.h, dx.h), sy = two_prod(dy.h, dy.h), sz = two_prod(dz.h, dz.h);
-        sx.l = __fmaf_rn(2.f * dx.h, dx.l, sx.l);
-        sy.l = __fmaf_rn(2.f * dy.h, dy.l, sy.l);
-        sz.l = __fmaf_rn(2.f * dz.h, dz.l, sz.l);
-        df s = two_sum_pos(sx.h, sy.h);
-        s.l = __fadd_rn(s.l, __fadd_rn(sx.l, sy.l));
+        const df dx = two_sum(px, -q.x), dy = two_sum(py, -q.y), dz = two_sum(pz, -q.z);
+        // |d|^2 = sum dh^2 (exact products) + 2 sum dh dl (dl^2 < 2^-48 dh^2 is dropped)
+        const df sx = two_prod(dx.h, dx.h), sy = two_prod(dy.h, dy.h), sz = two_prod(dz.h, dz.h);
+        const float cr = __fmaf_rn(dx.h, dx.l, __fmaf_rn(dy.h, dy.l, __fmul_rn(dz.h, dz.l)));
+        const df s = two_sum_pos(sx.h, sy.h);
         df r2 = two_sum_pos(s.h, sz.h);
-        r2.l = __fadd_rn(r2.l, __fadd_rn(s.l, sz.l));
-        r2 = two_sum(r2.h, r2.l);
-        const bool in = (r2.h < k.Rh) || (r2.h == k.Rh && r2.l < k.Rl);
+        r2.l = __fadd_rn(__fadd_rn(r2.l, __fadd_rn(s.l, __fadd_rn(sx.l, sy.l))), __fmaf_rn(2.f, cr, sz.l));
+        // r2 < R: (r2.h - Rh) is exact near the radius (Sterbenz) and decides the sign elsewhere
+        const bool in = __fadd_rn(__fsub_rn(r2.h, k.Rh), __fsub_rn(r2.l, k.Rl)) < 0.f;
         // a source beyond the cut-off for every target of the warp adds nothing: skip its
         // exponential (the loop runs over the same sources on every lane, so the vote is uniform)
         if (!__any_sync(0xffffffffu, in)) continue;
         // t = r2 * C
         df t = two_prod(r2.h, k.Ch);
         t.l = __fadd_rn(t.l, __fmaf_rn(r2.h, k.Cl, __fmul_rn(r2.l, k.Ch)));
-        float mf = rintf(__fmul_rn(t.h, 64.f));
-        int m = (int)mf;
-        float fh = __fsub_rn(t.h, __fmul_rn(mf, 0.015625f));        // exact: |fh| <= 1/128
+        // m = round(1024 t) by the 1.5 x 2^23 shift (exact below 2^22; t is clamped far above
+        // where 2^-t underflows), then t = m / 1024 + fh exactly
+        const float th = fminf(t.h, 2048.f);
+        const float y = __fmaf_rn(th, (float)kTab, 12582912.f);
+        const float mf = __fsub_rn(y, 12582912.f);
+        const int m = __float_as_int(y) - 0x4B400000;
+        const float fh = __fmaf_rn(mf, -1.f / kTab, th);
         // g = (fh + t.l) ln 2
         df g = two_prod(fh, Lh);
         g.l = __fadd_rn(g.l, __fmaf_rn(fh, Ll, __fmul_rn(t.l, Lh)));
-        // exp(-g) - 1 = -g + g^2/2 - g^3/6 + g^4/24 - g^5/120
-        df g2 = two_prod(g.h, g.h);
-        g2.l = __fmaf_rn(2.f * g.h, g.l, g2.l);
-        float rest = __fmul_rn(__fmul_rn(g2.h, g.h),
-                               __fmaf_rn(g.h, __fmaf_rn(g.h, -1.f / 120.f, 1.f / 24.f), -1.f / 6.f));
-        df D = fast_two_sum(-g.h, 0.5f * g2.h);   // |g| < 2, so |g| >= g^2 / 2
-        D.l = __fadd_rn(D.l, __fadd_rn(__fmaf_rn(0.5f, g2.l, -g.l), rest));
+        // exp(-g) - 1 = -g + g^2/2 - g^3/6 + ...; g.l holds t.l ln 2 and is not below ulp(g.h),
+        // so the float32 terms take the rounded sum gs = g.h + g.l
+        const float gs = __fadd_rn(g.h, g.l);
+        const float g2 = __fmul_rn(gs, gs);
+        const float rest = __fmul_rn(g2, __fmaf_rn(gs, -1.f / 6.f, 0.5f));
+        df D = fast_two_sum(-g.h, rest);          // |g| >= g^2 / 2
+        D.l = __fsub_rn(D.l, g.l);
         // E = T_j (1 + D)
-        const float2 T = tab[m & 63];
-        df p = two_prod(T.x, D.h);
-        df E = fast_two_sum(T.x, p.h);            // T in [1/2, 1], |p| < 0.01
+        const float2 T = tab[m & (kTab - 1)];
+        const df p = two_prod(T.x, D.h);
+        df E = fast_two_sum(T.x, p.h);            // T in [1/2, 1], |p| < 3e-4
         E.l = __fadd_rn(E.l, __fadd_rn(p.l, __fmaf_rn(T.x, D.l, __fmaf_rn(T.y, D.h, T.y))));
-        // 2^-e
-        int e = m >> 6;
-        float sc = e <= 125 ? __int_as_float((127 - e) << 23) : 0.f;
+        // 2^-e (zero from e = 127 on, and for a pair beyond the cut-off)
+        const int e = min(m >> kTabBits, 127);
+        const float sc = in ? __int_as_float((127 - e) << 23) : 0.f;
         E.h = __fmul_rn(E.h, sc);
         E.l = __fmul_rn(E.l, sc);
         // term = E * w, accumulated in double-float
         df P = two_prod(E.h, w.x);
         P.l = __fadd_rn(P.l, __fmaf_rn(E.h, w.y, __fmul_rn(E.l, w.x)));
-        if (!in) P.h = P.l = 0.f;
-        df a2 = two_sum(acc.h, P.h);
+        const df a2 = two_sum(acc.h, P.h);
         acc.h = a2.h;
         acc.l = __fadd_rn(acc.l, __fadd_rn(a2.l, P.l));
     }
@@ -164,8 +177,8 @@ __global__ void __launch_bounds__(kT) k_resid_df(const float4 *__restrict__ pos,
                                                  double *__restrict__ part) {
     __shared__ float4 s_p[kT];
     __shared__ float2 s_w[kT];
-    __shared__ float2 s_tab[64];
-    if (threadIdx.x < 64) s_tab[threadIdx.x] = c_tab[threadIdx.x];
+    __shared__ float2 s_tab[kTab];
+    load_table(s_tab);
     __syncthreads();
     const int4 sg = seg[blockIdx.x];
     bool valid;
@@ -202,8 +215,8 @@ __global__ void __launch_bounds__(kT) k_resid_df_batched(const PlanView *__restr
                                                          const int64_t *__restrict__ poff) {
     __shared__ float4 s_p[kT];
     __shared__ float2 s_w[kT];
-    __shared__ float2 s_tab[64];
-    if (threadIdx.x < 64) s_tab[threadIdx.x] = c_tab[threadIdx.x];
+    __shared__ float2 s_tab[kTab];
+    load_table(s_tab);
     __syncthreads();
     const int2 it = items[blockIdx.x];
     const PlanView &v = views[it.x];
@@ -250,9 +263,9 @@ bool g_tab_ready[64] = {false};
 
 void upload_table(int device, cudaStream_t s) {
     if (device >= 0 && device < 64 && g_tab_ready[device]) return;
-    float2 tab[64];
-    for (int j = 0; j < 64; ++j) split(std::exp2(-j / 64.0), tab[j].x, tab[j].y);
-    RBF_CUDA(cudaMemcpyToSymbolAsync(c_tab, tab, sizeof(tab), 0, cudaMemcpyHostToDevice, s));
+    std::vector<float2> tab(kTab);
+    for (int j = 0; j < kTab; ++j) split(std::exp2(-j / (double)kTab), tab[j].x, tab[j].y);
+    RBF_CUDA(cudaMemcpyToSymbolAsync(d_tab, tab.data(), kTab * sizeof(float2), 0, cudaMemcpyHostToDevice, s));
     RBF_CUDA(cudaStreamSynchronize(s));
     if (device >= 0 && device < 64) g_tab_ready[device] = true;
 }
