@@ -351,6 +351,20 @@ def run_ours(args, wl):
                           f"one MUFU.EX2 per pair",
             "probe": probe}
 
+    # float64 Gram-Schmidt vector work of FGMRES: CGS2 = two multi-dots and two multi-axpys
+    # over the j + 1 basis vectors at Arnoldi step j, one float64 FMA per 8-byte element streamed
+    its = [r["iterations"] for r in reps]
+    nv_sum = sum(sum(j % wl["m"] + 1 for j in range(it)) for it in its) / len(its)
+    dfma = 4.0 * nv_sum * n
+    vec_ms = statistics.mean(r["ms_solve"] - r["ms_matvec"] - r["ms_residual"] - r["ms_precond"] for r in reps)
+    dfma_peak = probe["num_sms"] * f_mhz * 1e6 * probe["dfma_per_clk_sm"]
+    vectors = {"dfma_per_step": dfma, "ms": vec_ms, "dfma_per_s": dfma / (vec_ms * 1e-3),
+               "peak_dfma_per_s": dfma_peak, "frac": dfma / (vec_ms * 1e-3) / dfma_peak,
+               "bytes_per_step": 8.0 * dfma,
+               "note": "solve time less products, residuals and preconditioner (also holds the small "
+                       "kernels and the host's Givens step); bound by the float64 FMA rate "
+                       "(rbf_probe_peaks), which streams 8 bytes per FMA below the copy bandwidth"}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle as orc
@@ -390,6 +404,7 @@ def run_ours(args, wl):
                       "ms_residual_f64": rep["ms_residual"], "ms_precond_total": rep["ms_precond"],
                       "failed_blocks": rep["precond_failed_blocks"]},
             "matvec": {"ms_per_launch": mv_ms, "pairs_per_s": achieved},
+            "fgmres_vectors": vectors,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": world * pairs_step / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
@@ -469,6 +484,20 @@ def run_assembled(args, wl):
     # z read once, y written once (binned order; the permutations add 2 x 12 n bytes)
     alg = stored * 8 + (n + 1) * 8 + n * 8
     achieved = alg / (ms_spmv * 1e-3) / 1e9
+    # float64 Gram-Schmidt vector work of FGMRES: CGS2 = two multi-dots and two multi-axpys
+    # over the j + 1 basis vectors at Arnoldi step j, one float64 FMA per 8-byte element streamed
+    its = [r["iterations"] for r in reps]
+    nv_sum = sum(sum(j % wl["m"] + 1 for j in range(it)) for it in its) / len(its)
+    dfma = 4.0 * nv_sum * n
+    vec_ms = statistics.mean(r["ms_solve"] - r["ms_matvec"] - r["ms_residual"] - r["ms_precond"] for r in reps)
+    dfma_peak = probe["num_sms"] * f_mhz * 1e6 * probe["dfma_per_clk_sm"]
+    vectors = {"dfma_per_step": dfma, "ms": vec_ms, "dfma_per_s": dfma / (vec_ms * 1e-3),
+               "peak_dfma_per_s": dfma_peak, "frac": dfma / (vec_ms * 1e-3) / dfma_peak,
+               "bytes_per_step": 8.0 * dfma,
+               "note": "solve time less products, residuals and preconditioner (also holds the small "
+                       "kernels and the host's Givens step); bound by the float64 FMA rate "
+                       "(rbf_probe_peaks), which streams 8 bytes per FMA below the copy bandwidth"}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle as orc

@@ -5,7 +5,9 @@
  * ex2.approx.f32 (the special-function unit), scalar FP32 FMA and packed
  * f32x2 FMA, each as operations per SM per clock, with the SM clock derived
  * from the cycle counter and the global nanosecond timer of the probe run.
- * These are the denominators of the product kernels' roofline.  It also times,
+ * These are the denominators of the product kernels' roofline.  The float64
+ * FMA rate bounds the float64 Gram-Schmidt vector work of FGMRES (one FMA per
+ * 8-byte element it streams).  It also times,
  * on one thread per SM, the issue-to-completion latency of the tensor-core step
  * of the product (two dependent tcgen05.mma of kind::tf32, M = 128, N = 32,
  * K = 8, then tcgen05.commit to an mbarrier), alone and four in a row.
@@ -27,9 +29,10 @@ typedef struct {
     double ffma2_lanes_per_clk_sm;  /* packed f32x2 FMA, FP32 lanes per SM per clock */
     double mma_commit_cycles;       /* SM cycles from issuing one MMA pair + commit to the mbarrier phase */
     double mma_commit4_cycles;      /* the same for four pairs (each with its commit) issued back to back */
+    double dfma_per_clk_sm;         /* float64 FMA per SM per clock */
 } rbf_probe_result;
 
-/* Runs three short kernels (about 10 ms each) and the latency kernel (under 1 ms)
+/* Runs four short kernels (about 10 ms each) and the latency kernel (under 1 ms)
  * on `device` (default stream) and fills *r.  Errors: RBF_ERR_INVALID (null r),
  * RBF_ERR_CUDA, RBF_ERR_TIMEOUT (an mbarrier wait of the latency kernel expired;
  * its waits are bounded at 100 ms). */

@@ -109,7 +109,8 @@ class Report(ctypes.Structure):
 class ProbeResult(ctypes.Structure):
     _fields_ = [("num_sms", ctypes.c_int), ("sm_mhz", ctypes.c_double), ("ex2_per_clk_sm", ctypes.c_double),
                 ("ffma_per_clk_sm", ctypes.c_double), ("ffma2_lanes_per_clk_sm", ctypes.c_double),
-                ("mma_commit_cycles", ctypes.c_double), ("mma_commit4_cycles", ctypes.c_double)]
+                ("mma_commit_cycles", ctypes.c_double), ("mma_commit4_cycles", ctypes.c_double),
+                ("dfma_per_clk_sm", ctypes.c_double)]
 
 
 class Density(ctypes.Structure):

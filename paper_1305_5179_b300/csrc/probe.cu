@@ -1,6 +1,7 @@
-// Throughput probes for the roofline of the product kernels: MUFU.EX2 and
-// FP32 FMA (scalar and packed f32x2) per SM per clock, with the SM clock read
-// from the cycle counter against the global nanosecond timer during the run.
+// Throughput probes for the rooflines: MUFU.EX2 and FP32 FMA (scalar and packed
+// f32x2) per SM per clock for the product kernels, FP64 FMA per SM per clock for
+// the float64 Arnoldi vector work, with the SM clock read from the cycle counter
+// against the global nanosecond timer during the run.
 #include "common.cuh"
 #include "tcgen05.cuh"
 #include "../../include/rbf_probe.h"
@@ -16,7 +17,8 @@ __device__ __forceinline__ unsigned long long gtimer() {
     return t;
 }
 
-// mode 0: ex2.approx chains; 1: scalar FFMA chains; 2: packed f32x2 FMA chains
+// mode 0: ex2.approx chains; 1: scalar FFMA chains; 2: packed f32x2 FMA chains;
+// 3: float64 FMA chains
 template <int kMode>
 __global__ void __launch_bounds__(kThreads) k_probe(int iters, float seed, float *out, unsigned long long *clk) {
     unsigned long long c0 = clock64(), t0 = gtimer();
@@ -33,6 +35,16 @@ __global__ void __launch_bounds__(kThreads) k_probe(int iters, float seed, float
 #pragma unroll
             for (int c = 0; c < kChains; ++c) v[c] = fmaf(v[c], 0.999999f, 1e-7f);
         }
+    } else if (kMode == 3) {
+        double d[kChains];
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) d[c] = (double)v[c];
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) d[c] = fma(d[c], 0.999999, 1e-7);
+        }
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) v[c] = (float)d[c];
     } else {
         unsigned long long p[kChains / 2], a, b;
         asm("mov.b64 %0, {%1,%2};" : "=l"(a) : "f"(0.999999f), "f"(0.999999f));
@@ -132,7 +144,7 @@ double run_probe_mma(int num_sms, int stages, cudaStream_t s) {
 
 template <int kMode>
 double run_probe(int num_sms, double ops_per_iter_per_thread, double *mhz, cudaStream_t s) {
-    const int blocks = num_sms * 8, iters = 20000;
+    const int blocks = num_sms * 8, iters = kMode == 3 ? 1000 : 20000;   // float64 runs far slower
     DevBuf<float> out;
     DevBuf<unsigned long long> clk;
     out.alloc(1, s);
@@ -187,6 +199,8 @@ extern "C" rbf_status rbf_probe_peaks(int device, rbf_probe_result *r) {
         r->ffma_per_clk_sm = run_probe<1>(sms, kChains, &m1, 0);
         r->ffma2_lanes_per_clk_sm = run_probe<2>(sms, kChains, &m2, 0);
         r->sm_mhz = (m0 + m1 + m2) / 3.0;
+        double m3;
+        r->dfma_per_clk_sm = run_probe<3>(sms, kChains, &m3, 0);
         r->mma_commit_cycles = run_probe_mma(sms, 1, 0);
         r->mma_commit4_cycles = run_probe_mma(sms, 4, 0);
         return RBF_OK;
