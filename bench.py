@@ -210,7 +210,7 @@ def oracle_rate(C64, wl, nrows, seed=0):
     """Pair evaluations per second of the FP64 oracle on `nrows` sampled rows."""
     import numpy as np
     import oracle
-    rows = np.random.default_rng(seed).choice(len(C64), nrows, replace=False)
+    rows = np.random.default_rng(seed).choice(len(C64), min(nrows, len(C64)), replace=False)
     z = np.random.default_rng(seed + 1).standard_normal(len(C64))
     t0 = time.perf_counter()
     _, cnt = oracle.kernel_rows(C64, z, float(np.float32(wl["sigma"])), float(np.float32(wl["k"])), rows)
@@ -227,7 +227,7 @@ def run_reference(args, wl):
     cl = make_cloud(wl)
     C64, _ = oracle.build_centers(cl.points, cl.normals, wl["delta"])
     C64 = C64.astype(np.float32).astype(np.float64)
-    nrows = args.ref_rows
+    nrows = min(args.ref_rows, len(C64))
     for _ in range(args.warmup):
         oracle_rate(C64, wl, max(100, nrows // 10))
     tot_pairs, tot_t = 0, 0.0
@@ -368,7 +368,7 @@ def run_ours(args, wl):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle as orc
-        Cc, _ = orc.build_centers(cl.points, cl.normals, wl["delta"])
+        Cc, bc = orc.build_centers(cl.points, cl.normals, wl["delta"])
         Cc = Cc.astype(np.float32).astype(np.float64)
         rate, cnt, dt = oracle_rate(Cc, wl, args.cpu_rows)
         cores = orc.num_threads()
@@ -376,11 +376,18 @@ def run_ours(args, wl):
         rate1, cnt1, dt1 = oracle_rate(Cc, wl, max(200, args.cpu_rows // 10), seed=1)
         orc.set_threads(cores)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_rows} sampled rows of the {len(Cc):,}-centre truncated operator "
+               "sample": f"{min(args.cpu_rows, len(Cc))} sampled rows of the {len(Cc):,}-centre operator "
                          f"({cnt:,} pairs, {dt:.1f} s), float64 row sums over a bucket list",
                "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
-                                 "sample": f"{max(200, args.cpu_rows // 10)} sampled rows ({cnt1:,} pairs, "
+                                 "sample": f"{min(max(200, args.cpu_rows // 10), len(Cc))} sampled rows ({cnt1:,} pairs, "
                                            f"{dt1:.1f} s)"}}
+        if wl["k"] == 0.0 and len(Cc) <= 20_000:
+            # the whole dense solve of the oracle (its own float64 Cholesky) on the same system
+            td = time.perf_counter()
+            _, res_d = orc.solve_dense(Cc, bc.astype(np.float32).astype(np.float64), float(np.float32(wl["sigma"])))
+            cpu["dense_solve"] = {"seconds": time.perf_counter() - td, "cores": cores, "n": len(Cc),
+                                  "residual": float(res_d),
+                                  "kind": "oracle: float64 Cholesky of the dense matrix, one refinement step"}
 
     if rank == 0:
         rep = reps[-1]
