@@ -78,8 +78,8 @@ WORKLOADS = {
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_product_tc launch on the
 # 3,000,000-centre torus, from one ncu capture (profiles/k_product_tc_torus_sector.md gives the
 # command); valid only while the kernel sources hash to the values it was taken with.
-PRODUCT_TRAFFIC = {"torus1m": (156.802816e6 + 9.439488e6, {
-    "paper_1305_5179_b300/csrc/product_tc.cu": "e88b711dd8bac2693725ddb8583b3f0939ec3c56801aa8cc94660514c3c1e58a",
+PRODUCT_TRAFFIC = {"torus1m": (156.98e6 + 9.09e6, {
+    "paper_1305_5179_b300/csrc/product_tc.cu": "9328d403021bb0d483177592c0f0177f86d64a8eb11dec7b8a16950a78928c77",
     "paper_1305_5179_b300/csrc/tcgen05.cuh": "b0f1821451b34e230cdc5000e9e34c3b6ce5dd95aef3f1df5a956d533ea2386e"})}
 
 # DRAM bytes of one k_spmv_csr launch per byte of its algorithmic traffic, from one ncu capture on

@@ -75,9 +75,6 @@ struct TcSmem {
 };
 static_assert(sizeof(TcSmem) <= kSmemTc, "shared memory layout");
 
-#ifndef RBF_TC_SUM
-#define RBF_TC_SUM 0
-#endif
 // Two exponentials / two cut-off masks (1.0 or 0.0) written straight into a register pair.
 __device__ __forceinline__ f2 ex2_pair(float a, float b) {
     f2 r;
@@ -316,31 +313,6 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
             float tv[32];
             tc5::tmem_ld_32x32(trow + (uint32_t)(s * kBlk), tv);
             const float4 *zz = reinterpret_cast<const float4 *>(S.z[s]);
-#if RBF_TC_SUM == 1
-            // scalar FMAs, four accumulators
-            float sa[4] = {0.f, 0.f, 0.f, 0.f};
-            if (code == 2) {
-#pragma unroll
-                for (int g = 0; g < 8; ++g) {
-                    const float4 Z = zz[g];
-                    sa[0] = fmaf(ex2_approx(tv[4 * g]), Z.x, sa[0]);
-                    sa[1] = fmaf(ex2_approx(tv[4 * g + 1]), Z.y, sa[1]);
-                    sa[2] = fmaf(ex2_approx(tv[4 * g + 2]), Z.z, sa[2]);
-                    sa[3] = fmaf(ex2_approx(tv[4 * g + 3]), Z.w, sa[3]);
-                }
-            } else {
-#pragma unroll
-                for (int g = 0; g < 8; ++g) {
-                    const float4 Z = zz[g];
-                    sa[0] = fmaf(ex2_approx(tv[4 * g]), Z.x * set_gt(tv[4 * g], thr), sa[0]);
-                    sa[1] = fmaf(ex2_approx(tv[4 * g + 1]), Z.y * set_gt(tv[4 * g + 1], thr), sa[1]);
-                    sa[2] = fmaf(ex2_approx(tv[4 * g + 2]), Z.z * set_gt(tv[4 * g + 2], thr), sa[2]);
-                    sa[3] = fmaf(ex2_approx(tv[4 * g + 3]), Z.w * set_gt(tv[4 * g + 3], thr), sa[3]);
-                }
-            }
-            acc[0] = fma2(pk(sa[0], sa[1]), pk(1.f, 1.f), acc[0]);
-            acc[1] = fma2(pk(sa[2], sa[3]), pk(1.f, 1.f), acc[1]);
-#else
             if (code == 2) {
 #pragma unroll
                 for (int g = 0; g < 8; ++g) {
@@ -361,7 +333,6 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
                     acc[2 * (g & 1) + 1] = fma2(e1, mul2(m1, pk(Z.z, Z.w)), acc[2 * (g & 1) + 1]);
                 }
             }
-#endif
             tc5::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc5::mbar_arrive(&S.empty[s]);
