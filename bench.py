@@ -78,9 +78,10 @@ WORKLOADS = {
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_product_tc launch on the
 # 3,000,000-centre torus, from one ncu capture (profiles/k_product_tc_torus_sector.md gives the
 # command); valid only while the kernel sources hash to the values it was taken with.
-PRODUCT_TRAFFIC = {"torus1m": (156.98e6 + 9.09e6, {
+PRODUCT_TRAFFIC = {"torus1m": (156.81e6 + 8.98e6, {
     "paper_1305_5179_b300/csrc/product_tc.cu": "9328d403021bb0d483177592c0f0177f86d64a8eb11dec7b8a16950a78928c77",
-    "paper_1305_5179_b300/csrc/tcgen05.cuh": "b0f1821451b34e230cdc5000e9e34c3b6ce5dd95aef3f1df5a956d533ea2386e"})}
+    "paper_1305_5179_b300/csrc/tcgen05.cuh": "b0f1821451b34e230cdc5000e9e34c3b6ce5dd95aef3f1df5a956d533ea2386e",
+    "paper_1305_5179_b300/csrc/product.cuh": "7da831b5eec7623181f7ab2ce78e05d90a3d41ff301a2883871a3679935d138c"})}
 
 # DRAM bytes of one k_spmv_csr launch per byte of its algorithmic traffic, from one ncu capture on
 # the 0.05-radian sector (23,871 centres, 514 MB of CSR; profiles/k_spmv_csr_torus_sector.md):
@@ -289,6 +290,7 @@ def run_ours(args, wl):
     pairs_mv = plan0.count_pairs()
     candidates_mv = plan0.count_candidate_pairs()
     pairs_grid = grid_pairs(plan0, wl, lo, hi, dims)
+    candidates_grid = plan0.count_grid_candidate_pairs(lo, hi, dims)
     n = plan0.n
     info = plan0.info()
     del plan0
@@ -400,6 +402,7 @@ def run_ours(args, wl):
                        "precond": f"{wl['precond']} core {wl['core']} block {wl['block']} shift {wl['shift']}",
                        "pairs_per_matvec": pairs_mv, "pairs_grid": pairs_grid, "pairs_per_step": pairs_step,
                        "candidate_pairs_per_matvec": candidates_mv, "waste_ratio": candidates_mv / pairs_mv,
+                       "candidate_pairs_grid": candidates_grid, "grid_waste_ratio": candidates_grid / pairs_grid,
                        "l2": "working set > L2 (FGMRES basis alone is "
                              f"{(wl['m'] + 1) * n * 8 / 1e9:.2f} GB)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",

@@ -388,6 +388,14 @@ rbf_status rbf_plan_eval_grid(rbf_plan *plan, const double *weights, const rbf_g
  * evaluation uses.  `count` is host memory. */
 rbf_status rbf_count_grid_pairs(rbf_plan *plan, const rbf_grid *g, int64_t *count, void *stream);
 
+/* Number of (node slot, centre) pairs the grid evaluation evaluates, counted like
+ * rbf_count_candidate_pairs over the grid's bricks (128 node slots each, cut into
+ * quarters of 32; the bricks and quarters are powers of two along each axis, chosen
+ * from the grid's spacings so that their boxes are compact; slots past the grid's
+ * edge are counted).  Divided by rbf_count_grid_pairs it is the grid evaluation's
+ * waste ratio.  `count` is host memory; synchronises `stream`. */
+rbf_status rbf_count_grid_candidate_pairs(rbf_plan *plan, const rbf_grid *g, int64_t *count, void *stream);
+
 /* One-shot form: plan from (centers, n, pp), evaluate, free. */
 rbf_status rbf_eval_grid(rbf_ctx *ctx, const float *centers, const double *weights, int64_t n,
                          const rbf_plan_params *pp, const rbf_grid *g, float *f, void *stream);

@@ -36,7 +36,8 @@ EXPORTS = (
     "rbf_matvec", "rbf_count_pairs", "rbf_count_candidate_pairs", "rbf_residual",
     "rbf_plan_assemble", "rbf_plan_release_csr", "rbf_plan_export_csr", "rbf_spmv",
     "rbf_schwarz_setup", "rbf_schwarz_apply",
-    "rbf_plan_solve", "rbf_solve", "rbf_plan_eval_grid", "rbf_count_grid_pairs", "rbf_eval_grid",
+    "rbf_plan_solve", "rbf_solve", "rbf_plan_eval_grid", "rbf_count_grid_pairs", "rbf_count_grid_candidate_pairs",
+    "rbf_eval_grid",
     "rbf_density_measures", "rbf_isosurface",
     "rbf_matvec_dense_noalloc",
     "rbf_batch_create", "rbf_batch_destroy", "rbf_batch_size", "rbf_batch_matvec", "rbf_batch_solve",
@@ -167,6 +168,7 @@ def lib() -> ctypes.CDLL:
                        ctypes.POINTER(Report), P], I),
         "rbf_plan_eval_grid": ([P, P, ctypes.POINTER(Grid), P, P], I),
         "rbf_count_grid_pairs": ([P, ctypes.POINTER(Grid), ctypes.POINTER(I64), P], I),
+        "rbf_count_grid_candidate_pairs": ([P, ctypes.POINTER(Grid), ctypes.POINTER(I64), P], I),
         "rbf_matvec_dense_noalloc": ([P, P, I64, F, P, P, P], I),
         "rbf_mlp_create": ([P, P, ctypes.POINTER(P)], I),
         "rbf_mlp_destroy": ([P], I),
@@ -509,6 +511,14 @@ class Plan:
         c = ctypes.c_int64(0)
         self.ctx.check(lib().rbf_count_grid_pairs(self._h, ctypes.byref(g), ctypes.byref(c), _stream(stream)),
                        "rbf_count_grid_pairs")
+        return int(c.value)
+
+    def count_grid_candidate_pairs(self, lo, hi, dims, stream=None) -> int:
+        """(node slot, centre) pairs the grid evaluation evaluates (its waste ratio's numerator)."""
+        g = _grid(lo, hi, dims)
+        c = ctypes.c_int64(0)
+        self.ctx.check(lib().rbf_count_grid_candidate_pairs(self._h, ctypes.byref(g), ctypes.byref(c),
+                                                            _stream(stream)), "rbf_count_grid_candidate_pairs")
         return int(c.value)
 
     def eval_grid(self, weights, lo, hi, dims, out=None, stream=None):

@@ -417,6 +417,15 @@ rbf_status rbf_count_grid_pairs(rbf_plan *P, const rbf_grid *g, int64_t *count, 
     });
 }
 
+rbf_status rbf_count_grid_candidate_pairs(rbf_plan *P, const rbf_grid *g, int64_t *count, void *stream) {
+    if (!P) return RBF_ERR_INVALID;
+    return guarded(P->ctx, [&]() {
+        RBF_CHECK(g && count, RBF_ERR_INVALID, "null pointer argument");
+        *count = count_grid_candidates(P, *g, S(stream));
+        return RBF_OK;
+    });
+}
+
 rbf_status rbf_isosurface(rbf_ctx *ctx, const float *f, const rbf_grid *g, float iso, const float *points,
                           int64_t npoints, float band, float *triangles, int64_t capacity, int64_t *ntri,
                           void *stream) {

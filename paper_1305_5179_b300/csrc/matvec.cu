@@ -237,16 +237,23 @@ void residual_binned_f64(rbf_plan *P, const float *bs, const double *xs, double 
 }
 
 // Grid evaluation shares the float32 product kernel with grid-generated targets.
-void matvec_grid_launch(rbf_plan *P, const PairList &pl, const float *ws, const rbf_grid &g, const int64_t bricks[3],
-                        float *f, cudaStream_t s) {
-    if (pl.any_split) P->partial.ensure((size_t)pl.nseg * kChunk, s);
-    MvArgs a = base_args(P, pl, ws, f, P->partial.p);
+// Grid fields of the kernel arguments: node placement, bricks and their shape.
+static void set_grid_args(MvArgs &a, const rbf_grid &g, const GridCache &gc) {
     for (int d = 0; d < 3; ++d) {
         a.glo[d] = g.lo[d];
         a.gstep[d] = g.dims[d] > 1 ? (float)(((double)g.hi[d] - (double)g.lo[d]) / (double)(g.dims[d] - 1)) : 0.f;
         a.gdim[d] = (int)g.dims[d];
-        a.bdim[d] = (int)bricks[d];
+        a.bdim[d] = (int)gc.bricks[d];
+        a.blog[d] = gc.blog[d];
+        a.qlog[d] = gc.qlog[d];
     }
+}
+
+void matvec_grid_launch(rbf_plan *P, const PairList &pl, const float *ws, const rbf_grid &g, const GridCache &gc,
+                        float *f, cudaStream_t s) {
+    if (pl.any_split) P->partial.ensure((size_t)pl.nseg * kChunk, s);
+    MvArgs a = base_args(P, pl, ws, f, P->partial.p);
+    set_grid_args(a, g, gc);
     ctx_check_device_error(P->ctx);
     if (P->kernel == RBF_KERNEL_IMQ) {
         if (pl.nseg > 0) {
@@ -357,17 +364,12 @@ __global__ void __launch_bounds__(kT64) k_count_grid_pairs(MvArgs a, double rc2,
 
 }  // namespace
 
-int64_t count_grid_pairs_launch(rbf_plan *P, const PairList &pl, const rbf_grid &g, const int64_t bricks[3],
+int64_t count_grid_pairs_launch(rbf_plan *P, const PairList &pl, const rbf_grid &g, const GridCache &gc,
                                 cudaStream_t s) {
     int64_t nodes = g.dims[0] * g.dims[1] * g.dims[2];
     if (P->k <= 0.f) return nodes * P->n;
     MvArgs a = base_args(P, pl, nullptr, nullptr, nullptr);
-    for (int d = 0; d < 3; ++d) {
-        a.glo[d] = g.lo[d];
-        a.gstep[d] = g.dims[d] > 1 ? (float)(((double)g.hi[d] - (double)g.lo[d]) / (double)(g.dims[d] - 1)) : 0.f;
-        a.gdim[d] = (int)g.dims[d];
-        a.bdim[d] = (int)bricks[d];
-    }
+    set_grid_args(a, g, gc);
     DevBuf<unsigned long long> c;
     c.alloc(1, s);
     c.zero(s);
@@ -384,13 +386,14 @@ int64_t count_grid_pairs_launch(rbf_plan *P, const PairList &pl, const rbf_grid 
 namespace {
 // Pairs the tensor-core product evaluates: per list entry, every quarter of 32 targets
 // whose code is not 0 times the block's sources.  One warp per tile.
+// tiles == nullptr: every tile has kChunk target slots (grid bricks)
 __global__ void k_count_candidates(const int32_t *__restrict__ off, const int2 *__restrict__ ebi,
                                    const int2 *__restrict__ tiles, int64_t ntiles,
                                    unsigned long long *__restrict__ cnt) {
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (t >= ntiles) return;
-    const int nt = tiles[t].y;
+    const int nt = tiles ? tiles[t].y : kChunk;
     unsigned long long c = 0;
     for (int e = off[t] + lane; e < off[t + 1]; e += 32) {
         const int w = ebi[e].y;
@@ -404,13 +407,14 @@ __global__ void k_count_candidates(const int32_t *__restrict__ off, const int2 *
 }
 }  // namespace
 
-int64_t count_candidates(rbf_plan *P, cudaStream_t s) {
+int64_t count_candidates(rbf_plan *P, cudaStream_t s) { return count_candidates_list(P->pl, P->tiles.p, s); }
+
+int64_t count_candidates_list(const PairList &pl, const int2 *tiles, cudaStream_t s) {
     DevBuf<unsigned long long> c;
     c.alloc(1, s);
     c.zero(s);
-    const PairList &pl = P->pl;
     if (pl.ntiles > 0 && pl.len > 0) {
-        k_count_candidates<<<(unsigned)ceil_div(pl.ntiles * 32, 256), 256, 0, s>>>(pl.off.p, pl.ebi.p, P->tiles.p,
+        k_count_candidates<<<(unsigned)ceil_div(pl.ntiles * 32, 256), 256, 0, s>>>(pl.off.p, pl.ebi.p, tiles,
                                                                                  pl.ntiles, c.p);
         RBF_LAUNCHED();
     }

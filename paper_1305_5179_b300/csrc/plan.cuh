@@ -38,6 +38,8 @@ struct GridCache {
     bool valid = false;
     rbf_grid g{};
     int64_t bricks[3] = {0, 0, 0};
+    int blog[3] = {3, 2, 2};     // brick of 2^blog nodes per axis (128 in all)
+    int qlog[3] = {2, 1, 2};     // its quarters of 2^qlog nodes per axis (32 in all)
     PairList pl;
 };
 
@@ -132,6 +134,8 @@ void matvec_binned(rbf_plan *P, const float *zs, float *ys, cudaStream_t s);
 int64_t count_pairs(rbf_plan *P, cudaStream_t s);
 // Pairs the tensor-core product evaluates (see rbf_count_candidate_pairs).
 int64_t count_candidates(rbf_plan *P, cudaStream_t s);
+// the same over any pair list; tiles == nullptr counts kChunk slots per tile (grid bricks)
+int64_t count_candidates_list(const PairList &pl, const int2 *tiles, cudaStream_t s);
 // r = b - A~ x in float64 (binned order); counts pairs when cnt != nullptr (device int64).
 void residual_binned_f64(rbf_plan *P, const float *bs, const double *xs, double *rs,
                          unsigned long long *cnt, cudaStream_t s);
@@ -160,6 +164,7 @@ void spmv_binned(rbf_plan *P, const float *zs, float *ys, cudaStream_t s);
 // grid.cu
 void eval_grid(rbf_plan *P, const double *weights, const rbf_grid &g, float *f, cudaStream_t s);
 int64_t count_grid_pairs(rbf_plan *P, const rbf_grid &g, cudaStream_t s);
+int64_t count_grid_candidates(rbf_plan *P, const rbf_grid &g, cudaStream_t s);
 
 // batch.cu
 rbf_batch *batch_create(rbf_ctx *ctx, rbf_plan *const *plans, int nplans, cudaStream_t s);

@@ -49,10 +49,12 @@ struct MvArgs {
     float scl, R;
     float *out;          // y (binned) or grid f, for tiles with a single segment
     float *partial;      // [seg][kChunk] partial sums of split tiles
-    // grid targets: bricks of 8 x 4 x 4 nodes
+    // grid targets: bricks of 2^blog[0] x 2^blog[1] x 2^blog[2] = 128 nodes (bdim[d] bricks along
+    // axis d), each cut into four quarters of 2^qlog[0] x 2^qlog[1] x 2^qlog[2] = 32 nodes
     float glo[3], gstep[3];
     int gdim[3];
     int bdim[3];
+    int blog[3], qlog[3];
     // inverse multiquadric plans (direct kernel): 1 / sigma^2, beta, squared cut-off (k sigma)^2
     float imq_ic, imq_beta, rc2f;
 };
@@ -74,12 +76,17 @@ __device__ __forceinline__ bool target_xyz(const MvArgs &a, int64_t t, int q, fl
         outidx = -1;
         return false;
     } else {
-        // brick of 8 x 4 x 4 nodes; quarter u = q / 32 is its (u & 1, u >> 1) block of 4 x 2 x 4 nodes
-        // (compact, so that the quarter box tests of the pair list are tight)
+        // brick t; quarter u = q / 32 is a compact block of the brick (x fastest among the
+        // quarters and among the 32 nodes of a quarter), so that the quarter box tests of the
+        // pair list are tight
         int64_t bx = t % a.bdim[0], by = (t / a.bdim[0]) % a.bdim[1], bz = t / ((int64_t)a.bdim[0] * a.bdim[1]);
         const int u = q >> 5, l = q & 31;
-        int ix = (int)bx * 8 + 4 * (u & 1) + (l & 3), iy = (int)by * 4 + 2 * (u >> 1) + ((l >> 2) & 1),
-            iz = (int)bz * 4 + (l >> 3);
+        const int nx = a.blog[0] - a.qlog[0], ny = a.blog[1] - a.qlog[1];   // log2 quarters along x, y
+        const int ux = u & ((1 << nx) - 1), uy = (u >> nx) & ((1 << ny) - 1), uz = u >> (nx + ny);
+        const int lx = l & ((1 << a.qlog[0]) - 1), ly = (l >> a.qlog[0]) & ((1 << a.qlog[1]) - 1),
+                  lz = l >> (a.qlog[0] + a.qlog[1]);
+        int ix = ((int)bx << a.blog[0]) + (ux << a.qlog[0]) + lx, iy = ((int)by << a.blog[1]) + (uy << a.qlog[1]) + ly,
+            iz = ((int)bz << a.blog[2]) + (uz << a.qlog[2]) + lz;
         bool v = ix < a.gdim[0] && iy < a.gdim[1] && iz < a.gdim[2];
         x = fmaf((float)ix, a.gstep[0], a.glo[0]);
         y = fmaf((float)iy, a.gstep[1], a.glo[1]);

@@ -424,6 +424,31 @@ def test_eval_grid_truncated_ragged(ctx, rbf, product):
 
 
 @PRODUCTS
+def test_eval_grid_anisotropic_shapes(ctx, rbf, product):
+    """Grids whose spacings differ by axis get other brick and quarter shapes (chosen from
+    the spacings): a flat box, a one-node slice in z, a thin slab in x.  Every node is
+    compared on sampled sets with the oracle's direct sum, and the evaluated pairs bound the
+    pairs within the cut-off from above."""
+    _, C, _ = torus_patch(theta=0.1)
+    Cd, C64 = c4(C)
+    plan = rbf.Plan(ctx, Cd, sigma=0.02, k=6.0, product=product)
+    w = np.random.default_rng(8).standard_normal(len(C))
+    lo = C64.min(0) - 0.05
+    hi = C64.max(0) + 0.05
+    mid = 0.5 * (lo + hi)
+    cases = [
+        (lo, hi, (48, 44, 96)),                                                               # fine in z
+        (np.array([lo[0], lo[1], mid[2]]), np.array([hi[0], hi[1], mid[2]]), (50, 41, 1)),   # a slice
+        (np.array([mid[0] - 0.01, lo[1], lo[2]]), np.array([mid[0] + 0.01, hi[1], hi[2]]), (3, 60, 45)),
+    ]
+    for i, (a, b_, dims) in enumerate(cases):
+        _grid_check(plan, C64, w, 0.02, 6.0, a, b_, dims, seed=10 + i)
+        pairs = plan.count_grid_pairs(a, b_, dims)
+        cand = plan.count_grid_candidate_pairs(a, b_, dims)
+        assert pairs > 0 and cand >= pairs, (dims, pairs, cand)
+
+
+@PRODUCTS
 def test_eval_grid_single_node_and_far_grid(ctx, rbf, product):
     rng = np.random.default_rng(1)
     C = rng.uniform(0, 1, (500, 3))
