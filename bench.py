@@ -207,6 +207,20 @@ def max_over_ranks(v, world):
 
 
 # ----------------------------------------------------------------------------- oracle arm
+def host_info():
+    """The host the oracle ran on: CPU model and logical CPUs (from /proc/cpuinfo)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "logical_cpus": os.cpu_count()}
+
+
 def oracle_rate(C64, wl, nrows, seed=0):
     """Pair evaluations per second of the FP64 oracle on `nrows` sampled rows."""
     import numpy as np
@@ -243,7 +257,7 @@ def run_reference(args, wl):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": wl["desc"], "sample": f"{nrows} sampled rows per step", "sigma": wl["sigma"],
                       "k": wl["k"]},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "host": host_info(),
                             "sample": f"{nrows} sampled rows of the {len(C64):,}-centre operator per step, "
                                       f"float64 row sums over a bucket list"},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -377,7 +391,7 @@ def run_ours(args, wl):
         orc.set_threads(1)
         rate1, cnt1, dt1 = oracle_rate(Cc, wl, max(200, args.cpu_rows // 10), seed=1)
         orc.set_threads(cores)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "host": host_info(),
                "sample": f"{min(args.cpu_rows, len(Cc))} sampled rows of the {len(Cc):,}-centre operator "
                          f"({cnt:,} pairs, {dt:.1f} s), float64 row sums over a bucket list",
                "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
@@ -514,7 +528,7 @@ def run_assembled(args, wl):
         Cc, _ = orc.build_centers(cl.points, cl.normals, wl["delta"])
         Cc = Cc.astype(np.float32).astype(np.float64)
         rate, cnt, dt = oracle_rate(Cc, wl, min(args.cpu_rows, 20000))
-        cpu = {"value": rate, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+        cpu = {"value": rate, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle", "host": host_info(),
                "sample": f"{min(args.cpu_rows, 20000)} sampled rows of the {len(Cc):,}-centre truncated operator "
                          f"({cnt:,} pairs, {dt:.1f} s), float64 row sums over a bucket list"}
     if rank == 0:
@@ -826,7 +840,7 @@ def run_density_reference(args, wl):
            "value": v, "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic", "config": {"workload": wl["desc"]},
-           "cpu_baseline": {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle", "host": host_info(),
                             "sample": f"{rows} sampled points per step, brute force over all {len(X):,} points"},
            "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
