@@ -226,9 +226,14 @@ __global__ void __launch_bounds__(kThreads) k_bmaxpy(const double *__restrict__ 
 // dst = src / scale(problem) (0 where the scale is 0)
 __global__ void k_bscale(const double *__restrict__ src, const double *__restrict__ scale,
                          double *__restrict__ dst, const int4 *__restrict__ chunks) {
+    __shared__ double s_inv;    // one float64 division per CTA
     const int4 c = chunks[blockIdx.x];
-    const double sv = scale[c.x];
-    const double inv = sv > 0.0 ? 1.0 / sv : 0.0;
+    if (threadIdx.x == 0) {
+        const double sv = scale[c.x];
+        s_inv = sv > 0.0 ? 1.0 / sv : 0.0;
+    }
+    __syncthreads();
+    const double inv = s_inv;
     for (int i = threadIdx.x; i < c.z; i += blockDim.x) dst[c.y + i] = src[c.y + i] * inv;
 }
 

@@ -125,12 +125,15 @@ __global__ void __launch_bounds__(kThreads) k_maxpy(const double *__restrict__ V
     }
 }
 
-// dst = src / s (s on the device), float64
+// dst = src * (1 / s) (s on the device), float64.  One thread per CTA forms the
+// reciprocal: a float64 division costs many float64 FMA slots on this GPU.
 __global__ void k_scale(const double *__restrict__ src, const double *__restrict__ sptr, double *__restrict__ dst,
                         int64_t n) {
+    __shared__ double s_inv;
+    if (threadIdx.x == 0) s_inv = 1.0 / *sptr;
+    __syncthreads();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double inv = 1.0 / *sptr;
-    if (i < n) dst[i] = src[i] * inv;
+    if (i < n) dst[i] = src[i] * s_inv;
 }
 
 __global__ void k_sqrt(double *p) { *p = sqrt(*p); }
