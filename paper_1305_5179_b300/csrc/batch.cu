@@ -2,9 +2,10 @@
 // uneven size): flexible GMRES in lockstep over all problems with every step on
 // the device, so that a whole solve is one CUDA graph.
 //
-//  * the product is one persistent kernel: CTAs pull (problem, segment) work
-//    items, longest first, from an atomic counter, so small and large problems
-//    share the GPU without a launch per problem;
+//  * the product is one launch over all problems, (problem, segment) work items
+//    longest first: with the tensor-core product one CTA per item, with the
+//    CUDA-core product persistent CTAs that pull items from an atomic counter; so
+//    small and large problems share the GPU without a launch per problem;
 //  * the Arnoldi dot products and updates are segmented reductions over chunks of
 //    <= kRange entries that never cross a problem boundary (float64, fixed order);
 //  * the Hessenberg column, Givens rotations, residual estimate and the final
