@@ -32,8 +32,8 @@ __device__ __forceinline__ void dom_of(int64_t blkid, int core, int B, int64_t n
 }
 
 // Blocked Cholesky of the padded matrix (Bp = B rounded up to 32, identity beyond B) in
-// shared memory, tiles of 32 x 32, right-looking: the diagonal tile by all threads (per
-// column: pivot, scaled column, the tile's trailing triangle), the panel below it by one
+// shared memory, tiles of 32 x 32, right-looking: the diagonal tile by one warp in
+// registers (per column: pivot, scaled column, the tile's trailing triangle), the panel below it by one
 // thread per row (substitution against the diagonal tile), the trailing tiles by the
 // four warps (each lane one column of a tile, the panel rows broadcast from shared
 // memory).  A pivot that is not positive and finite fails the attempt.
@@ -79,28 +79,32 @@ __global__ void __launch_bounds__(kSetupThreads) k_schwarz_setup(const float4 *_
         __syncthreads();
         for (int k = 0; k < T; ++k) {
             const int k0 = 32 * k;
-            // 1. diagonal tile, in shared memory: per column jj the pivot, the column scaled by
-            //    it, then the tile's remaining lower triangle updated (32 x 32 elements spread
-            //    over the CTA's threads)
-            for (int jj = 0; jj < 32; ++jj) {
-                const int j = k0 + jj;
-                const float d = A[j * ld + j];
-                if (threadIdx.x == 0 && (!(d > 0.f) || !isfinite(d))) s_fail = 1;
-                const float ljj = sqrtf(fmaxf(d, 1e-30f));
-                __syncthreads();
-                if (threadIdx.x < 32) {
-                    const int r = k0 + threadIdx.x;
-                    if (threadIdx.x == jj) A[j * ld + j] = ljj;
-                    else if ((int)threadIdx.x > jj) A[r * ld + j] /= ljj;
+            // 1. diagonal tile by warp 0, in registers: lane r holds row k0 + r; per column jj
+            //    the pivot, the column scaled by it (shuffled to the other rows), then the
+            //    tile's remaining lower triangle updated, with no CTA barrier in between
+            if (warp == 0) {
+                float x[32];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) x[c] = A[(k0 + lane) * ld + k0 + c];
+                bool bad = false;
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) {
+                    const float d = __shfl_sync(0xffffffffu, x[jj], jj);
+                    bad |= !(d > 0.f) || !isfinite(d);
+                    const float ljj = sqrtf(fmaxf(d, 1e-30f));
+                    if (lane == jj) x[jj] = ljj;
+                    else if (lane > jj) x[jj] /= ljj;
+#pragma unroll
+                    for (int cc = 0; cc < 32; ++cc) {
+                        if (cc <= jj) continue;
+                        const float lc = __shfl_sync(0xffffffffu, x[jj], cc);   // L[k0 + cc][k0 + jj]
+                        if (lane >= cc) x[cc] = fmaf(-x[jj], lc, x[cc]);
+                    }
                 }
-                __syncthreads();
-                for (int e = threadIdx.x; e < 32 * 32; e += kSetupThreads) {
-                    const int rr = e >> 5, cc = e & 31;
-                    if (cc > jj && rr >= cc)
-                        A[(k0 + rr) * ld + k0 + cc] =
-                            fmaf(-A[(k0 + rr) * ld + j], A[(k0 + cc) * ld + j], A[(k0 + rr) * ld + k0 + cc]);
-                }
-                __syncthreads();     // the next pivot is written by this update
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                    if (c <= lane) A[(k0 + lane) * ld + k0 + c] = x[c];
+                if (lane == 0 && bad) s_fail = 1;
             }
             __syncthreads();
             if (s_fail) break;
