@@ -33,7 +33,8 @@ __device__ __forceinline__ void dom_of(int64_t blkid, int core, int B, int64_t n
 
 // Blocked Cholesky of the padded matrix (Bp = B rounded up to 32, identity beyond B) in
 // shared memory, tiles of 32 x 32, right-looking: the diagonal tile by one warp in
-// registers (per column: pivot, scaled column, the tile's trailing triangle), the panel below it by one
+// registers (per column: pivot, column scaled by its reciprocal, the tile's trailing
+// triangle), the panel below it by one
 // thread per row (substitution against the diagonal tile), the trailing tiles by the
 // four warps (each lane one column of a tile, the panel rows broadcast from shared
 // memory).  A pivot that is not positive and finite fails the attempt.
@@ -47,6 +48,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_schwarz_setup(const float4 *_
     float *A = sm;                                  // Bp x (Bp + 1), padded rows
     float4 *P = reinterpret_cast<float4 *>(sm + Bp * ld);   // the block's positions
     __shared__ int s_fail;
+    __shared__ float s_rcp[32];     // reciprocal pivots of the current diagonal tile
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t d0, c0;
     int cl;
@@ -91,9 +93,13 @@ __global__ void __launch_bounds__(kSetupThreads) k_schwarz_setup(const float4 *_
                 for (int jj = 0; jj < 32; ++jj) {
                     const float d = __shfl_sync(0xffffffffu, x[jj], jj);
                     bad |= !(d > 0.f) || !isfinite(d);
-                    const float ljj = sqrtf(fmaxf(d, 1e-30f));
-                    if (lane == jj) x[jj] = ljj;
-                    else if (lane > jj) x[jj] /= ljj;
+                    const float ljj = sqrtf(fmaxf(d, 1e-30f)), rl = __frcp_rn(ljj);
+                    if (lane == jj) {
+                        x[jj] = ljj;
+                        s_rcp[jj] = rl;     // for the panel below
+                    } else if (lane > jj) {
+                        x[jj] *= rl;
+                    }
 #pragma unroll
                     for (int cc = 0; cc < 32; ++cc) {
                         if (cc <= jj) continue;
@@ -119,7 +125,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_schwarz_setup(const float4 *_
                     float acc = x[c];
 #pragma unroll
                     for (int m = 0; m < c; ++m) acc = fmaf(-x[m], A[(k0 + c) * ld + k0 + m], acc);
-                    x[c] = acc / A[(k0 + c) * ld + k0 + c];
+                    x[c] = acc * s_rcp[c];
                 }
 #pragma unroll
                 for (int c = 0; c < 32; ++c) A[r * ld + k0 + c] = x[c];
