@@ -273,7 +273,7 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
     w32.alloc(n, s);
     w64.alloc(n, s);
     part.alloc((size_t)(m + 1) * G, s);
-    hdev.alloc(3 * (m + 1), s);
+    hdev.alloc((size_t)m * 3 * (m + 1), s);   // per Arnoldi step of a cycle: h, h2, |w|
     x.alloc(n, s);
     x.zero(s);
     r.alloc(n, s);
@@ -299,7 +299,8 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
     }
 
     Intervals t_mv, t_res, t_pc;
-    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hcol(m + 2), yh(m), hbuf(3 * (m + 1));
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hcol(m + 2), yh(m),
+        hbuf((size_t)m * 3 * (m + 1));
     int it = 0, cycles = 0;
     double beta = bnorm, est = 1.0, true_rel = bnorm > 0 ? 1.0 : 0.0;
     bool converged = bnorm == 0.0, breakdown = false;
@@ -340,6 +341,39 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
         int j = 0, k = 0;
+        // Host side of Arnoldi step jj: Hessenberg column from its slot (h + h2, |w|), Givens
+        // rotations, residual estimate.  False ends the cycle (breakdown, an exact solution
+        // in the Krylov space, or the tolerance met).
+        auto take_column = [&](int jj, const double *hb) -> bool {
+            const int nv = jj + 1;
+            for (int i = 0; i < nv; ++i) hcol[i] = hb[i] + hb[m + 1 + i];
+            hcol[nv] = hb[2 * (m + 1)];
+            bool finite = true;
+            for (int i = 0; i <= nv; ++i) finite = finite && std::isfinite(hcol[i]);
+            if (!finite) {
+                breakdown = true;
+                return false;
+            }
+            for (int i = 0; i <= nv; ++i) H[(size_t)i * m + jj] = hcol[i];
+            for (int i = 0; i < jj; ++i) {
+                double t = cs[i] * H[(size_t)i * m + jj] + sn[i] * H[(size_t)(i + 1) * m + jj];
+                H[(size_t)(i + 1) * m + jj] = -sn[i] * H[(size_t)i * m + jj] + cs[i] * H[(size_t)(i + 1) * m + jj];
+                H[(size_t)i * m + jj] = t;
+            }
+            double a = H[(size_t)jj * m + jj], bb = H[(size_t)(jj + 1) * m + jj];
+            double rho = std::hypot(a, bb);
+            cs[jj] = rho > 0 ? a / rho : 1.0;
+            sn[jj] = rho > 0 ? bb / rho : 0.0;
+            H[(size_t)jj * m + jj] = rho;
+            H[(size_t)(jj + 1) * m + jj] = 0.0;
+            g[jj + 1] = -sn[jj] * g[jj];
+            g[jj] = cs[jj] * g[jj];
+            est = std::fabs(g[jj + 1]) / bnorm;
+            k = jj + 1;
+            if (hcol[nv] == 0.0) return false;                            // exact solution in the Krylov space
+            if (!p.fixed_iterations && est <= tol) return false;
+            return true;
+        };
         for (j = 0; j < m && it < max_it; ++j) {
             double *Vj = V.p + (size_t)j * n;
             float *Zj = Z.p + (size_t)j * n;
@@ -359,16 +393,17 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
             op(Zj, w32.p);
             t_mv.end(s);
             const int nv = j + 1;
+            double *h1 = hdev.p + (size_t)j * 3 * (m + 1);   // this step's slot
+            double *h2 = h1 + (m + 1);
+            double *hn = h1 + 2 * (m + 1);
             // pass 1
             k_mdot<float><<<G, kThreads, 0, s>>>(V.p, n, nv, w32.p, n, part.p);
             RBF_LAUNCHED();
-            k_mdot_final<<<nv, kThreads, 0, s>>>(part.p, G, hdev.p, 0);
+            k_mdot_final<<<nv, kThreads, 0, s>>>(part.p, G, h1, 0);
             RBF_LAUNCHED();
-            k_maxpy<float><<<G, kThreads, 0, s>>>(V.p, n, nv, hdev.p, w32.p, w64.p, n, nullptr);
+            k_maxpy<float><<<G, kThreads, 0, s>>>(V.p, n, nv, h1, w32.p, w64.p, n, nullptr);
             RBF_LAUNCHED();
             // pass 2 (re-orthogonalisation), accumulating into h, with |w|^2 partials
-            double *h2 = hdev.p + (m + 1);
-            double *hn = hdev.p + 2 * (m + 1);
             k_mdot<double><<<G, kThreads, 0, s>>>(V.p, n, nv, w64.p, n, part.p);
             RBF_LAUNCHED();
             k_mdot_final<<<nv, kThreads, 0, s>>>(part.p, G, h2, 0);
@@ -379,37 +414,29 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
             RBF_LAUNCHED();
             k_sqrt<<<1, 1, 0, s>>>(hn);
             RBF_LAUNCHED();
-            RBF_CUDA(cudaMemcpyAsync(hbuf.data(), hdev.p, 3 * (m + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
             k_scale<<<g1(n), kThreads, 0, s>>>(w64.p, hn, V.p + (size_t)(j + 1) * n, n);
             RBF_LAUNCHED();
-            RBF_CUDA(cudaStreamSynchronize(s));
             ++it;
-            for (int i = 0; i < nv; ++i) hcol[i] = hbuf[i] + hbuf[m + 1 + i];
-            hcol[nv] = hbuf[2 * (m + 1)];
-            bool finite = true;
-            for (int i = 0; i <= nv; ++i) finite = finite && std::isfinite(hcol[i]);
-            if (!finite) {
-                breakdown = true;
-                break;
-            }
-            for (int i = 0; i <= nv; ++i) H[(size_t)i * m + j] = hcol[i];
-            for (int i = 0; i < j; ++i) {
-                double t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
-                H[(size_t)(i + 1) * m + j] = -sn[i] * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
-                H[(size_t)i * m + j] = t;
-            }
-            double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
-            double rho = std::hypot(a, bb);
-            cs[j] = rho > 0 ? a / rho : 1.0;
-            sn[j] = rho > 0 ? bb / rho : 0.0;
-            H[(size_t)j * m + j] = rho;
-            H[(size_t)(j + 1) * m + j] = 0.0;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = cs[j] * g[j];
-            est = std::fabs(g[j + 1]) / bnorm;
-            k = j + 1;
-            if (hcol[nv] == 0.0) break;                               // exact solution in the Krylov space
-            if (!p.fixed_iterations && est <= tol) break;
+            // with a fixed iteration count nothing on the device waits for the host: the
+            // columns are read back once at the end of the cycle
+            if (p.fixed_iterations) continue;
+            RBF_CUDA(cudaMemcpyAsync(hbuf.data(), h1, 3 * (m + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+            RBF_CUDA(cudaStreamSynchronize(s));
+            if (!take_column(j, hbuf.data())) break;
+        }
+        if (p.fixed_iterations && j > 0) {
+            // steps after a breakdown ran on non-finite or zero-scaled vectors; their columns
+            // are never used
+            RBF_CUDA(cudaMemcpyAsync(hbuf.data(), hdev.p, (size_t)j * 3 * (m + 1) * sizeof(double),
+                                     cudaMemcpyDeviceToHost, s));
+            RBF_CUDA(cudaStreamSynchronize(s));
+            int used = j;
+            for (int jj = 0; jj < j; ++jj)
+                if (!take_column(jj, hbuf.data() + (size_t)jj * 3 * (m + 1))) {
+                    used = jj + 1;
+                    break;
+                }
+            it -= j - used;   // count the steps the cycle used, as the step-by-step form does
         }
         if (k == 0) break;
         // back substitution for y (k x k upper triangular)

@@ -327,6 +327,23 @@ def test_fgmres_first_iterations_match_oracle(ctx, rbf, sphere_c1):
     assert rel2(A @ x.cpu().numpy(), A @ xo) <= 1e-4
 
 
+def test_fgmres_fixed_count_equals_step_by_step(ctx, rbf, sphere_c1):
+    """With a fixed iteration count the Hessenberg columns are read back once per cycle;
+    the iterates are bitwise those of the step-by-step form (a tolerance never met), over
+    two restart cycles and with the Schwarz preconditioner."""
+    C, b = oracle.build_centers(sphere_c1.points, sphere_c1.normals, 0.05)
+    Cd, _ = c4(C)
+    b32 = dev(b.astype(np.float32))
+    plan = rbf.Plan(ctx, Cd, sigma=0.1, k=0.0)
+    for kw in (dict(), dict(precond="schwarz", core=96, block=128, shift=1e-2)):
+        xf, rf = plan.solve(b32, m=10, max_it=20, fixed_iterations=True, **kw)
+        xs, rs = plan.solve(b32, m=10, max_it=20, tol=1e-30, **kw)
+        assert rf["iterations"] == rs["iterations"] == 20
+        assert torch.equal(xf, xs)
+        assert rf["residual_estimate"] == rs["residual_estimate"]
+        assert rf["residual_true"] == rs["residual_true"]
+
+
 def test_fgmres_true_residual_report(ctx, rbf, sphere_c1):
     C, b = oracle.build_centers(sphere_c1.points, sphere_c1.normals, 0.05)
     Cd, C64 = c4(C)
