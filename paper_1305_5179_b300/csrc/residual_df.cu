@@ -21,7 +21,8 @@
 //   accumulator once per block.
 // Per-term relative error is of order 1e-14.  Pairs beyond the cut-off get a zero
 // scale 2^-e, so their terms are exactly zero; every intermediate stays finite for
-// t below 1e20.
+// t below 1e20.  For one plan each pair's entry is evaluated once and serves both of
+// its rows (the symmetric form below); batches use the one-sided form.
 #include <cmath>
 #include <vector>
 
@@ -70,64 +71,87 @@ __device__ __forceinline__ void load_table(float2 *s_tab) {
     for (int j = threadIdx.x; j < kTab; j += blockDim.x) s_tab[j] = d_tab[j];
 }
 
+// Squared distance of a target and a source in double-float, and the cut-off test.
+struct PairR2 {
+    df r2;
+    bool in;
+};
+__device__ __forceinline__ PairR2 pair_r2(float px, float py, float pz, const float4 q, const DfConst &k) {
+    const df dx = two_sum(px, -q.x), dy = two_sum(py, -q.y), dz = two_sum(pz, -q.z);
+    // |d|^2 = sum dh^2 (exact products) + 2 sum dh dl (dl^2 < 2^-48 dh^2 is dropped)
+    const df sx = two_prod(dx.h, dx.h), sy = two_prod(dy.h, dy.h), sz = two_prod(dz.h, dz.h);
+    const float cr = __fmaf_rn(dx.h, dx.l, __fmaf_rn(dy.h, dy.l, __fmul_rn(dz.h, dz.l)));
+    const df s = two_sum_pos(sx.h, sy.h);
+    df r2 = two_sum_pos(s.h, sz.h);
+    r2.l = __fadd_rn(__fadd_rn(r2.l, __fadd_rn(s.l, __fadd_rn(sx.l, sy.l))), __fmaf_rn(2.f, cr, sz.l));
+    // r2 < R: (r2.h - Rh) is exact near the radius (Sterbenz) and decides the sign elsewhere
+    const bool in = __fadd_rn(__fsub_rn(r2.h, k.Rh), __fsub_rn(r2.l, k.Rl)) < 0.f;
+    return {r2, in};
+}
+
+// The matrix entry 2^-t, t = r2 C, in double-float; exactly zero beyond the cut-off.
+__device__ __forceinline__ df pair_exp(const PairR2 &pr, const DfConst &k, const float2 *__restrict__ tab) {
+    const float Lh = k.Lh, Ll = k.Ll;
+    const df r2 = pr.r2;
+    // t = r2 * C
+    df t = two_prod(r2.h, k.Ch);
+    t.l = __fadd_rn(t.l, __fmaf_rn(r2.h, k.Cl, __fmul_rn(r2.l, k.Ch)));
+    // m = round(1024 t) by the 1.5 x 2^23 shift (exact below 2^22; t is clamped far above
+    // where 2^-t underflows), then t = m / 1024 + fh exactly
+    const float th = fminf(t.h, 2048.f);
+    const float y = __fmaf_rn(th, (float)kTab, 12582912.f);
+    const float mf = __fsub_rn(y, 12582912.f);
+    const int m = __float_as_int(y) - 0x4B400000;
+    const float fh = __fmaf_rn(mf, -1.f / kTab, th);
+    // g = (fh + t.l) ln 2
+    df g = two_prod(fh, Lh);
+    g.l = __fadd_rn(g.l, __fmaf_rn(fh, Ll, __fmul_rn(t.l, Lh)));
+    // exp(-g) - 1 = -g + g^2/2 - g^3/6 + ...; g.l holds t.l ln 2 and is not below ulp(g.h),
+    // so the float32 terms take the rounded sum gs = g.h + g.l
+    const float gs = __fadd_rn(g.h, g.l);
+    const float g2 = __fmul_rn(gs, gs);
+    const float rest = __fmul_rn(g2, __fmaf_rn(gs, -1.f / 6.f, 0.5f));
+    df D = fast_two_sum(-g.h, rest);          // |g| >= g^2 / 2
+    D.l = __fsub_rn(D.l, g.l);
+    // E = T_j (1 + D)
+    const float2 T = tab[m & (kTab - 1)];
+    const df p = two_prod(T.x, D.h);
+    df E = fast_two_sum(T.x, p.h);            // T in [1/2, 1], |p| < 3e-4
+    E.l = __fadd_rn(E.l, __fadd_rn(p.l, __fmaf_rn(T.x, D.l, __fmaf_rn(T.y, D.h, T.y))));
+    // 2^-e (zero from e = 127 on, and for a pair beyond the cut-off)
+    const int e = min(m >> kTabBits, 127);
+    const float sc = pr.in ? __int_as_float((127 - e) << 23) : 0.f;
+    E.h = __fmul_rn(E.h, sc);
+    E.l = __fmul_rn(E.l, sc);
+    return E;
+}
+
+// E * w for a double-float weight w = (hi, lo), and acc += it, in double-float
+__device__ __forceinline__ df times_w(const df E, const float2 w) {
+    df P = two_prod(E.h, w.x);
+    P.l = __fadd_rn(P.l, __fmaf_rn(E.h, w.y, __fmul_rn(E.l, w.x)));
+    return P;
+}
+__device__ __forceinline__ void add_to(df &acc, const df P) {
+    const df a2 = two_sum(acc.h, P.h);
+    acc.h = a2.h;
+    acc.l = __fadd_rn(acc.l, __fadd_rn(a2.l, P.l));
+}
+
 // sum over one staged block of w_j 2^(-t_ij) for the target (px, py, pz); called by
 // every lane of a warp with the same cnt
 __device__ __forceinline__ df block_terms(float px, float py, float pz, const float4 *__restrict__ sp,
                                           const float2 *__restrict__ sw, int cnt, const DfConst &k,
                                           const float2 *__restrict__ tab) {
-    const float Lh = k.Lh, Ll = k.Ll;
     df acc = {0.f, 0.f};
     for (int j = 0; j < cnt; ++j) {
         const float4 q = sp[j];
         const float2 w = sw[j];
-        const df dx = two_sum(px, -q.x), dy = two_sum(py, -q.y), dz = two_sum(pz, -q.z);
-        // |d|^2 = sum dh^2 (exact products) + 2 sum dh dl (dl^2 < 2^-48 dh^2 is dropped)
-        const df sx = two_prod(dx.h, dx.h), sy = two_prod(dy.h, dy.h), sz = two_prod(dz.h, dz.h);
-        const float cr = __fmaf_rn(dx.h, dx.l, __fmaf_rn(dy.h, dy.l, __fmul_rn(dz.h, dz.l)));
-        const df s = two_sum_pos(sx.h, sy.h);
-        df r2 = two_sum_pos(s.h, sz.h);
-        r2.l = __fadd_rn(__fadd_rn(r2.l, __fadd_rn(s.l, __fadd_rn(sx.l, sy.l))), __fmaf_rn(2.f, cr, sz.l));
-        // r2 < R: (r2.h - Rh) is exact near the radius (Sterbenz) and decides the sign elsewhere
-        const bool in = __fadd_rn(__fsub_rn(r2.h, k.Rh), __fsub_rn(r2.l, k.Rl)) < 0.f;
+        const PairR2 pr = pair_r2(px, py, pz, q, k);
         // a source beyond the cut-off for every target of the warp adds nothing: skip its
         // exponential (the loop runs over the same sources on every lane, so the vote is uniform)
-        if (!__any_sync(0xffffffffu, in)) continue;
-        // t = r2 * C
-        df t = two_prod(r2.h, k.Ch);
-        t.l = __fadd_rn(t.l, __fmaf_rn(r2.h, k.Cl, __fmul_rn(r2.l, k.Ch)));
-        // m = round(1024 t) by the 1.5 x 2^23 shift (exact below 2^22; t is clamped far above
-        // where 2^-t underflows), then t = m / 1024 + fh exactly
-        const float th = fminf(t.h, 2048.f);
-        const float y = __fmaf_rn(th, (float)kTab, 12582912.f);
-        const float mf = __fsub_rn(y, 12582912.f);
-        const int m = __float_as_int(y) - 0x4B400000;
-        const float fh = __fmaf_rn(mf, -1.f / kTab, th);
-        // g = (fh + t.l) ln 2
-        df g = two_prod(fh, Lh);
-        g.l = __fadd_rn(g.l, __fmaf_rn(fh, Ll, __fmul_rn(t.l, Lh)));
-        // exp(-g) - 1 = -g + g^2/2 - g^3/6 + ...; g.l holds t.l ln 2 and is not below ulp(g.h),
-        // so the float32 terms take the rounded sum gs = g.h + g.l
-        const float gs = __fadd_rn(g.h, g.l);
-        const float g2 = __fmul_rn(gs, gs);
-        const float rest = __fmul_rn(g2, __fmaf_rn(gs, -1.f / 6.f, 0.5f));
-        df D = fast_two_sum(-g.h, rest);          // |g| >= g^2 / 2
-        D.l = __fsub_rn(D.l, g.l);
-        // E = T_j (1 + D)
-        const float2 T = tab[m & (kTab - 1)];
-        const df p = two_prod(T.x, D.h);
-        df E = fast_two_sum(T.x, p.h);            // T in [1/2, 1], |p| < 3e-4
-        E.l = __fadd_rn(E.l, __fadd_rn(p.l, __fmaf_rn(T.x, D.l, __fmaf_rn(T.y, D.h, T.y))));
-        // 2^-e (zero from e = 127 on, and for a pair beyond the cut-off)
-        const int e = min(m >> kTabBits, 127);
-        const float sc = in ? __int_as_float((127 - e) << 23) : 0.f;
-        E.h = __fmul_rn(E.h, sc);
-        E.l = __fmul_rn(E.l, sc);
-        // term = E * w, accumulated in double-float
-        df P = two_prod(E.h, w.x);
-        P.l = __fadd_rn(P.l, __fmaf_rn(E.h, w.y, __fmul_rn(E.l, w.x)));
-        const df a2 = two_sum(acc.h, P.h);
-        acc.h = a2.h;
-        acc.l = __fadd_rn(acc.l, __fadd_rn(a2.l, P.l));
+        if (!__any_sync(0xffffffffu, pr.in)) continue;
+        add_to(acc, times_w(pair_exp(pr, k, tab), w));
     }
     return acc;
 }
@@ -168,27 +192,156 @@ __device__ __forceinline__ double resid_segment(const float4 *__restrict__ pos, 
     return acc;
 }
 
-__global__ void __launch_bounds__(kT) k_resid_df(const float4 *__restrict__ pos, const int2 *__restrict__ tiles,
-                                                 const double *__restrict__ x,
-                                                 const int2 *__restrict__ blk, const int32_t *__restrict__ ent,
-                                                 const int2 *__restrict__ ebi, const int4 *__restrict__ seg,
-                                                 int64_t n, DfConst kc,
-                                                 const float *__restrict__ b, double *__restrict__ out,
-                                                 double *__restrict__ part) {
+// ---------------------------------------------------------------- symmetric form
+// A~ is symmetric, so one evaluation of a pair's entry serves both rows.  A pair (i, j),
+// i in the CTA's tile T and j in a block of its list, is taken from this side when j's
+// tile comes after T (both rows) or is T itself (this row only: the tile meets its own
+// blocks from both sides), and skipped when j's tile comes before T (the other side
+// takes it).  Every pair within the cut-off appears in both tiles' lists, so each is
+// counted once per row.  Row j's share, sum_i a_ij x_i over this warp's 32 targets, is
+// summed per source in double-float and added to a 128-bit fixed-point accumulator
+// (units of 2^-80) with integer atomics: integer addition is exact, so the result does
+// not depend on the order the CTAs run in.
+constexpr int kFix = 80;
+
+// v 2^kFix as a signed 128-bit integer, truncated toward zero below 2^-kFix (|v| < 2^44)
+__device__ __forceinline__ __int128 to_fix(float v) {
+    const unsigned u = __float_as_uint(v);
+    const int ex = (int)((u >> 23) & 0xffu);
+    if (ex == 0) return 0;                              // zero, or below 2^-126
+    const unsigned long long m = (u & 0x7fffffu) | 0x800000u;
+    const int sh = ex - 150 + kFix;                    // v = m 2^(ex - 150)
+    unsigned __int128 mag = 0;
+    if (sh >= 0) mag = (unsigned __int128)m << (sh < 100 ? sh : 100);
+    else if (sh > -24) mag = m >> (-sh);
+    return (u >> 31) ? -(__int128)mag : (__int128)mag;
+}
+
+__device__ __forceinline__ void atomic_add_fix(unsigned long long *a, __int128 v) {
+    const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)((unsigned __int128)v >> 64);
+    const unsigned long long old = atomicAdd(a, lo);
+    atomicAdd(a + 1, hi + (old + lo < old ? 1ull : 0ull));
+}
+
+// one segment: target-side sum returned; source-side sums added to fix_acc (2 words per
+// centre, binned order).  Staging as resid_segment, plus each source's tile; qs is this
+// warp's 16 x 33 scratch of per-pair source-side terms (16 sources at a time).
+__device__ __forceinline__ double resid_segment_sym(const float4 *__restrict__ pos, const int2 tl, int64_t T,
+                                                    const double *__restrict__ x, const int2 *__restrict__ blk,
+                                                    const int32_t *__restrict__ ent, const int2 *__restrict__ ebi,
+                                                    const int32_t *__restrict__ tile_of, const int4 sg,
+                                                    const DfConst &kc, float4 *s_p, float2 *s_w, int *s_tj,
+                                                    float2 (*qs)[33], const float2 *s_tab,
+                                                    unsigned long long *__restrict__ fix_acc, bool &valid, int64_t &i) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quarter_shift = 8 + 2 * warp;
+    float4 *wp = s_p + 32 * warp;
+    float2 *ww = s_w + 32 * warp;
+    int *wt = s_tj + 32 * warp;
+    i = (int64_t)tl.x + threadIdx.x;
+    valid = (int)threadIdx.x < tl.y;
+    const float4 p = valid ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 xi = make_float2(0.f, 0.f);                  // this target's weight (zero for an empty slot)
+    if (valid) {
+        const double xv = x[i];
+        xi.x = (float)xv;
+        xi.y = (float)(xv - (double)xi.x);
+    }
+    double acc = 0.0;
+    for (int e = sg.y; e < sg.z; ++e) {
+        if (ebi && ((ebi[e].y >> quarter_shift) & 3) == 0) continue;
+        const int2 bi = blk[ent[e] & 0x7fffffff];
+        __syncwarp();
+        if (lane < bi.y) {
+            wp[lane] = pos[bi.x + lane];
+            const double xv = x[bi.x + lane];
+            const float xh = (float)xv;
+            ww[lane] = make_float2(xh, (float)(xv - (double)xh));
+            wt[lane] = tile_of[bi.x + lane];
+        }
+        __syncwarp();
+        df a = {0.f, 0.f};
+        // the block's sources in two halves of 16, so that the scratch holds 16 columns
+        for (int h0 = 0; h0 < bi.y; h0 += 16) {
+            const int h1 = min(h0 + 16, bi.y);
+            unsigned symmask = 0;
+            for (int j = h0; j < h1; ++j) {
+                const int tj = wt[j];
+                if (tj < T) continue;                   // the other tile takes this pair
+                const float4 q = wp[j];
+                const float2 w = ww[j];
+                const PairR2 pr = pair_r2(p.x, p.y, p.z, q, kc);
+                if (!__any_sync(0xffffffffu, pr.in)) continue;
+                const df E = pair_exp(pr, kc, s_tab);
+                add_to(a, times_w(E, w));
+                if (tj > T) {                           // row j's term a_ij x_i
+                    const df Q = times_w(E, xi);
+                    qs[j - h0][lane] = make_float2(Q.h, Q.l);
+                    symmask |= 1u << (j - h0);
+                }
+            }
+            if (symmask) {
+                // column c = lane & 15 summed over rows 16 (lane >> 4) .. + 15 by each half of
+                // the warp, the halves combined by a shuffle; the first half holds the sums
+                __syncwarp();
+                const int c = lane & 15, r0 = (lane >> 4) * 16;
+                df cs = {0.f, 0.f};
+                if ((symmask >> c) & 1u)
+                    for (int r = r0; r < r0 + 16; ++r) {
+                        const float2 v = qs[c][r];
+                        add_to(cs, df{v.x, v.y});
+                    }
+                const df other = {__shfl_down_sync(0xffffffffu, cs.h, 16), __shfl_down_sync(0xffffffffu, cs.l, 16)};
+                if (lane < 16 && ((symmask >> c) & 1u)) {
+                    add_to(cs, other);
+                    atomic_add_fix(fix_acc + 2 * (bi.x + h0 + c), to_fix(cs.h) + to_fix(cs.l));
+                }
+                __syncwarp();
+            }
+        }
+        acc += (double)a.h + (double)a.l;
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(kT) k_resid_df_sym(const float4 *__restrict__ pos, const int2 *__restrict__ tiles,
+                                                     const double *__restrict__ x, const int2 *__restrict__ blk,
+                                                     const int32_t *__restrict__ ent, const int2 *__restrict__ ebi,
+                                                     const int4 *__restrict__ seg, const int32_t *__restrict__ tile_of,
+                                                     DfConst kc, const float *__restrict__ b, double *__restrict__ out,
+                                                     double *__restrict__ part, unsigned long long *__restrict__ fix_acc) {
     __shared__ float4 s_p[kT];
     __shared__ float2 s_w[kT];
+    __shared__ int s_tj[kT];
+    __shared__ float2 s_q[kT / 32][16][33];
     __shared__ float2 s_tab[kTab];
     load_table(s_tab);
     __syncthreads();
     const int4 sg = seg[blockIdx.x];
     bool valid;
     int64_t i;
-    double acc = resid_segment(pos, tiles[sg.x], x, blk, ent, ebi, sg, kc, s_p, s_w, s_tab, valid, i);
+    double acc = resid_segment_sym(pos, tiles[sg.x], sg.x, x, blk, ent, ebi, tile_of, sg, kc, s_p, s_w, s_tj,
+                                   s_q[threadIdx.x >> 5], s_tab, fix_acc, valid, i);
     if (sg.w) {
         if (valid) out[i] = (double)b[i] - acc;
     } else {
         part[(int64_t)blockIdx.x * kChunk + threadIdx.x] = acc;
     }
+}
+
+// tile_of[i] = the tile holding binned position i
+__global__ void k_tile_of(const int2 *__restrict__ tiles, int32_t *__restrict__ tile_of) {
+    const int2 tl = tiles[blockIdx.x];
+    for (int q = threadIdx.x; q < tl.y; q += blockDim.x) tile_of[tl.x + q] = (int32_t)blockIdx.x;
+}
+
+// out[j] -= the source-side sum of row j (fixed point)
+__global__ void k_resid_fix_finish(const unsigned long long *__restrict__ fix_acc, int64_t n, double *__restrict__ out) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const unsigned long long lo = fix_acc[2 * j], hi = fix_acc[2 * j + 1];
+    const double v = ((double)(long long)hi * 18446744073709551616.0 + (double)lo) * 0x1p-80;
+    out[j] -= v;
 }
 
 __global__ void k_reduce_resid_df(const int32_t *__restrict__ tile_seg, const int2 *__restrict__ tiles,
@@ -304,13 +457,26 @@ void residual_binned_df(rbf_plan *P, const float *bs, const double *xs, double *
     }
     DevBuf<double> part;
     if (pl.any_split) part.alloc((size_t)pl.nseg * kChunk, s);
+    DevBuf<int32_t> tile_of;
+    DevBuf<unsigned long long> fix;
+    tile_of.alloc(P->n, s);
+    fix.alloc(2 * (size_t)P->n, s);
+    fix.zero(s);
+    if (pl.ntiles > 0) {
+        k_tile_of<<<(unsigned)pl.ntiles, kChunk, 0, s>>>(P->tiles.p, tile_of.p);
+        RBF_LAUNCHED();
+    }
     if (pl.nseg > 0) {
-        k_resid_df<<<(unsigned)pl.nseg, kT, 0, s>>>(P->pos.p, P->tiles.p, xs, P->blk.p, pl.ent.p, pl.ebi.p, pl.seg.p,
-                                                    P->n, kc, bs, rs, part.p);
+        k_resid_df_sym<<<(unsigned)pl.nseg, kT, 0, s>>>(P->pos.p, P->tiles.p, xs, P->blk.p, pl.ent.p, pl.ebi.p,
+                                                        pl.seg.p, tile_of.p, kc, bs, rs, part.p, fix.p);
         RBF_LAUNCHED();
     }
     if (pl.any_split) {
         k_reduce_resid_df<<<(unsigned)pl.ntiles, kChunk, 0, s>>>(pl.tile_seg.p, P->tiles.p, part.p, bs, rs);
+        RBF_LAUNCHED();
+    }
+    if (P->n > 0) {
+        k_resid_fix_finish<<<(unsigned)ceil_div(P->n, (int64_t)256), 256, 0, s>>>(fix.p, P->n, rs);
         RBF_LAUNCHED();
     }
 }
