@@ -201,10 +201,14 @@ __device__ __forceinline__ double resid_segment(const float4 *__restrict__ pos, 
 // counted once per row.  Row j's share, sum_i a_ij x_i over this warp's 32 targets, is
 // summed per source in double-float and added to a 128-bit fixed-point accumulator
 // (units of 2^-80) with integer atomics: integer addition is exact, so the result does
-// not depend on the order the CTAs run in.
+// not depend on the order the CTAs run in.  Range: a row's source-side sum, and each
+// warp's share of it, must stay below 2^44 in magnitude (entries are at most 1, so
+// weights below about 1e13 / the row's neighbour count); the truncation below 2^-80
+// costs at most 2^-80 per share.
 constexpr int kFix = 80;
 
-// v 2^kFix as a signed 128-bit integer, truncated toward zero below 2^-kFix (|v| < 2^44)
+// v 2^kFix as a signed 128-bit integer, truncated toward zero below 2^-kFix; shares of
+// 2^44 and above saturate (see the range above)
 __device__ __forceinline__ __int128 to_fix(float v) {
     const unsigned u = __float_as_uint(v);
     const int ex = (int)((u >> 23) & 0xffu);
