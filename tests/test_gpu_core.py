@@ -227,6 +227,24 @@ def test_residual_float64(ctx, rbf, mode):
     assert bn == pytest.approx(np.linalg.norm(b32.astype(np.float64)), rel=1e-12)
 
 
+def test_residual_df_is_bitwise_reproducible(ctx, rbf):
+    """The double-float residual adds the rows' shares from other tiles through integer
+    (fixed-point) atomics, so repeated calls give identical bits whatever order the CTAs
+    run in; and it matches the oracle's float64 residual on sampled rows."""
+    _, C, b = torus_patch(theta=0.3, seed=5)
+    Cd, C64 = c4(C)
+    plan = rbf.Plan(ctx, Cd, sigma=0.02, k=6.0)
+    x = np.random.default_rng(9).standard_normal(len(C))
+    b32 = b.astype(np.float32)
+    r1, _ = plan.residual(dev(b32), dev(x, torch.float64), mode="df")
+    r2, _ = plan.residual(dev(b32), dev(x, torch.float64), mode="df")
+    assert torch.equal(r1, r2)
+    rows = np.random.default_rng(10).choice(len(C), 2000, replace=False)
+    r64 = oracle.residual_rows(C64, b32.astype(np.float64), x, float(F32(0.02)), float(F32(6.0)), rows)
+    scale, _ = oracle.kernel_rows(C64, np.abs(x), float(F32(0.02)), float(F32(6.0)), rows)
+    assert np.abs(r1.cpu().numpy()[rows] - r64).max() <= 1e-12 * scale.max()
+
+
 def test_residual_modes_agree_dense(ctx, rbf, sphere_c1):
     """Double-float and native float64 residuals agree to ~1e-13 of sum |a_ij x_j| on
     the untruncated C1 operator with the oracle's (large, oscillating) weights."""
