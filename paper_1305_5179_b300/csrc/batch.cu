@@ -48,6 +48,8 @@ struct rbf_batch {
     PBuf<double> part_d;
     PBuf<int64_t> part_off_d;
     PBuf<unsigned int> counter;
+    PBuf<int32_t> tile_of;                 // per binned position, its problem's tile
+    PBuf<unsigned long long> fix;          // residual: fixed-point row accumulators (2 words each)
     int persistent_ctas = 0;
     bool tc = false;              // every plan takes the tensor-core product
     int schwarz_block = 0;        // block size of the current Schwarz set-up (0 = none)
@@ -406,6 +408,12 @@ rbf_batch *batch_create(rbf_ctx *ctx, rbf_plan *const *plans, int nplans, cudaSt
         }
         Bt->N = Bt->off[nplans];
         RBF_CHECK(Bt->N < (1LL << 31), RBF_ERR_UNSUPPORTED, "batch of %lld centres (limit 2^31)", (long long)Bt->N);
+        // the residual's symmetric form: each problem's tile of every binned position, and
+        // the fixed-point row accumulators
+        Bt->tile_of.alloc(std::max<int64_t>(Bt->N, 1), s);
+        Bt->fix.alloc(2 * std::max<int64_t>(Bt->N, 1), s);
+        for (int b = 0; b < nplans; ++b)
+            tile_of_launch(plans[b]->tiles.p, plans[b]->pl.ntiles, Bt->tile_of.p + Bt->off[b], s);
         // one segment length for the whole batch: the persistent product balances across problems
         const int64_t seglen = std::max<int64_t>(64, 2 * ceil_div(std::max<int64_t>(total_len, 1),
                                                                   std::max<int64_t>(total_tiles, 1)));
@@ -450,6 +458,7 @@ rbf_batch *batch_create(rbf_ctx *ctx, rbf_plan *const *plans, int nplans, cudaSt
             v.seg = Bt->bseg[b].p;
             v.tile_seg = Bt->btile_seg[b].p;
             v.perm = P->perm.p;
+            v.tile_of = Bt->tile_of.p + Bt->off[b];
             v.partial = splitv[b] ? Bt->part_f.p + poff[b] : nullptr;
             v.n = P->n;
             v.off = Bt->off[b];
@@ -589,7 +598,8 @@ static void batch_solve_body(rbf_batch *Bt, int m, int max_it, bool precond, cud
     while (it < max_it) {
         if (!first) {
             residual_df_batched(Bt->views.p, Bt->seg_items.p, Bt->nseg_items, Bt->split_tiles.p, Bt->nsplit, Bt->bs.p,
-                                Bt->x.p, Bt->r.p, Bt->part_d.p, Bt->part_off_d.p, Bt->ctx->device, s);
+                                Bt->x.p, Bt->r.p, Bt->part_d.p, Bt->part_off_d.p, Bt->fix.p, Bt->N,
+                                Bt->ctx->device, s);
         }
         first = false;
         batch_norm2(Bt, Bt->r.p, Bt->hN.p, s);
@@ -644,7 +654,8 @@ static void batch_solve_body(rbf_batch *Bt, int m, int max_it, bool precond, cud
         it += steps;
     }
     residual_df_batched(Bt->views.p, Bt->seg_items.p, Bt->nseg_items, Bt->split_tiles.p, Bt->nsplit, Bt->bs.p,
-                        Bt->x.p, Bt->r.p, Bt->part_d.p, Bt->part_off_d.p, Bt->ctx->device, s);
+                        Bt->x.p, Bt->r.p, Bt->part_d.p, Bt->part_off_d.p, Bt->fix.p, Bt->N, Bt->ctx->device,
+                        s);
     batch_norm2(Bt, Bt->r.p, Bt->rn2.p, s);
 }
 

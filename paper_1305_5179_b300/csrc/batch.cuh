@@ -14,6 +14,7 @@ struct PlanView {
     const int4 *seg;
     const int32_t *tile_seg;
     const int32_t *perm;
+    const int32_t *tile_of;  // tile of each binned position (this problem's own tile numbers)
     float *partial;        // nseg x kChunk partial sums (split tiles only), or null
     int64_t n;             // centres of this problem
     int64_t off;           // offset of this problem in the concatenated vectors
@@ -37,9 +38,12 @@ void product_tc_prepare(int device);
 // Uploads the exp2 table once per device (synchronises; call before any capture).
 void residual_df_prepare(int device, cudaStream_t s);
 
-// r = b - A~ x for every problem of a batch (double-float), vectors concatenated in
-// binned order.  items: (problem, segment) pairs; splits: (problem, tile) pairs of
-// split tiles.  (residual_df.cu)
+// r = b - A~ x for every problem of a batch (double-float, each pair evaluated once for
+// both rows), vectors concatenated in binned order.  items: (problem, segment) pairs;
+// splits: (problem, tile) pairs of split tiles; fix: 2 x ntotal words of fixed-point
+// accumulator, zeroed here on the stream.  (residual_df.cu)
 void residual_df_batched(const PlanView *views, const int2 *items, int64_t nitems, const int2 *splits,
                          int64_t nsplits, const float *bs, const double *xs, double *rs, double *part_pool,
-                         const int64_t *part_off, int device, cudaStream_t s);
+                         const int64_t *part_off, unsigned long long *fix, int64_t ntotal, int device, cudaStream_t s);
+// tile_of[i] = the tile holding binned position i (tiles of one plan)
+void tile_of_launch(const int2 *tiles, int64_t ntiles, int32_t *tile_of, cudaStream_t s);

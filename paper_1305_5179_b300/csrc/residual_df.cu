@@ -22,7 +22,7 @@
 // Per-term relative error is of order 1e-14.  Pairs beyond the cut-off get a zero
 // scale 2^-e, so their terms are exactly zero; every intermediate stays finite for
 // t below 1e20.  For one plan each pair's entry is evaluated once and serves both of
-// its rows (the symmetric form below); batches use the one-sided form.
+// its rows (the symmetric form below), in a batch within each problem.
 #include <cmath>
 #include <vector>
 
@@ -136,60 +136,6 @@ __device__ __forceinline__ void add_to(df &acc, const df P) {
     const df a2 = two_sum(acc.h, P.h);
     acc.h = a2.h;
     acc.l = __fadd_rn(acc.l, __fadd_rn(a2.l, P.l));
-}
-
-// sum over one staged block of w_j 2^(-t_ij) for the target (px, py, pz); called by
-// every lane of a warp with the same cnt
-__device__ __forceinline__ df block_terms(float px, float py, float pz, const float4 *__restrict__ sp,
-                                          const float2 *__restrict__ sw, int cnt, const DfConst &k,
-                                          const float2 *__restrict__ tab) {
-    df acc = {0.f, 0.f};
-    for (int j = 0; j < cnt; ++j) {
-        const float4 q = sp[j];
-        const float2 w = sw[j];
-        const PairR2 pr = pair_r2(px, py, pz, q, k);
-        // a source beyond the cut-off for every target of the warp adds nothing: skip its
-        // exponential (the loop runs over the same sources on every lane, so the vote is uniform)
-        if (!__any_sync(0xffffffffu, pr.in)) continue;
-        add_to(acc, times_w(pair_exp(pr, k, tab), w));
-    }
-    return acc;
-}
-
-// One segment of one problem: acc over the segment's blocks for target thread.  Warp
-// w holds the tile's targets 32w .. 32w + 31 and walks the segment on its own: it
-// skips a block whose pair-list code for that quarter says no pair is within the
-// cut-off (those terms are zero) and stages the others in its own slice of shared
-// memory (one source per lane), so warps never wait for each other.  s_p and s_w
-// hold 32 entries per warp of the CTA.
-__device__ __forceinline__ double resid_segment(const float4 *__restrict__ pos, const int2 tl, const double *__restrict__ x,
-                                                const int2 *__restrict__ blk, const int32_t *__restrict__ ent,
-                                                const int2 *__restrict__ ebi, const int4 sg, const DfConst &kc,
-                                                float4 *s_p, float2 *s_w, const float2 *s_tab, bool &valid,
-                                                int64_t &i) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int quarter_shift = 8 + 2 * warp;
-    float4 *wp = s_p + 32 * warp;
-    float2 *ww = s_w + 32 * warp;
-    i = (int64_t)tl.x + threadIdx.x;
-    valid = (int)threadIdx.x < tl.y;
-    float4 p = valid ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    double acc = 0.0;
-    for (int e = sg.y; e < sg.z; ++e) {
-        if (ebi && ((ebi[e].y >> quarter_shift) & 3) == 0) continue;
-        const int2 bi = blk[ent[e] & 0x7fffffff];
-        __syncwarp();
-        if (lane < bi.y) {
-            wp[lane] = pos[bi.x + lane];
-            const double xv = x[bi.x + lane];
-            const float xh = (float)xv;
-            ww[lane] = make_float2(xh, (float)(xv - (double)xh));
-        }
-        __syncwarp();
-        df a = block_terms(p.x, p.y, p.z, wp, ww, bi.y, kc, s_tab);
-        acc += (double)a.h + (double)a.l;
-    }
-    return acc;
 }
 
 // ---------------------------------------------------------------- symmetric form
@@ -333,6 +279,56 @@ __global__ void __launch_bounds__(kT) k_resid_df_sym(const float4 *__restrict__ 
     }
 }
 
+// batched: one CTA per (problem, segment), the symmetric form within each problem
+__global__ void __launch_bounds__(kT) k_resid_df_sym_batched(const PlanView *__restrict__ views,
+                                                             const int2 *__restrict__ items, float Lh, float Ll,
+                                                             const float *__restrict__ bs, const double *__restrict__ xs,
+                                                             double *__restrict__ rs, double *__restrict__ pool,
+                                                             const int64_t *__restrict__ poff,
+                                                             unsigned long long *__restrict__ fix) {
+    __shared__ float4 s_p[kT];
+    __shared__ float2 s_w[kT];
+    __shared__ int s_tj[kT];
+    __shared__ float2 s_q[kT / 32][16][33];
+    __shared__ float2 s_tab[kTab];
+    load_table(s_tab);
+    __syncthreads();
+    const int2 it = items[blockIdx.x];
+    const PlanView &v = views[it.x];
+    const int4 sg = v.seg[it.y];
+    DfConst kc;
+    kc.Ch = v.Ch;
+    kc.Cl = v.Cl;
+    kc.Rh = v.Rh;
+    kc.Rl = v.Rl;
+    kc.Lh = Lh;
+    kc.Ll = Ll;
+    bool valid;
+    int64_t i;
+    double acc = resid_segment_sym(v.pos, v.tiles[sg.x], sg.x, xs + v.off, v.blk, v.ent, v.ebi, v.tile_of, sg, kc,
+                                   s_p, s_w, s_tj, s_q[threadIdx.x >> 5], s_tab, fix + 2 * v.off, valid, i);
+    if (sg.w) {
+        if (valid) rs[v.off + i] = (double)bs[v.off + i] - acc;
+    } else {
+        pool[poff[it.x] + (int64_t)it.y * kChunk + threadIdx.x] = acc;
+    }
+}
+
+__global__ void k_reduce_resid_df_batched(const PlanView *__restrict__ views, const int2 *__restrict__ splits,
+                                          const double *__restrict__ pool, const int64_t *__restrict__ poff,
+                                          const float *__restrict__ bs, double *__restrict__ rs) {
+    const int2 it = splits[blockIdx.x];
+    const PlanView &v = views[it.x];
+    int s0 = v.tile_seg[it.y], s1 = v.tile_seg[it.y + 1];
+    const int2 tl = v.tiles[it.y];
+    for (int q = threadIdx.x; q < tl.y; q += blockDim.x) {
+        double acc = 0.0;
+        for (int sidx = s0; sidx < s1; ++sidx) acc += pool[poff[it.x] + (int64_t)sidx * kChunk + q];
+        int64_t i = v.off + tl.x + q;
+        rs[i] = (double)bs[i] - acc;
+    }
+}
+
 // tile_of[i] = the tile holding binned position i
 __global__ void k_tile_of(const int2 *__restrict__ tiles, int32_t *__restrict__ tile_of) {
     const int2 tl = tiles[blockIdx.x];
@@ -364,52 +360,6 @@ __global__ void k_reduce_resid_df(const int32_t *__restrict__ tile_seg, const in
     }
 }
 
-// batched: one CTA per (problem, segment)
-__global__ void __launch_bounds__(kT) k_resid_df_batched(const PlanView *__restrict__ views,
-                                                         const int2 *__restrict__ items, float Lh, float Ll,
-                                                         const float *__restrict__ bs, const double *__restrict__ xs,
-                                                         double *__restrict__ rs, double *__restrict__ pool,
-                                                         const int64_t *__restrict__ poff) {
-    __shared__ float4 s_p[kT];
-    __shared__ float2 s_w[kT];
-    __shared__ float2 s_tab[kTab];
-    load_table(s_tab);
-    __syncthreads();
-    const int2 it = items[blockIdx.x];
-    const PlanView &v = views[it.x];
-    const int4 sg = v.seg[it.y];
-    DfConst kc;
-    kc.Ch = v.Ch;
-    kc.Cl = v.Cl;
-    kc.Rh = v.Rh;
-    kc.Rl = v.Rl;
-    kc.Lh = Lh;
-    kc.Ll = Ll;
-    bool valid;
-    int64_t i;
-    double acc = resid_segment(v.pos, v.tiles[sg.x], xs + v.off, v.blk, v.ent, v.ebi, sg, kc, s_p, s_w, s_tab, valid,
-                               i);
-    if (sg.w) {
-        if (valid) rs[v.off + i] = (double)bs[v.off + i] - acc;
-    } else {
-        pool[poff[it.x] + (int64_t)it.y * kChunk + threadIdx.x] = acc;
-    }
-}
-
-__global__ void k_reduce_resid_df_batched(const PlanView *__restrict__ views, const int2 *__restrict__ splits,
-                                          const double *__restrict__ pool, const int64_t *__restrict__ poff,
-                                          const float *__restrict__ bs, double *__restrict__ rs) {
-    const int2 it = splits[blockIdx.x];
-    const PlanView &v = views[it.x];
-    int s0 = v.tile_seg[it.y], s1 = v.tile_seg[it.y + 1];
-    const int2 tl = v.tiles[it.y];
-    for (int q = threadIdx.x; q < tl.y; q += blockDim.x) {
-        double acc = 0.0;
-        for (int sidx = s0; sidx < s1; ++sidx) acc += pool[poff[it.x] + (int64_t)sidx * kChunk + q];
-        int64_t i = v.off + tl.x + q;
-        rs[i] = (double)bs[i] - acc;
-    }
-}
 
 inline void split(double v, float &h, float &l) {
     h = (float)v;
@@ -433,18 +383,31 @@ void residual_df_prepare(int device, cudaStream_t s) { upload_table(device, s); 
 
 void residual_df_batched(const PlanView *views, const int2 *items, int64_t nitems, const int2 *splits,
                          int64_t nsplits, const float *bs, const double *xs, double *rs, double *part_pool,
-                         const int64_t *part_off, int device, cudaStream_t s) {
+                         const int64_t *part_off, unsigned long long *fix, int64_t ntotal, int device,
+                         cudaStream_t s) {
     upload_table(device, s);
     float Lh, Ll;
     split(0.6931471805599453, Lh, Ll);
+    if (ntotal > 0) RBF_CUDA(cudaMemsetAsync(fix, 0, 2 * (size_t)ntotal * sizeof(unsigned long long), s));
     if (nitems > 0) {
-        k_resid_df_batched<<<(unsigned)nitems, kT, 0, s>>>(views, items, Lh, Ll, bs, xs, rs, part_pool, part_off);
+        k_resid_df_sym_batched<<<(unsigned)nitems, kT, 0, s>>>(views, items, Lh, Ll, bs, xs, rs, part_pool, part_off,
+                                                               fix);
         RBF_LAUNCHED();
     }
     if (nsplits > 0) {
         k_reduce_resid_df_batched<<<(unsigned)nsplits, kChunk, 0, s>>>(views, splits, part_pool, part_off, bs, rs);
         RBF_LAUNCHED();
     }
+    if (ntotal > 0) {
+        k_resid_fix_finish<<<(unsigned)ceil_div(ntotal, (int64_t)256), 256, 0, s>>>(fix, ntotal, rs);
+        RBF_LAUNCHED();
+    }
+}
+
+void tile_of_launch(const int2 *tiles, int64_t ntiles, int32_t *tile_of, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    k_tile_of<<<(unsigned)ntiles, kChunk, 0, s>>>(tiles, tile_of);
+    RBF_LAUNCHED();
 }
 
 void residual_binned_df(rbf_plan *P, const float *bs, const double *xs, double *rs, cudaStream_t s) {
