@@ -11,8 +11,10 @@
 //
 // Per inner step j: Z_j = M^-1 V_j; w = A~ Z_j; two passes of h = V^T w,
 // w -= V h (fused multi-dot and multi-axpy kernels with fixed-order reductions);
-// V_{j+1} = w / |w|.  The column of H is copied to the host (one synchronisation
-// per step) where the rotations are applied.
+// V_{j+1} = w / |w|.  Each step's column of H goes to its own device slot; the host
+// applies the rotations after reading it back, once per step when a tolerance is
+// checked, once per cycle for a fixed iteration count (nothing on the device waits
+// for the host in between).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
