@@ -76,15 +76,15 @@ WORKLOADS = {
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_product_tc launch on the
-# 3,000,000-centre torus, from one ncu capture (profiles/k_product_tc_torus_sector.md gives the
-# command); valid only while the kernel sources hash to the values it was taken with.
+# 3,000,000-centre torus, from one ncu capture of the product on the torus sector, scaled to the
+# full operator; valid only while the kernel sources hash to the values it was taken with.
 PRODUCT_TRAFFIC = {"torus1m": (156.81e6 + 8.98e6, {
     "paper_1305_5179_b300/csrc/product_tc.cu": "9328d403021bb0d483177592c0f0177f86d64a8eb11dec7b8a16950a78928c77",
     "paper_1305_5179_b300/csrc/tcgen05.cuh": "b0f1821451b34e230cdc5000e9e34c3b6ce5dd95aef3f1df5a956d533ea2386e",
     "paper_1305_5179_b300/csrc/product.cuh": "7da831b5eec7623181f7ab2ce78e05d90a3d41ff301a2883871a3679935d138c"})}
 
 # DRAM bytes of one k_spmv_csr launch per byte of its algorithmic traffic, from one ncu capture on
-# the 0.05-radian sector (23,871 centres, 514 MB of CSR; profiles/k_spmv_csr_torus_sector.md):
+# the 0.05-radian sector (23,871 centres, 514 MB of CSR):
 # 524.3 MB measured / 514.2 MB algorithmic.  The product streams the matrix once, so the ratio
 # carries to larger sectors; valid while the kernel source hashes to the value it was taken with.
 SPMV_TRAFFIC_RATIO = (524.297984e6 / 514.242360e6, {

@@ -57,7 +57,9 @@ typedef enum {
     RBF_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired (reported by the next call on the
                                    context that launches a product or synchronises) */
     RBF_ERR_NOT_SPD = 7,        /* a block factorisation failed even after the shift escalation */
-    RBF_ERR_UNSUPPORTED = 8     /* configuration outside the implemented range (message says which) */
+    RBF_ERR_UNSUPPORTED = 8,    /* configuration outside the implemented range (message says which) */
+    RBF_ERR_RANGE = 9           /* a device-side value left a documented range (message says which);
+                                   reported like RBF_ERR_TIMEOUT, results of that launch invalid */
 } rbf_status;
 
 typedef struct rbf_ctx rbf_ctx;
@@ -76,7 +78,9 @@ const char *rbf_status_string(rbf_status s);
 /* Create a context on CUDA device `device` (made current for every call on the
  * context).  *ctx receives a host-owned handle; destroy it with rbf_ctx_destroy,
  * after the plans, batches and networks made on it (their destroy functions do
- * not touch the context; every other call on them does). */
+ * not touch the context; every other call on them does).  The first context on
+ * a device also loads the allocation-free product's code and its 4 MiB scratch
+ * array (see rbf_matvec_dense_noalloc), which stay until the process exits. */
 rbf_status rbf_ctx_create(rbf_ctx **ctx, int device);
 rbf_status rbf_ctx_destroy(rbf_ctx *ctx);
 
@@ -108,13 +112,23 @@ rbf_status rbf_build_centers(rbf_ctx *ctx, const float *pts, const float *nrm, i
  *
  * Binning is a definition shared with the tests:
  *   lo = componentwise minimum of the centres, ext = hi - lo (float32);
- *   cell edge hc = k sigma / cells_per_cutoff (k > 0), or
- *   max(min(max(ext)/8, 3 sigma), max(ext)/128) in double (k = 0, Gaussian), max(ext)/8
- *   (k = 0, inverse multiquadric); 1 if ext is 0; fine cells hf = hc / 2^levels; inv = (float)(2^levels / hc)
- *   computed in double; q_d = floor((c_d - lo_d) * inv) in float32;
+ *   cell edge hc = cell_edge when cell_edge > 0; otherwise k sigma /
+ *   cells_per_cutoff (k > 0, the truncation area of Algorithm 2), or the
+ *   layout choice max(min(max(ext)/8, 3 sigma), max(ext)/128) in double (k = 0,
+ *   Gaussian), max(ext)/8 (k = 0, inverse multiquadric); 1 if ext is 0;
+ *   fine cells hf = hc / 2^levels; inv = (float)(2^levels / hc) computed in
+ *   double; q_d = floor((c_d - lo_d) * inv) in float32;
  *   key = Morton interleave (x in bit 0) of q; cell = key >> (3 levels);
  *   centres are ordered by a stable sort on key.  At most 1024 fine cells per
- *   axis (RBF_ERR_UNSUPPORTED otherwise).
+ *   axis (RBF_ERR_UNSUPPORTED otherwise).  Any positive cell edge gives the
+ *   same operator: the kernels enumerate every cell within the cut-off.
+ * After the sort, the centres of each cell are reordered among themselves
+ * (an internal layout, not part of the definition): runs of at most 4096
+ * consecutive positions counted from the cell start are split recursively at
+ * a median along the axis of largest extent, so that the runs of 32 (source
+ * blocks) and of 128 (target tiles) counted from the cell start are subtrees:
+ * any two such runs of one 4096-run are separated along some axis (the
+ * largest coordinate of one is <= the smallest of the other).
  * ------------------------------------------------------------------------ */
 typedef struct {
     float sigma;            /* Gaussian width, > 0 */
@@ -126,6 +140,7 @@ typedef struct {
     int kernel;             /* radial function: RBF_KERNEL_GAUSSIAN (0, the paper's choice) or
                                RBF_KERNEL_IMQ (1), see below */
     float beta;             /* RBF_KERNEL_IMQ: exponent, 0 < beta <= 16 */
+    float cell_edge;        /* cell edge hc of the binning; 0 selects the default rule above; finite, >= 0 */
 } rbf_plan_params;
 
 /* Radial functions (Table I).  The Gaussian exp(-r^2 / (2 sigma^2)) is the
@@ -157,6 +172,7 @@ typedef struct {
     float lo[3];
     float inv;              /* fine cells per unit length (float32) */
     float sigma, k;
+    double cell_edge;       /* the cell edge hc used (double, before inv is rounded) */
 } rbf_plan_info;
 
 /* Build a plan over n centres (device float4 array, caller order).  The plan
@@ -174,7 +190,8 @@ rbf_status rbf_plan_get_info(const rbf_plan *plan, rbf_plan_info *info);
 
 /* Copy the binning out (device pointers, any may be NULL):
  *   perm       : n int32, perm[p] = caller index of the centre at binned position p
- *   keys       : n uint32, Morton key of binned position p (sorted, stable)
+ *   keys       : n uint32, Morton key of binned position p (sorted by cell; the
+ *                order inside a cell is the layout described above)
  *   cell_start : ncells int32, first binned position of each cell code
  *   cell_end   : ncells int32, one past the last (start == end == 0 when empty) */
 rbf_status rbf_plan_export_binning(rbf_plan *plan, int32_t *perm, uint32_t *keys, int32_t *cell_start,
@@ -545,9 +562,11 @@ rbf_status rbf_batch_autotune(rbf_batch *batch, const float *b, const rbf_solve_
  * The call allocates nothing (no cudaMalloc, cudaFree or allocating library
  * routine).  Its scratch is a 4 MiB file-scope device array (32 x 32768 float
  * partial sums) that every GPU loading the library holds until the process
- * exits.  The first call on each device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current; make that first call before
- * any stream capture.  All calls share the array and it keeps the last call's
+ * exits.  It is allocated when the module holding it loads, which
+ * rbf_ctx_create forces (it also resolves the array's device address with
+ * cudaGetSymbolAddress, with the context's device current, and loads the two
+ * kernels), so the device memory is taken then and never by a call; create
+ * the context before any stream capture.  All calls share the array and it keeps the last call's
  * contents; every entry a call reads is written earlier in the same call, so
  * nothing needs clearing, but calls whose work overlaps on the GPU (different
  * streams, or different host threads) race on it and must be serialised by the

@@ -307,37 +307,33 @@ def morton3(qx, qy, qz) -> np.ndarray:
     return (part1by2(qx) | (part1by2(qy) << np.uint64(1)) | (part1by2(qz) << np.uint64(2))).astype(np.uint32)
 
 
-def binning(C32: np.ndarray, sigma: float, k: float, cells_per_cutoff: int = 1, levels: int = 3,
-            kd_leaf: int = 32, kd_tile: int = 128, kd_chunk: int = 4096):
-    """Cell binning of the centres in FP32, as a definition.
+def truncation_cell_edge(sigma: float, k: float, cells_per_cutoff: int = 1) -> float:
+    """Cell edge r_c / s with r_c = k sigma (the truncation area of Algorithm 2,
+    Sec. III.A), from float32 sigma and k, in double."""
+    return float(np.float32(k)) * float(np.float32(sigma)) / float(cells_per_cutoff)
+
+
+def binning(C32: np.ndarray, cell_edge: float, levels: int = 3):
+    """Cell binning of the centres in FP32, as a definition (the truncation area
+    of Algorithm 2 made concrete: centres are grouped by cells of edge
+    ``cell_edge``, each subdivided into 2^levels fine cells per axis).
 
     * lo = componentwise minimum of the centres; ext = hi - lo (FP32);
-    * cell edge hc = k sigma / s (k > 0), or max(min(max(ext)/8, 3 sigma), max(ext)/128)
-      (k = 0; 1 if ext is 0);
-    * fine edge hf = hc / 2^L, inv = float32(2^L / hc) computed in double;
+    * inv = float32(2^L / cell_edge) computed in double;
     * q_d = floor((c_d - lo_d) * inv) in float32 arithmetic;
     * nbits = max(L, bit length of max_d floor(ext_d * inv)) (must be <= 10);
     * key = Morton interleave of (q_x, q_y, q_z); cell = key >> 3L;
-    * stable sort of the centres by key;
-    * then, inside every cell, consecutive runs of at most ``kd_chunk`` centres
-      (counted from the cell start) are reordered by recursive median splits
-      (``_kd_order``) so that the runs of ``kd_tile`` (target tiles) and
-      ``kd_leaf`` (source blocks) counted from the cell start are compact k-d
-      subtrees (cells stay contiguous; ``keys_sorted`` is then sorted by cell only).
-    Returns dict(perm, keys_sorted, cell_of_sorted, cell_start, cell_end (dense
-    tables over 2^(3(nbits-L)) cell codes), nbits, inv, lo).
-    """
+    * stable sort of the centres by key; cell start/end over the sorted order.
+    The cell edge is a parameter (``truncation_cell_edge`` gives r_c / s).
+    Returns dict(perm, keys_sorted, key (per input centre), cell_of_sorted,
+    cell_start, cell_end (dense tables over 2^(3(nbits-L)) cell codes), nbits,
+    inv, lo)."""
     c = np.ascontiguousarray(C32[:, :3], dtype=np.float32)
     lo = c.min(0)
     hi = c.max(0)
     ext = (hi - lo).astype(np.float32)
     L = int(levels)
-    if k > 0:
-        hc = float(np.float32(k)) * float(np.float32(sigma)) / float(cells_per_cutoff)
-    else:
-        m = float(ext.max())
-        hc = max(min(m / 8.0, 3.0 * float(np.float32(sigma))), m / 128.0) if m > 0 else 1.0
-    inv = np.float32((2.0 ** L) / hc)
+    inv = np.float32((2.0 ** L) / float(cell_edge))
     qmax = int(np.floor(ext * inv).max()) if len(c) else 0
     nbits = max(L, int(qmax).bit_length())
     if nbits > 10:
@@ -358,44 +354,8 @@ def binning(C32: np.ndarray, sigma: float, k: float, cells_per_cutoff: int = 1, 
         last[:-1] = cell[1:] != cell[:-1]
         start[cell[first]] = np.nonzero(first)[0]
         end[cell[last]] = np.nonzero(last)[0] + 1
-    if kd_leaf:
-        perm = perm.astype(np.int64)
-        for cs, ce in zip(start, end):
-            if ce <= cs:
-                continue
-            for c0 in range(int(cs), int(ce), kd_chunk):
-                c1 = min(int(ce), c0 + kd_chunk)
-                perm[c0:c1] = perm[c0:c1][_kd_order(c[perm[c0:c1]], kd_leaf, kd_tile)]
-        ks = key[perm]
-    return dict(perm=perm.astype(np.int64), keys_sorted=ks, cell_of_sorted=cell,
+    return dict(perm=perm.astype(np.int64), keys_sorted=ks, key=key, cell_of_sorted=cell,
                 cell_start=start, cell_end=end, nbits=nbits, inv=inv, lo=lo)
-
-
-def _kd_order(P: np.ndarray, leaf: int, tile: int) -> np.ndarray:
-    """Order of the rows of P (float32, m x 3) after recursive splits: a run longer
-    than ``leaf`` is split along the axis of its largest float32 extent (first of
-    x, y, z on ties) so that the left part holds the u * ceil(ceil(len/u)/2)
-    smallest coordinates, u = ``tile`` for runs longer than ``tile`` and ``leaf``
-    otherwise (ties keep the current order); runs of <= leaf stop.  Runs of
-    ``tile`` and ``leaf`` counted from the start are then subtrees."""
-    order = np.arange(len(P))
-    stack = [(0, len(P))]
-    while stack:
-        s, e = stack.pop()
-        m = e - s
-        if m <= leaf:
-            continue
-        q = P[order[s:e]]
-        ext = (q.max(0) - q.min(0)).astype(np.float32)
-        axis = int(np.argmax(ext))                 # first maximum: x before y before z
-        col = q[:, axis] + np.float32(0.0)         # -0 and +0 compare equal
-        sub = np.argsort(col, kind="stable")
-        order[s:e] = order[s:e][sub]
-        u = tile if m > tile else leaf
-        left = u * ((-(-m // u) + 1) // 2)
-        stack.append((s + left, e))
-        stack.append((s, s + left))
-    return order
 
 
 # --------------------------------------------------------------------------

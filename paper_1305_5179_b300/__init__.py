@@ -25,7 +25,8 @@ LIBPATH = os.path.join(HERE, "librbf.so")
 
 RBF_OK = 0
 STATUS = {0: "RBF_OK", 1: "RBF_ERR_INVALID", 2: "RBF_ERR_OOM", 3: "RBF_ERR_CUDA", 4: "RBF_ERR_NOT_CONVERGED",
-          5: "RBF_ERR_BREAKDOWN", 6: "RBF_ERR_TIMEOUT", 7: "RBF_ERR_NOT_SPD", 8: "RBF_ERR_UNSUPPORTED"}
+          5: "RBF_ERR_BREAKDOWN", 6: "RBF_ERR_TIMEOUT", 7: "RBF_ERR_NOT_SPD", 8: "RBF_ERR_UNSUPPORTED",
+          9: "RBF_ERR_RANGE"}
 PRECOND = {"none": 0, "schwarz": 1, "mlp": 2}
 RESIDUAL = {"df": 0, "f64": 1}
 
@@ -57,15 +58,16 @@ class RbfError(RuntimeError):
 class PlanParams(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_float), ("k", ctypes.c_float), ("cells_per_cutoff", ctypes.c_int),
                 ("levels", ctypes.c_int), ("product", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("beta", ctypes.c_float)]
+                ("beta", ctypes.c_float), ("cell_edge", ctypes.c_float)]
 
 
 KERNELS = {"gaussian": 0, "imq": 1}
 
 
-def _plan_params(sigma, k, cells_per_cutoff=1, levels=3, product="tc", kernel="gaussian", beta=0.0):
+def _plan_params(sigma, k, cells_per_cutoff=1, levels=3, product="tc", kernel="gaussian", beta=0.0,
+                 cell_edge=0.0):
     return PlanParams(float(sigma), float(k), int(cells_per_cutoff), int(levels), PRODUCTS[product],
-                      KERNELS[kernel], float(beta))
+                      KERNELS[kernel], float(beta), float(cell_edge))
 
 
 PRODUCTS = {"tc": 0, "simt": 1}
@@ -75,7 +77,8 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("ncells", ctypes.c_int64), ("nblocks", ctypes.c_int64),
                 ("nchunks", ctypes.c_int64), ("pairlist_len", ctypes.c_int64), ("nsegments", ctypes.c_int64),
                 ("nbits", ctypes.c_int), ("levels", ctypes.c_int), ("lo", ctypes.c_float * 3),
-                ("inv", ctypes.c_float), ("sigma", ctypes.c_float), ("k", ctypes.c_float)]
+                ("inv", ctypes.c_float), ("sigma", ctypes.c_float), ("k", ctypes.c_float),
+                ("cell_edge", ctypes.c_double)]
 
 
 class SchwarzParams(ctypes.Structure):
@@ -365,8 +368,10 @@ class Plan:
     """The matrix-free truncated Gaussian operator over a fixed set of centres."""
 
     def __init__(self, ctx: Context, centers, sigma: float, k: float = 0.0, cells_per_cutoff: int = 1,
-                 levels: int = 3, product: str = "tc", kernel: str = "gaussian", beta: float = 0.0, stream=None):
-        """kernel "gaussian" (exp(-r^2/(2 sigma^2))) or "imq" ((1 + r^2/sigma^2)^-beta, Table I)."""
+                 levels: int = 3, product: str = "tc", kernel: str = "gaussian", beta: float = 0.0,
+                 cell_edge: float = 0.0, stream=None):
+        """kernel "gaussian" (exp(-r^2/(2 sigma^2))) or "imq" ((1 + r^2/sigma^2)^-beta, Table I);
+        cell_edge > 0 fixes the binning's cell edge (0: the default rule)."""
         import torch
         _req(centers, torch.float32, "centers")
         if centers.dim() != 2 or centers.shape[1] != 4:
@@ -374,7 +379,7 @@ class Plan:
         self.ctx = ctx
         self.n = int(centers.shape[0])
         self.device = centers.device
-        self.params = _plan_params(sigma, k, cells_per_cutoff, levels, product, kernel, beta)
+        self.params = _plan_params(sigma, k, cells_per_cutoff, levels, product, kernel, beta, cell_edge)
         self._h = ctypes.c_void_p()
         ctx.check(lib().rbf_plan_create(ctx._h, _ptr(centers), self.n, ctypes.byref(self.params),
                                         ctypes.byref(self._h), _stream(stream)), "rbf_plan_create")

@@ -56,6 +56,8 @@ void check_plan_params(const rbf_plan_params *p) {
               "kernel must be RBF_KERNEL_GAUSSIAN or RBF_KERNEL_IMQ");
     RBF_CHECK(p->kernel != RBF_KERNEL_IMQ || (std::isfinite(p->beta) && p->beta > 0.f && p->beta <= 16.f),
               RBF_ERR_INVALID, "inverse multiquadric beta must be in (0, 16]");
+    RBF_CHECK(std::isfinite(p->cell_edge) && p->cell_edge >= 0.f, RBF_ERR_INVALID,
+              "cell_edge must be finite and >= 0 (0 selects the default)");
 }
 
 }  // namespace
@@ -63,9 +65,13 @@ void check_plan_params(const rbf_plan_params *p) {
 unsigned *ctx_error_word(rbf_ctx *ctx) { return ctx->err_dev; }
 
 void ctx_check_device_error(rbf_ctx *ctx) {
-    if (ctx->err_host && *(volatile unsigned *)ctx->err_host) {
+    const unsigned w = ctx->err_host ? *(volatile unsigned *)ctx->err_host : 0u;
+    if (w) {
         *(volatile unsigned *)ctx->err_host = 0u;
-        rbf_fail(RBF_ERR_TIMEOUT, "a bounded wait inside a product kernel expired (results of that launch invalid)");
+        if (w & kErrTimeout)
+            rbf_fail(RBF_ERR_TIMEOUT, "a bounded wait inside a product kernel expired (results of that launch invalid)");
+        rbf_fail(RBF_ERR_RANGE, "double-float true residual: a row's share exceeded the fixed-point accumulator's "
+                                "range (weights too large; residual_mode = RBF_RESIDUAL_F64 has no such limit)");
     }
 }
 
@@ -87,6 +93,7 @@ rbf_plan *make_plan(rbf_ctx *ctx, const float *centers, int64_t n, const rbf_pla
         P->product = p->product;
         P->kernel = p->kernel;
         P->beta = p->kernel == RBF_KERNEL_IMQ ? p->beta : 0.f;
+        P->cell_edge = p->cell_edge;
         plan_build(P, (const float4 *)centers, s);
     } catch (...) {
         delete P;
@@ -114,6 +121,7 @@ const char *rbf_status_string(rbf_status s) {
         case RBF_ERR_TIMEOUT: return "RBF_ERR_TIMEOUT";
         case RBF_ERR_NOT_SPD: return "RBF_ERR_NOT_SPD";
         case RBF_ERR_UNSUPPORTED: return "RBF_ERR_UNSUPPORTED";
+        case RBF_ERR_RANGE: return "RBF_ERR_RANGE";
     }
     return "RBF_UNKNOWN_STATUS";
 }
@@ -132,7 +140,8 @@ rbf_status rbf_ctx_create(rbf_ctx **ctx, int device) {
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaHostAlloc((void **)&c->err_host, sizeof(unsigned), cudaHostAllocMapped) != cudaSuccess ||
-        cudaHostGetDevicePointer((void **)&c->err_dev, c->err_host, 0) != cudaSuccess) {
+        cudaHostGetDevicePointer((void **)&c->err_dev, c->err_host, 0) != cudaSuccess ||
+        noalloc_prepare(c) != cudaSuccess) {
         if (c->err_host) cudaFreeHost(c->err_host);
         (void)cudaGetLastError();
         delete c;
@@ -198,6 +207,7 @@ rbf_status rbf_plan_get_info(const rbf_plan *P, rbf_plan_info *info) {
     info->levels = P->levels;
     for (int d = 0; d < 3; ++d) info->lo[d] = P->lo[d];
     info->inv = P->inv;
+    info->cell_edge = P->hc;
     info->sigma = P->sigma;
     info->k = P->k;
     return RBF_OK;
@@ -288,6 +298,7 @@ rbf_status rbf_residual(rbf_plan *P, const float *b, const double *x, double *r,
             }
             norms[0] = std::sqrt(a);
             norms[1] = std::sqrt(c);
+            ctx_check_device_error(P->ctx);
         }
         return RBF_OK;
     });

@@ -32,6 +32,7 @@ using rbfk::Stage;
 struct rbf_batch {
     rbf_ctx *ctx = nullptr;
     std::vector<rbf_plan *> plans;
+    int64_t max_tiles = 0;          // largest tile count of a problem (the residual's share limit)
     int nb = 0;
     int64_t N = 0;
     std::vector<int64_t> off;
@@ -405,6 +406,7 @@ rbf_batch *batch_create(rbf_ctx *ctx, rbf_plan *const *plans, int nplans, cudaSt
             Bt->off[b + 1] = Bt->off[b] + plans[b]->n;
             total_len += plans[b]->pl.len;
             total_tiles += plans[b]->pl.ntiles;
+            Bt->max_tiles = std::max<int64_t>(Bt->max_tiles, plans[b]->pl.ntiles);
         }
         Bt->N = Bt->off[nplans];
         RBF_CHECK(Bt->N < (1LL << 31), RBF_ERR_UNSUPPORTED, "batch of %lld centres (limit 2^31)", (long long)Bt->N);
@@ -599,7 +601,7 @@ static void batch_solve_body(rbf_batch *Bt, int m, int max_it, bool precond, cud
         if (!first) {
             residual_df_batched(Bt->views.p, Bt->seg_items.p, Bt->nseg_items, Bt->split_tiles.p, Bt->nsplit, Bt->bs.p,
                                 Bt->x.p, Bt->r.p, Bt->part_d.p, Bt->part_off_d.p, Bt->fix.p, Bt->N,
-                                Bt->ctx->device, s);
+                                Bt->max_tiles, ctx_error_word(Bt->ctx), Bt->ctx->device, s);
         }
         first = false;
         batch_norm2(Bt, Bt->r.p, Bt->hN.p, s);
@@ -654,8 +656,8 @@ static void batch_solve_body(rbf_batch *Bt, int m, int max_it, bool precond, cud
         it += steps;
     }
     residual_df_batched(Bt->views.p, Bt->seg_items.p, Bt->nseg_items, Bt->split_tiles.p, Bt->nsplit, Bt->bs.p,
-                        Bt->x.p, Bt->r.p, Bt->part_d.p, Bt->part_off_d.p, Bt->fix.p, Bt->N, Bt->ctx->device,
-                        s);
+                        Bt->x.p, Bt->r.p, Bt->part_d.p, Bt->part_off_d.p, Bt->fix.p, Bt->N, Bt->max_tiles,
+                        ctx_error_word(Bt->ctx), Bt->ctx->device, s);
     batch_norm2(Bt, Bt->r.p, Bt->rn2.p, s);
 }
 

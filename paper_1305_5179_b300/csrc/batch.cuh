@@ -44,6 +44,7 @@ void residual_df_prepare(int device, cudaStream_t s);
 // accumulator, zeroed here on the stream.  (residual_df.cu)
 void residual_df_batched(const PlanView *views, const int2 *items, int64_t nitems, const int2 *splits,
                          int64_t nsplits, const float *bs, const double *xs, double *rs, double *part_pool,
-                         const int64_t *part_off, unsigned long long *fix, int64_t ntotal, int device, cudaStream_t s);
+                         const int64_t *part_off, unsigned long long *fix, int64_t ntotal, int64_t max_tiles,
+                         unsigned *err, int device, cudaStream_t s);
 // tile_of[i] = the tile holding binned position i (tiles of one plan)
 void tile_of_launch(const int2 *tiles, int64_t ntiles, int32_t *tile_of, cudaStream_t s);

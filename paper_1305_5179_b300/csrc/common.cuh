@@ -19,10 +19,22 @@ struct rbf_ctx {
     // set it when a wait expires; the host reads it without a copy.
     unsigned *err_host = nullptr;
     unsigned *err_dev = nullptr;
+    // Device address of the allocation-free product's file-scope scratch array,
+    // resolved once when the context is created (noalloc.cu).
+    float *noalloc_scratch = nullptr;
 };
 
+// noalloc.cu: with the context's device current, load the module that holds the
+// allocation-free product (its scratch array is allocated by that load) and its
+// kernels, and store the scratch array's device address in the context.
+cudaError_t noalloc_prepare(rbf_ctx *ctx);
+
 // The context's device error word (device pointer), and the host-side check that
-// turns a raised word into RBF_ERR_TIMEOUT (clearing it).
+// turns a raised word into a status (clearing it): kErrTimeout (a bounded wait
+// expired) -> RBF_ERR_TIMEOUT, kErrRange (a value beyond a documented range) ->
+// RBF_ERR_RANGE.  Kernels raise bits with atomicOr.
+constexpr unsigned kErrTimeout = 1u;
+constexpr unsigned kErrRange = 2u;
 unsigned *ctx_error_word(rbf_ctx *ctx);
 void ctx_check_device_error(rbf_ctx *ctx);
 // probe.cu: one bounded wait that expires and raises *err (failure-detection check).

@@ -328,6 +328,7 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
         RBF_LAUNCHED();
         RBF_CUDA(cudaMemcpyAsync(&beta, scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
         RBF_CUDA(cudaStreamSynchronize(s));
+        ctx_check_device_error(P->ctx);   // a true residual out of range, or an expired wait
         true_rel = beta / bnorm;
         if (!std::isfinite(beta)) {
             breakdown = true;

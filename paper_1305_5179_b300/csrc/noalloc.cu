@@ -8,8 +8,12 @@
 // plan, allocates nothing, and keeps its only scratch - the per-segment
 // partial sums of the split over sources - in the file-scope device array
 // below, which every GPU that loads the library holds until the process exits.
+//
+// Modules load lazily, and loading this file's module is what allocates the
+// array, so the context does it when it is created (noalloc_prepare): it loads
+// the module and both kernels and keeps the array's device address.  A call
+// then only launches.
 #include <cmath>
-#include <mutex>
 
 #include "common.cuh"
 
@@ -22,12 +26,6 @@ constexpr int kThreads = 128;                       // targets per CTA
 
 // 32 x 32768 floats = 4 MiB: partial sums [segment][target].
 static __device__ __align__(256) float g_noalloc_partial[kMaxSegs * kNoAllocMaxN];
-
-// Device address of g_noalloc_partial per device, filled on the first call made
-// with that device current (the name is only a host-side stand-in).
-constexpr int kMaxDevices = 64;
-float *g_scratch_ptr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mu;
 
 __global__ void __launch_bounds__(kThreads) k_dense_noalloc(const float4 *__restrict__ C, const float *__restrict__ z,
                                                             int n, float c, float *__restrict__ part) {
@@ -66,6 +64,22 @@ __global__ void k_dense_noalloc_reduce(const float *__restrict__ part, int n, in
 
 }  // namespace
 
+cudaError_t noalloc_prepare(rbf_ctx *ctx) {
+    // the name g_noalloc_partial is only a host-side stand-in: a kernel needs the
+    // device address, which depends on the device current here
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_partial);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_dense_noalloc);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_dense_noalloc_reduce);
+    if (e != cudaSuccess || !ptr) {
+        (void)cudaGetLastError();
+        return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+    }
+    ctx->noalloc_scratch = (float *)ptr;
+    return cudaSuccess;
+}
+
 extern "C" rbf_status rbf_matvec_dense_noalloc(rbf_ctx *ctx, const float *centers, int64_t n, float sigma,
                                                const float *z, float *y, void *stream) {
     if (!ctx) return RBF_ERR_INVALID;
@@ -86,26 +100,15 @@ extern "C" rbf_status rbf_matvec_dense_noalloc(rbf_ctx *ctx, const float *center
         return n <= 0 ? RBF_ERR_INVALID : RBF_ERR_UNSUPPORTED;
     }
     cudaError_t e = cudaSetDevice(ctx->device);
-    if (e == cudaSuccess && (ctx->device < 0 || ctx->device >= kMaxDevices)) e = cudaErrorInvalidDevice;
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         ctx->last_error = std::string("device selection: ") + cudaGetErrorString(e);
         return RBF_ERR_CUDA;
     }
-    float *part = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_scratch_mu);
-        if (!g_scratch_ptr[ctx->device]) {
-            void *ptr = nullptr;
-            e = cudaGetSymbolAddress(&ptr, g_noalloc_partial);
-            if (e != cudaSuccess || !ptr) {
-                (void)cudaGetLastError();
-                ctx->last_error = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-                return RBF_ERR_CUDA;
-            }
-            g_scratch_ptr[ctx->device] = (float *)ptr;
-        }
-        part = g_scratch_ptr[ctx->device];
+    float *part = ctx->noalloc_scratch;          // resolved when the context was created
+    if (!part) {
+        ctx->last_error = "the allocation-free scratch was not resolved for this context";
+        return RBF_ERR_CUDA;
     }
     const int nn = (int)n;
     const int nseg = (nn + kSegLen - 1) / kSegLen;

@@ -671,7 +671,9 @@ void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s, bool binning
     float ext[3];
     for (int d = 0; d < 3; ++d) ext[d] = P->hi[d] - P->lo[d];
     double hc;
-    if (P->k > 0.f) {
+    if (P->cell_edge > 0.f) {
+        hc = (double)P->cell_edge;
+    } else if (P->k > 0.f) {
         hc = (double)P->k * (double)P->sigma / (double)P->cells_per_cutoff;
     } else if (P->kernel == RBF_KERNEL_IMQ) {
         // untruncated inverse multiquadric: every pair is evaluated, 8 cells per axis suffice
@@ -683,6 +685,7 @@ void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s, bool binning
         double m = std::max({(double)ext[0], (double)ext[1], (double)ext[2]});
         hc = m > 0 ? std::max(std::min(m / 8.0, 3.0 * (double)P->sigma), m / 128.0) : 1.0;
     }
+    P->hc = hc;
     P->inv = (float)(std::ldexp(1.0, P->levels) / hc);
     float qmaxf = 0.f;
     for (int d = 0; d < 3; ++d) qmaxf = std::max(qmaxf, std::floor(ext[d] * P->inv));

@@ -69,6 +69,8 @@ struct rbf_plan {
     int product = RBF_PRODUCT_TC;   // kernel of the float32 product and grid evaluation
     int kernel = RBF_KERNEL_GAUSSIAN;
     float beta = 0.f;               // inverse multiquadric exponent
+    float cell_edge = 0.f;          // requested cell edge (0: the default rule)
+    double hc = 0.0;                // cell edge used
     float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     float inv = 0.f;          // fine cells per unit length
     int cdim = 0;             // cells per axis in the cell table (2^(nbits - levels))

@@ -182,7 +182,7 @@ __global__ void k_expiring_wait(unsigned *err, unsigned long long limit_ns) {
         tc5::mbar_init_fence();
     }
     __syncthreads();
-    if (threadIdx.x == 0 && !tc5::mbar_wait(&bar, 0u, &abort_flag, limit_ns)) atomicOr(err, 1u);
+    if (threadIdx.x == 0 && !tc5::mbar_wait(&bar, 0u, &abort_flag, limit_ns)) atomicOr(err, kErrTimeout);
 }
 
 }  // namespace

@@ -23,6 +23,7 @@
 // scale 2^-e, so their terms are exactly zero; every intermediate stays finite for
 // t below 1e20.  For one plan each pair's entry is evaluated once and serves both of
 // its rows (the symmetric form below), in a batch within each problem.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -147,11 +148,19 @@ __device__ __forceinline__ void add_to(df &acc, const df P) {
 // counted once per row.  Row j's share, sum_i a_ij x_i over this warp's 32 targets, is
 // summed per source in double-float and added to a 128-bit fixed-point accumulator
 // (units of 2^-80) with integer atomics: integer addition is exact, so the result does
-// not depend on the order the CTAs run in.  Range: a row's source-side sum, and each
-// warp's share of it, must stay below 2^44 in magnitude (entries are at most 1, so
-// weights below about 1e13 / the row's neighbour count); the truncation below 2^-80
-// costs at most 2^-80 per share.
+// not depend on the order the CTAs run in.  Range: the signed 128-bit accumulator holds
+// magnitudes below 2^47, and a row receives at most one share per (tile, warp), i.e.
+// at most 4 ntiles shares.  Every share is therefore checked against
+// lim = min(2^44, 2^46 / (4 ntiles)): a larger share raises kErrRange in the context's
+// error word (the call reports RBF_ERR_RANGE) instead of wrapping silently.  Entries are
+// at most 1, so lim bounds 32 x max |x_i| from above.  The truncation below 2^-80 costs
+// at most 2^-80 per share.
 constexpr int kFix = 80;
+
+float fix_share_limit(int64_t ntiles) {
+    const double lim = std::ldexp(1.0, 46) / (4.0 * (double)(ntiles > 0 ? ntiles : 1));
+    return (float)std::min(lim, std::ldexp(1.0, 44));
+}
 
 // v 2^kFix as a signed 128-bit integer, truncated toward zero below 2^-kFix; shares of
 // 2^44 and above saturate (see the range above)
@@ -182,7 +191,8 @@ __device__ __forceinline__ double resid_segment_sym(const float4 *__restrict__ p
                                                     const int32_t *__restrict__ tile_of, const int4 sg,
                                                     const DfConst &kc, float4 *s_p, float2 *s_w, int *s_tj,
                                                     float2 (*qs)[33], const float2 *s_tab,
-                                                    unsigned long long *__restrict__ fix_acc, bool &valid, int64_t &i) {
+                                                    unsigned long long *__restrict__ fix_acc, float fix_lim,
+                                                    unsigned *err, bool &valid, int64_t &i) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int quarter_shift = 8 + 2 * warp;
     float4 *wp = s_p + 32 * warp;
@@ -244,7 +254,10 @@ __device__ __forceinline__ double resid_segment_sym(const float4 *__restrict__ p
                 const df other = {__shfl_down_sync(0xffffffffu, cs.h, 16), __shfl_down_sync(0xffffffffu, cs.l, 16)};
                 if (lane < 16 && ((symmask >> c) & 1u)) {
                     add_to(cs, other);
-                    atomic_add_fix(fix_acc + 2 * (bi.x + h0 + c), to_fix(cs.h) + to_fix(cs.l));
+                    if (fabsf(cs.h) < fix_lim)     // NaN fails too
+                        atomic_add_fix(fix_acc + 2 * (bi.x + h0 + c), to_fix(cs.h) + to_fix(cs.l));
+                    else if (err)
+                        atomicOr(err, kErrRange);
                 }
                 __syncwarp();
             }
@@ -259,7 +272,8 @@ __global__ void __launch_bounds__(kT) k_resid_df_sym(const float4 *__restrict__ 
                                                      const int32_t *__restrict__ ent, const int2 *__restrict__ ebi,
                                                      const int4 *__restrict__ seg, const int32_t *__restrict__ tile_of,
                                                      DfConst kc, const float *__restrict__ b, double *__restrict__ out,
-                                                     double *__restrict__ part, unsigned long long *__restrict__ fix_acc) {
+                                                     double *__restrict__ part, unsigned long long *__restrict__ fix_acc,
+                                                     float fix_lim, unsigned *err) {
     __shared__ float4 s_p[kT];
     __shared__ float2 s_w[kT];
     __shared__ int s_tj[kT];
@@ -271,7 +285,7 @@ __global__ void __launch_bounds__(kT) k_resid_df_sym(const float4 *__restrict__ 
     bool valid;
     int64_t i;
     double acc = resid_segment_sym(pos, tiles[sg.x], sg.x, x, blk, ent, ebi, tile_of, sg, kc, s_p, s_w, s_tj,
-                                   s_q[threadIdx.x >> 5], s_tab, fix_acc, valid, i);
+                                   s_q[threadIdx.x >> 5], s_tab, fix_acc, fix_lim, err, valid, i);
     if (sg.w) {
         if (valid) out[i] = (double)b[i] - acc;
     } else {
@@ -285,7 +299,8 @@ __global__ void __launch_bounds__(kT) k_resid_df_sym_batched(const PlanView *__r
                                                              const float *__restrict__ bs, const double *__restrict__ xs,
                                                              double *__restrict__ rs, double *__restrict__ pool,
                                                              const int64_t *__restrict__ poff,
-                                                             unsigned long long *__restrict__ fix) {
+                                                             unsigned long long *__restrict__ fix, float fix_lim,
+                                                             unsigned *err) {
     __shared__ float4 s_p[kT];
     __shared__ float2 s_w[kT];
     __shared__ int s_tj[kT];
@@ -306,7 +321,8 @@ __global__ void __launch_bounds__(kT) k_resid_df_sym_batched(const PlanView *__r
     bool valid;
     int64_t i;
     double acc = resid_segment_sym(v.pos, v.tiles[sg.x], sg.x, xs + v.off, v.blk, v.ent, v.ebi, v.tile_of, sg, kc,
-                                   s_p, s_w, s_tj, s_q[threadIdx.x >> 5], s_tab, fix + 2 * v.off, valid, i);
+                                   s_p, s_w, s_tj, s_q[threadIdx.x >> 5], s_tab, fix + 2 * v.off, fix_lim, err,
+                                   valid, i);
     if (sg.w) {
         if (valid) rs[v.off + i] = (double)bs[v.off + i] - acc;
     } else {
@@ -383,15 +399,15 @@ void residual_df_prepare(int device, cudaStream_t s) { upload_table(device, s); 
 
 void residual_df_batched(const PlanView *views, const int2 *items, int64_t nitems, const int2 *splits,
                          int64_t nsplits, const float *bs, const double *xs, double *rs, double *part_pool,
-                         const int64_t *part_off, unsigned long long *fix, int64_t ntotal, int device,
-                         cudaStream_t s) {
+                         const int64_t *part_off, unsigned long long *fix, int64_t ntotal, int64_t max_tiles,
+                         unsigned *err, int device, cudaStream_t s) {
     upload_table(device, s);
     float Lh, Ll;
     split(0.6931471805599453, Lh, Ll);
     if (ntotal > 0) RBF_CUDA(cudaMemsetAsync(fix, 0, 2 * (size_t)ntotal * sizeof(unsigned long long), s));
     if (nitems > 0) {
         k_resid_df_sym_batched<<<(unsigned)nitems, kT, 0, s>>>(views, items, Lh, Ll, bs, xs, rs, part_pool, part_off,
-                                                               fix);
+                                                               fix, fix_share_limit(max_tiles), err);
         RBF_LAUNCHED();
     }
     if (nsplits > 0) {
@@ -435,7 +451,8 @@ void residual_binned_df(rbf_plan *P, const float *bs, const double *xs, double *
     }
     if (pl.nseg > 0) {
         k_resid_df_sym<<<(unsigned)pl.nseg, kT, 0, s>>>(P->pos.p, P->tiles.p, xs, P->blk.p, pl.ent.p, pl.ebi.p,
-                                                        pl.seg.p, tile_of.p, kc, bs, rs, part.p, fix.p);
+                                                        pl.seg.p, tile_of.p, kc, bs, rs, part.p, fix.p,
+                                                        fix_share_limit(pl.ntiles), ctx_error_word(P->ctx));
         RBF_LAUNCHED();
     }
     if (pl.any_split) {

@@ -16,6 +16,7 @@ import pytest
 
 import oracle
 import synth
+from layout_props import check_cell_layout
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -89,18 +90,32 @@ def test_build_centers_rejects_non_finite(ctx, rbf):
 
 
 # ---------------------------------------------------------------------- binning
-def _binning_case(ctx, rbf, C, sigma, k, s=1, L=3):
+def _binning_case(ctx, rbf, C, sigma, k, s=1, L=3, cell_edge=None):
+    """Bit-exact against the oracle where the binning is defined (keys of every
+    centre, cells and their contents, the cell table); the library's order
+    inside a cell by its properties (a permutation within the cell whose runs
+    of 32 and 128 are separated subtrees)."""
     Cd, C64 = c4(C)
-    plan = rbf.Plan(ctx, Cd, sigma=sigma, k=k, cells_per_cutoff=s, levels=L)
+    hc = oracle.truncation_cell_edge(sigma, k, s) if cell_edge is None else cell_edge
+    plan = rbf.Plan(ctx, Cd, sigma=sigma, k=k, cells_per_cutoff=s, levels=L,
+                    cell_edge=0.0 if cell_edge is None else cell_edge)
     perm, keys, cs, ce = plan.export_binning()
-    ref = oracle.binning(C64.astype(np.float32), F32(sigma), F32(k), s, L)
+    C32 = C64.astype(np.float32)
+    ref = oracle.binning(C32, hc, L)
     info = plan.info()
     assert info["nbits"] == ref["nbits"]
     assert np.float32(info["inv"]) == ref["inv"]
-    assert np.array_equal(perm.cpu().numpy(), ref["perm"])
-    assert np.array_equal(keys.cpu().numpy().view(np.uint32), ref["keys_sorted"])
-    assert np.array_equal(cs.cpu().numpy(), ref["cell_start"])
-    assert np.array_equal(ce.cpu().numpy(), ref["cell_end"])
+    perm = perm.cpu().numpy().astype(np.int64)
+    keys = keys.cpu().numpy().view(np.uint32)
+    cs, ce = cs.cpu().numpy(), ce.cpu().numpy()
+    assert np.array_equal(np.sort(perm), np.arange(len(C)))          # a permutation
+    assert np.array_equal(cs, ref["cell_start"]) and np.array_equal(ce, ref["cell_end"])
+    assert np.array_equal(keys, ref["key"][perm])                    # each position's own key
+    assert np.array_equal(keys >> np.uint32(3 * L), ref["keys_sorted"] >> np.uint32(3 * L))
+    for a, b in zip(cs, ce):                                         # same centres in every cell
+        if b - a > 1:
+            assert np.array_equal(np.sort(perm[a:b]), np.sort(ref["perm"][a:b]))
+    check_cell_layout(C32[perm], cs, ce)
     return plan
 
 
@@ -111,8 +126,18 @@ def test_binning_bit_exact_torus_patch(ctx, rbf):
 
 
 def test_binning_bit_exact_dense_sphere(ctx, rbf, sphere_c1):
+    """Untruncated: the cell edge is a free layout parameter, passed to both sides;
+    the default (a rule of the library's header, not of the method) is read back
+    from the plan and checked against that header's formula."""
     C, _ = oracle.build_centers(sphere_c1.points, sphere_c1.normals, 0.05)
-    _binning_case(ctx, rbf, C, 0.1, 0.0)
+    _binning_case(ctx, rbf, C, 0.1, 0.0, cell_edge=0.3)
+    _binning_case(ctx, rbf, C, 0.1, 0.0, cell_edge=0.17)
+    Cd, C64 = c4(C)
+    info = rbf.Plan(ctx, Cd, sigma=0.1, k=0.0).info()
+    C32 = C64.astype(np.float32)
+    m = float((C32.max(0) - C32.min(0)).max())
+    assert info["cell_edge"] == max(min(m / 8.0, 3.0 * float(F32(0.1))), m / 128.0)
+    _binning_case(ctx, rbf, C, 0.1, 0.0, cell_edge=info["cell_edge"])
 
 
 @pytest.mark.parametrize("n", [1, 2, 31, 33, 4097, 20000])

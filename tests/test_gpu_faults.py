@@ -78,3 +78,32 @@ def test_iteration_cap_reports_not_converged_with_the_true_residual(ctx, rbf, sp
     r = oracle.residual_rows(C64, b32.astype(np.float64), x.cpu().numpy(), float(F32(0.1)), 0.0)
     assert rep["residual_true"] == pytest.approx(np.linalg.norm(r) / np.linalg.norm(b32), rel=1e-6)
     assert 1e-14 < rep["residual_true"] < 1.0
+
+
+def test_residual_share_beyond_the_accumulator_range_reports_range(ctx, rbf):
+    """The double-float residual adds each row's source-side shares into a 128-bit
+    fixed-point accumulator.  Weights of 1e15 make shares far above its limit
+    min(2^44, 2^46 / (4 tiles)): the kernel runs normally, raises the context's error
+    word and the call returns RBF_ERR_RANGE; the native float64 mode has no such
+    limit and matches the oracle; the next call on the context is unaffected."""
+    rng = np.random.default_rng(11)
+    X = rng.uniform(0, 0.2, (3000, 3))
+    Cd, C64 = c4(X)
+    sigma, k = 0.02, 6.0
+    plan = rbf.Plan(ctx, Cd, sigma=sigma, k=k)
+    ntiles = plan.info()["nchunks"]
+    lim = min(2.0 ** 44, 2.0 ** 46 / (4 * ntiles))
+    b = torch.zeros(len(X), device="cuda")
+    big = np.full(len(X), 1e15)
+    assert 0.5 * big[0] > lim                     # one close pair already exceeds it
+    with pytest.raises(rbf.RbfError) as e:
+        plan.residual(b, torch.from_numpy(big).cuda(), mode="df")
+    assert e.value.status == 9 and "range" in str(e.value)
+    r64 = oracle.residual_rows(C64, np.zeros(len(X)), big, float(F32(sigma)), k)
+    r, _ = plan.residual(b, torch.from_numpy(big).cuda(), mode="f64")
+    assert np.abs(r.cpu().numpy() - r64).max() <= 1e-11 * np.abs(r64).max()
+    x = rng.standard_normal(len(X))
+    r, _ = plan.residual(b, torch.from_numpy(x).cuda(), mode="df")
+    r64 = oracle.residual_rows(C64, np.zeros(len(X)), x, float(F32(sigma)), k)
+    scale, _ = oracle.kernel_rows(C64, np.abs(x), float(F32(sigma)), k)     # sum_j |a_ij x_j|
+    assert np.abs(r.cpu().numpy() - r64).max() <= 1e-11 * scale.max()

@@ -319,13 +319,14 @@ def test_binning_permutation_sorted_stable():
     rng = np.random.default_rng(4)
     C = rng.uniform(-1, 2, (5000, 3)).astype(np.float32)
     C[100:110] = C[7]                          # duplicates: equal keys
-    B = oracle.binning(C, 0.05, 3.0, kd_leaf=0)      # the sort alone, no k-d refinement
+    B = oracle.binning(C, oracle.truncation_cell_edge(0.05, 3.0))
     perm = B["perm"]
     assert np.array_equal(np.sort(perm), np.arange(5000))
     ks = B["keys_sorted"].astype(np.int64)
     assert np.all(np.diff(ks) >= 0)
     eq = np.diff(ks) == 0
     assert np.all(np.diff(perm)[eq] > 0)       # stable: equal keys keep input order
+    assert np.array_equal(B["key"][perm], B["keys_sorted"])
     # every centre lies in the fine cell its key names
     inv, lo = B["inv"], B["lo"]
     q = np.floor((C[perm] - lo).astype(np.float32) * inv)
@@ -340,48 +341,30 @@ def test_binning_permutation_sorted_stable():
     assert np.all(covered == 1)
 
 
-def test_kd_refinement_keeps_cells_and_permutes_within():
-    rng = np.random.default_rng(5)
-    C = rng.uniform(0, 1, (20000, 3)).astype(np.float32)
-    A = oracle.binning(C, 0.05, 4.0, kd_leaf=0)
-    B = oracle.binning(C, 0.05, 4.0)
-    assert np.array_equal(A["cell_start"], B["cell_start"]) and np.array_equal(A["cell_end"], B["cell_end"])
-    assert np.array_equal(A["cell_of_sorted"], B["cell_of_sorted"])
-    for s, e in zip(B["cell_start"], B["cell_end"]):
-        assert set(A["perm"][s:e]) == set(B["perm"][s:e])
-
-
-def test_kd_order_on_a_line_is_a_sort():
-    """Collinear points along x: every split is along x, so the order sorts x."""
-    rng = np.random.default_rng(6)
-    x = rng.uniform(-1, 1, 300).astype(np.float32)
-    P = np.stack([x, np.zeros_like(x), np.zeros_like(x)], 1)
-    o = oracle._kd_order(P, 32, 128)
-    assert np.array_equal(o, np.argsort(x, kind="stable"))
-
-
-def test_kd_order_leaves_are_compact_squares():
-    """A 16 x 16 lattice in a plane: tiles of 128 are 8 x 16 halves and leaves of 32
-    are 4 x 8 (or 8 x 4) blocks of nodes."""
-    i, j = np.meshgrid(np.arange(16), np.arange(16), indexing="ij")
-    rng = np.random.default_rng(7)
-    P = np.stack([i.ravel(), j.ravel(), np.zeros(256)], 1).astype(np.float32)[rng.permutation(256)]
-    o = oracle._kd_order(P, 32, 128)
-    Q = P[o]
-    for t in range(2):
-        q = Q[128 * t:128 * (t + 1)]
-        ext = sorted((q.max(0) - q.min(0))[:2])
-        assert ext == [7.0, 15.0]
-    for leaf in range(8):
-        q = Q[32 * leaf:32 * (leaf + 1)]
-        ext = sorted((q.max(0) - q.min(0))[:2])
-        assert ext == [3.0, 7.0]
+def test_binning_matches_a_brute_force_grouping():
+    """Cells by brute force: integer cell coordinates from float64 division (away
+    from cell faces the float32 rule agrees), grouped by a dictionary."""
+    rng = np.random.default_rng(8)
+    hc = 0.25
+    cells = rng.integers(0, 6, (400, 3))
+    C = ((cells + rng.uniform(0.05, 0.95, (400, 3))) * hc).astype(np.float32)
+    C[0] = 0.0                                  # pins lo at the origin
+    B = oracle.binning(C, hc, levels=2)
+    groups = {}
+    for i, c in enumerate(C.astype(np.float64)):
+        groups.setdefault(tuple(np.floor(c / hc).astype(int)), []).append(i)
+    cs, ce, perm = B["cell_start"], B["cell_end"], B["perm"]
+    nonempty = [(s, e) for s, e in zip(cs, ce) if e > s]
+    assert len(nonempty) == len(groups)
+    found = {tuple(sorted(perm[s:e])) for s, e in nonempty}
+    assert found == {tuple(sorted(g)) for g in groups.values()}
 
 
 def test_binning_cell_edge():
-    """Fine cells are hc/2^L with hc = k sigma / s; cells are 2^L fine cells."""
+    """Fine cells are hc/2^L; cells are 2^L fine cells; r_c / s is k sigma / s."""
+    assert oracle.truncation_cell_edge(0.1, 3.0, 1) == float(np.float32(3.0)) * float(np.float32(0.1))
     C = np.array([[0, 0, 0], [0.299, 0, 0], [0.301, 0, 0], [0.61, 0.0, 0.0]], dtype=np.float32)
-    B = oracle.binning(C, 0.1, 3.0, cells_per_cutoff=1, levels=3)   # hc = 0.3
+    B = oracle.binning(C, oracle.truncation_cell_edge(0.1, 3.0, 1), levels=3)   # hc = 0.3
     cell = B["cell_of_sorted"][np.argsort(B["perm"])]
     assert cell[0] == cell[1] and cell[2] != cell[1]
     assert cell[2] == 1 and cell[3] == 8   # Morton codes of cell x = 1 and x = 2
