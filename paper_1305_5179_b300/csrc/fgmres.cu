@@ -314,6 +314,7 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
                 t_res.begin(s);
                 residual_binned(P, p.residual_mode, bs.p, x.p, r.p, s);
                 t_res.end(s);
+                have_true = true;   // a solve that stops here needs no second residual for this x
             } else {
                 // float32 product for the restart vector; the float64 residual runs once at the end
                 k_to_f32<<<g1(n), kThreads, 0, s>>>(x.p, w32.p, n);
