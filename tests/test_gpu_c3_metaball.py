@@ -52,4 +52,36 @@ def test_c3_refinement_residual_on_sampled_rows(c3):
     print(f"  C3 double-float residual, 10,000 sampled rows: max error {err:.2e} of max sum|a x|; "
           f"true relative residual after 20 iterations {rep['residual_true']:.3e}")
     assert err <= 1e-11
-    assert np.isfinite(rep["residual_true"]) and rep["residual_true"] < 1.0
+    assert rep["residual_true"] == pytest.approx(float(np.linalg.norm(r.cpu().numpy()) / np.linalg.norm(
+        b.double().cpu().numpy())), rel=1e-9)
+
+
+def test_c3_refinement_residuals_agree_at_every_restart(c3, capsys):
+    """FP64 refinement (every FGMRES(50) restart recomputes b - A~ x in double-float): the
+    library's true residual after 50, 100, 150 and 200 iterations agrees with the
+    oracle's float64 rows (10,000 sampled) to 1e-11 of max sum |a x| at every restart,
+    the reported relative residual equals the norm of the library's residual vector,
+    and every restart lowers it.  The refinement does not stagnate within reach: on
+    B300 the same solve measured 5.8e-5 after 400, 1.9e-5 after 1,000 and 9.0e-6 after
+    2,000 iterations (about 0.12 s per iteration), so node residual 1e-6 on this
+    configuration is a matter of many thousands of iterations, not of precision."""
+    rbf, ctx, plan, C, b, C64, rows = c3
+    bh = b.double().cpu().numpy()
+    hist = []
+    for k in (50, 100, 150, 200):
+        x, rep = plan.solve(b, m=50, max_it=k, fixed_iterations=True)
+        assert rep["iterations"] == k
+        r, (rn, bn) = plan.residual(b, x)
+        xs = x.cpu().numpy()
+        r64 = oracle.residual_rows(C64, bh, xs, float(F32(SIGMA)), float(F32(K)), rows)
+        scale, _ = oracle.kernel_rows(C64, np.abs(xs), float(F32(SIGMA)), float(F32(K)), rows)
+        err = np.abs(r.cpu().numpy()[rows] - r64).max() / scale.max()
+        assert err <= 1e-11, (k, err)
+        assert rep["residual_true"] == pytest.approx(rn / bn, rel=1e-9)
+        hist.append((k, rep["residual_true"], float(np.linalg.norm(r64) / np.linalg.norm(bh[rows])), err))
+    with capsys.disabled():
+        print("\n  C3 refinement (iterations, true relative residual, sampled-row oracle residual, row error):",
+              ", ".join(f"{k}: {t:.3e} / {o:.3e} / {e:.1e}" for k, t, o, e in hist))
+    t = [h[1] for h in hist]
+    assert all(b_ < a_ for a_, b_ in zip(t, t[1:]))                     # every restart gains
+    assert t[-1] < 1e-3
