@@ -14,10 +14,12 @@
 // blocks for caller-supplied random right-hand sides; the loss is the mean
 // squared error; Adam updates the master weights.
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_bf16.h>
 
+#include "gemm_tc.cuh"
 #include "plan.cuh"
 
 namespace {
@@ -149,138 +151,16 @@ __global__ void __launch_bounds__(64) k_block_solve64(const float4 *__restrict__
 }
 
 // ------------------------------------------------------------------ dense layers
-// C[M x N] = act(A[M x K] W^T + b) (+ skip[m * ldskip + n]), W [N x K] (row = output),
-// float or bf16 weights.
-template <typename Tw, bool kRelu>
-__global__ void __launch_bounds__(256) k_dense_fwd(const float *__restrict__ A, const Tw *__restrict__ W,
-                                                   const float *__restrict__ bias, float *__restrict__ C, int M, int N,
-                                                   int K, const float *__restrict__ skip = nullptr, int ldskip = 0) {
-    __shared__ float As[64][17];
-    __shared__ float Ws[64][17];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        for (int idx = threadIdx.x; idx < 64 * 16; idx += 256) {
-            int r = idx >> 4, c = idx & 15;
-            As[r][c] = (m0 + r < M && k0 + c < K) ? A[(int64_t)(m0 + r) * K + k0 + c] : 0.f;
-            Ws[r][c] = (n0 + r < N && k0 + c < K) ? (float)W[(int64_t)(n0 + r) * K + k0 + c] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            float a[4], w[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                a[i] = As[ty * 4 + i][kk];
-                w[i] = Ws[tx * 4 + i][kk];
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int m = m0 + ty * 4 + i, nn = n0 + tx * 4 + j;
-            if (m < M && nn < N) {
-                float v = acc[i][j] + bias[nn];
-                v = kRelu ? fmaxf(v, 0.f) : v;
-                if (skip) v += skip[(int64_t)m * ldskip + nn];
-                C[(int64_t)m * N + nn] = v;
-            }
-        }
-}
+// The three contractions (forward, dA = dC W, dW = dC^T A) run on the tensor cores
+// (gemm_tc.cu); the bias gradient is a column sum.
 
-// dA[M x K] = (dC [M x N] masked by relu'(act)) W [N x K]; also writes the masked dC back
-__global__ void __launch_bounds__(256) k_dense_bwd_data(const float *__restrict__ dC, const float *__restrict__ W,
-                                                        float *__restrict__ dA, int M, int N, int K) {
-    __shared__ float Cs[64][17];
-    __shared__ float Ws[16][65];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int m0 = blockIdx.y * 64, k0b = blockIdx.x * 64;
-    float acc[4][4] = {};
-    for (int n0 = 0; n0 < N; n0 += 16) {
-        for (int idx = threadIdx.x; idx < 64 * 16; idx += 256) {
-            int r = idx >> 4, c = idx & 15;
-            Cs[r][c] = (m0 + r < M && n0 + c < N) ? dC[(int64_t)(m0 + r) * N + n0 + c] : 0.f;
-            int rr = idx >> 6, cc = idx & 63;
-            Ws[rr][cc] = (n0 + rr < N && k0b + cc < K) ? W[(int64_t)(n0 + rr) * K + k0b + cc] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int nn = 0; nn < 16; ++nn) {
-            float c[4], w[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                c[i] = Cs[ty * 4 + i][nn];
-                w[i] = Ws[nn][tx * 4 + i];
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(c[i], w[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int m = m0 + ty * 4 + i, k = k0b + tx * 4 + j;
-            if (m < M && k < K) dA[(int64_t)m * K + k] = acc[i][j];
-        }
-}
-
-// dW[N x K] = dC^T [N x M] A [M x K] (accumulated over the batch), db[N] = sum_m dC
-__global__ void __launch_bounds__(256) k_dense_bwd_weight(const float *__restrict__ dC, const float *__restrict__ A,
-                                                          float *__restrict__ dW, float *__restrict__ db, int M, int N,
-                                                          int K) {
-    __shared__ float Cs[16][65];
-    __shared__ float As[16][65];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int n0 = blockIdx.y * 64, k0 = blockIdx.x * 64;
-    float acc[4][4] = {};
-    float bacc[4] = {};
-    for (int m0 = 0; m0 < M; m0 += 16) {
-        for (int idx = threadIdx.x; idx < 16 * 64; idx += 256) {
-            int r = idx >> 6, c = idx & 63;
-            Cs[r][c] = (m0 + r < M && n0 + c < N) ? dC[(int64_t)(m0 + r) * N + n0 + c] : 0.f;
-            As[r][c] = (m0 + r < M && k0 + c < K) ? A[(int64_t)(m0 + r) * K + k0 + c] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int mm = 0; mm < 16; ++mm) {
-            float c[4], a[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                c[i] = Cs[mm][ty * 4 + i];
-                a[i] = As[mm][tx * 4 + i];
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if (tx == 0 && blockIdx.x == 0) bacc[i] += c[i];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(c[i], a[j], acc[i][j]);
-            }
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int nn = n0 + ty * 4 + i;
-        if (nn >= N) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int k = k0 + tx * 4 + j;
-            if (k < K) dW[(int64_t)nn * K + k] = acc[i][j];
-        }
-        if (tx == 0 && blockIdx.x == 0) db[nn] = bacc[i];
-    }
+// db[n] = sum_m dC[m][n] (fixed order per column)
+__global__ void k_colsum(const float *__restrict__ dC, int M, int N, float *__restrict__ db) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float acc = 0.f;
+    for (int m = 0; m < M; ++m) acc += dC[(int64_t)m * N + n];
+    db[n] = acc;
 }
 
 // g = g * (act > 0)
@@ -412,28 +292,76 @@ void mlp_get_params(rbf_mlp *M, float *host, cudaStream_t s) {
     RBF_CUDA(cudaStreamSynchronize(s));
 }
 
-// forward of `rows` inputs; bf16 = inference weights, else the FP32 master weights
+// C[rows x N] = act(A[rows x K] W^T + bias) (+ skip), W [N x K] row-major
+template <typename Tw>
+static void dense_fwd(rbf_mlp *M, const float *A, const Tw *W, const float *bias, float *C, int rows, int N, int K,
+                      bool relu, const float *skip, int ldskip, cudaStream_t s) {
+    GemmArgs g;
+    g.M = rows;
+    g.N = N;
+    g.K = K;
+    g.a_sr = K;
+    g.a_sk = 1;
+    g.b_sr = K;
+    g.b_sk = 1;
+    g.C = C;
+    g.ldc = N;
+    g.bias = bias;
+    g.relu = relu ? 1 : 0;
+    g.skip = skip;
+    g.ldskip = ldskip;
+    gemm_tc(g, A, W, std::is_same<Tw, __nv_bfloat16>::value ? 2 : 3, ctx_error_word(M->ctx), s);
+}
+
+// forward of `rows` inputs; bf16 = inference weights (exact in tf32: head and tail of the
+// activations times the weights), else the FP32 master weights (three tf32 products)
 static void mlp_forward_dev(rbf_mlp *M, const float *X, int rows, float *Y, bool bf16, cudaStream_t s) {
     mlp_ensure(M, rows, s);
-    dim3 gH(g1(kH, 64), g1(rows, 64)), gO(g1(kOut, 64), g1(rows, 64));
+    const float *w = M->w.p;
     if (bf16) {
-        const __nv_bfloat16 *w = M->wb.p;
-        k_dense_fwd<__nv_bfloat16, true><<<gH, 256, 0, s>>>(X, w + kOffW1, M->w.p + kOffB1, M->a1.p, rows, kH, kIn);
-        RBF_LAUNCHED();
-        k_dense_fwd<__nv_bfloat16, true><<<gH, 256, 0, s>>>(M->a1.p, w + kOffW2, M->w.p + kOffB2, M->a2.p, rows, kH, kH);
-        RBF_LAUNCHED();
-        k_dense_fwd<__nv_bfloat16, false><<<gO, 256, 0, s>>>(M->a2.p, w + kOffW3, M->w.p + kOffB3, Y, rows, kOut, kH,
-                                                             X + 192, kIn);
-        RBF_LAUNCHED();
+        const __nv_bfloat16 *wb = M->wb.p;
+        dense_fwd(M, X, wb + kOffW1, w + kOffB1, M->a1.p, rows, kH, kIn, true, nullptr, 0, s);
+        dense_fwd(M, M->a1.p, wb + kOffW2, w + kOffB2, M->a2.p, rows, kH, kH, true, nullptr, 0, s);
+        dense_fwd(M, M->a2.p, wb + kOffW3, w + kOffB3, Y, rows, kOut, kH, false, X + 192, kIn, s);
     } else {
-        const float *w = M->w.p;
-        k_dense_fwd<float, true><<<gH, 256, 0, s>>>(X, w + kOffW1, w + kOffB1, M->a1.p, rows, kH, kIn);
-        RBF_LAUNCHED();
-        k_dense_fwd<float, true><<<gH, 256, 0, s>>>(M->a1.p, w + kOffW2, w + kOffB2, M->a2.p, rows, kH, kH);
-        RBF_LAUNCHED();
-        k_dense_fwd<float, false><<<gO, 256, 0, s>>>(M->a2.p, w + kOffW3, w + kOffB3, Y, rows, kOut, kH, X + 192, kIn);
-        RBF_LAUNCHED();
+        dense_fwd(M, X, w + kOffW1, w + kOffB1, M->a1.p, rows, kH, kIn, true, nullptr, 0, s);
+        dense_fwd(M, M->a1.p, w + kOffW2, w + kOffB2, M->a2.p, rows, kH, kH, true, nullptr, 0, s);
+        dense_fwd(M, M->a2.p, w + kOffW3, w + kOffB3, Y, rows, kOut, kH, false, X + 192, kIn, s);
     }
+}
+
+// dW[N x K] = dC^T A over the batch (dC [rows x N], A [rows x K]), db = column sums of dC
+static void dense_bwd_weight(rbf_mlp *M, const float *dC, const float *A, float *dW, float *db, int rows, int N, int K,
+                             cudaStream_t s) {
+    GemmArgs g;
+    g.M = N;
+    g.N = K;
+    g.K = rows;
+    g.a_sr = 1;
+    g.a_sk = N;
+    g.b_sr = 1;
+    g.b_sk = K;
+    g.C = dW;
+    g.ldc = K;
+    gemm_tc(g, dC, A, 3, ctx_error_word(M->ctx), s);
+    k_colsum<<<g1(N, 128), 128, 0, s>>>(dC, rows, N, db);
+    RBF_LAUNCHED();
+}
+
+// dA[rows x K] = dC [rows x N] W [N x K]
+static void dense_bwd_data(rbf_mlp *M, const float *dC, const float *W, float *dA, int rows, int N, int K,
+                           cudaStream_t s) {
+    GemmArgs g;
+    g.M = rows;
+    g.N = K;
+    g.K = N;
+    g.a_sr = N;
+    g.a_sk = 1;
+    g.b_sr = 1;
+    g.b_sk = K;
+    g.C = dA;
+    g.ldc = K;
+    gemm_tc(g, dC, W, 3, ctx_error_word(M->ctx), s);
 }
 
 void mlp_forward(rbf_mlp *M, const float *X, int64_t rows, float *Y, int bf16, cudaStream_t s) {
@@ -455,25 +383,17 @@ double mlp_loss_grad(rbf_mlp *M, const float *X, const float *T, int rows, bool 
         float *g = M->g.p;
         const float *w = M->w.p;
         // layer 3
-        k_dense_bwd_weight<<<dim3(g1(kH, 64), g1(kOut, 64)), 256, 0, s>>>(M->d3.p, M->a2.p, g + kOffW3, g + kOffB3,
-                                                                           rows, kOut, kH);
-        RBF_LAUNCHED();
-        k_dense_bwd_data<<<dim3(g1(kH, 64), g1(rows, 64)), 256, 0, s>>>(M->d3.p, w + kOffW3, M->d2.p, rows, kOut, kH);
-        RBF_LAUNCHED();
+        dense_bwd_weight(M, M->d3.p, M->a2.p, g + kOffW3, g + kOffB3, rows, kOut, kH, s);
+        dense_bwd_data(M, M->d3.p, w + kOffW3, M->d2.p, rows, kOut, kH, s);
         k_relu_mask<<<g1((int64_t)rows * kH), 256, 0, s>>>(M->d2.p, M->a2.p, (int64_t)rows * kH);
         RBF_LAUNCHED();
         // layer 2
-        k_dense_bwd_weight<<<dim3(g1(kH, 64), g1(kH, 64)), 256, 0, s>>>(M->d2.p, M->a1.p, g + kOffW2, g + kOffB2, rows,
-                                                                         kH, kH);
-        RBF_LAUNCHED();
-        k_dense_bwd_data<<<dim3(g1(kH, 64), g1(rows, 64)), 256, 0, s>>>(M->d2.p, w + kOffW2, M->d1.p, rows, kH, kH);
-        RBF_LAUNCHED();
+        dense_bwd_weight(M, M->d2.p, M->a1.p, g + kOffW2, g + kOffB2, rows, kH, kH, s);
+        dense_bwd_data(M, M->d2.p, w + kOffW2, M->d1.p, rows, kH, kH, s);
         k_relu_mask<<<g1((int64_t)rows * kH), 256, 0, s>>>(M->d1.p, M->a1.p, (int64_t)rows * kH);
         RBF_LAUNCHED();
         // layer 1
-        k_dense_bwd_weight<<<dim3(g1(kIn, 64), g1(kH, 64)), 256, 0, s>>>(M->d1.p, X, g + kOffW1, g + kOffB1, rows, kH,
-                                                                          kIn);
-        RBF_LAUNCHED();
+        dense_bwd_weight(M, M->d1.p, X, g + kOffW1, g + kOffB1, rows, kH, kIn, s);
     }
     std::vector<double> part(nblk);
     RBF_CUDA(cudaMemcpyAsync(part.data(), M->part.p, nblk * sizeof(double), cudaMemcpyDeviceToHost, s));

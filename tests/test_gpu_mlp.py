@@ -118,13 +118,13 @@ def test_fgmres_with_learned_preconditioner(rbf, ctx, patch, capsys):
         print("\n  residual after 40 FGMRES iterations (true, ms, fallback blocks):", res)
     # What the trained network gains over the method without it, as a number: the ratio of
     # the unpreconditioned residual to the network-preconditioned one after the same 40
-    # iterations.  Measured on B300: none 0.10731, network 0.10702 (gain 1.003, i.e. none),
+    # iterations.  Measured on B300: none 0.10731, network 0.10703 (gain 1.003, i.e. none),
     # the exact shifted block solves it learns 0.1526 (gain 0.70), the network's initial
-    # guess 0.2825 (gain 0.38).  Every step is deterministic; the bounds allow 3%.
+    # guess 0.2915 (gain 0.37).  Every step is deterministic; the bounds allow 3%.
     gain = {k: res["none"][0] / v[0] for k, v in res.items()}
     with capsys.disabled():
         print("  gain over no preconditioner (residual ratio):", {k: round(v, 4) for k, v in gain.items()})
     assert gain["mlp"] == pytest.approx(1.003, abs=0.03)
     assert gain["ras64"] == pytest.approx(0.703, abs=0.03)
-    assert gain["mlp+x0"] == pytest.approx(0.380, abs=0.03)
+    assert gain["mlp+x0"] == pytest.approx(0.368, abs=0.03)
     assert res["mlp"][2] == 0                                   # no block fell back to RAS
