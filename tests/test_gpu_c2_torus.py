@@ -50,7 +50,10 @@ def test_c2_solve_residual_sampled_rows(c2):
     assert np.abs(r.cpu().numpy()[rows] - r64).max() <= 1e-11 * scale.max()
     assert rep["residual_true"] == pytest.approx(rn / bn, rel=1e-9)
     assert rep["precond_failed_blocks"] == 0
-    # the position noise (1e-3, a tenth of delta) leaves about 0.1 that no smooth interpolant removes
+    # Krylov stagnation on a numerically singular system, not a missing interpolant (the
+    # matrix is positive definite): on a 19,098-centre sector of this cloud 9.7% of |b| lies
+    # in eigenvectors with |lambda| < 1e-6 lambda_max (0.06% without the position noise), and
+    # GMRES does not resolve those components; measured 0.114 after these 50 iterations
     assert rep["residual_true"] < 0.2
     print(f"  C2 after 50 RAS-FGMRES iterations: relative residual {rep['residual_true']:.4f}")
 
