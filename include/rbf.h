@@ -173,6 +173,9 @@ typedef struct {
     float inv;              /* fine cells per unit length (float32) */
     float sigma, k;
     double cell_edge;       /* the cell edge hc used (double, before inv is rounded) */
+    int symmetric;          /* 1: the tensor-core product evaluates each in-range pair once and adds
+                               its transposed share to the source's row (plans whose (tile, block)
+                               list averages fewer than 128 entries per tile); 0: from both sides */
 } rbf_plan_info;
 
 /* Build a plan over n centres (device float4 array, caller order).  The plan

@@ -78,7 +78,7 @@ class PlanInfo(ctypes.Structure):
                 ("nchunks", ctypes.c_int64), ("pairlist_len", ctypes.c_int64), ("nsegments", ctypes.c_int64),
                 ("nbits", ctypes.c_int), ("levels", ctypes.c_int), ("lo", ctypes.c_float * 3),
                 ("inv", ctypes.c_float), ("sigma", ctypes.c_float), ("k", ctypes.c_float),
-                ("cell_edge", ctypes.c_double)]
+                ("cell_edge", ctypes.c_double), ("symmetric", ctypes.c_int)]
 
 
 class SchwarzParams(ctypes.Structure):

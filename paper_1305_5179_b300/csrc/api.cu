@@ -208,6 +208,7 @@ rbf_status rbf_plan_get_info(const rbf_plan *P, rbf_plan_info *info) {
     for (int d = 0; d < 3; ++d) info->lo[d] = P->lo[d];
     info->inv = P->inv;
     info->cell_edge = P->hc;
+    info->symmetric = P->sym_ready ? 1 : 0;
     info->sigma = P->sigma;
     info->k = P->k;
     return RBF_OK;

@@ -197,6 +197,21 @@ MvArgs base_args(const rbf_plan *P, const PairList &pl, const float *w, float *o
 }  // namespace
 
 void matvec_binned(rbf_plan *P, const float *zs, float *ys, cudaStream_t s) {
+    if (P->kernel == RBF_KERNEL_GAUSSIAN && P->product == RBF_PRODUCT_TC && P->sym_ready) {
+        // symmetric form: every in-range pair evaluated once (see rbf_plan::sym)
+        const PairList &sl = P->sym;
+        if (sl.any_split) P->partial.ensure((size_t)sl.nseg * kChunk, s);
+        MvArgs a = base_args(P, sl, zs, ys, P->partial.p);
+        a.colpart = P->colpart.p;
+        ctx_check_device_error(P->ctx);
+        product_tc_sym_launch(P, a, s);
+        if (sl.any_split) {
+            k_reduce_segments<false><<<(unsigned)sl.ntiles, kChunk, 0, s>>>(a, sl.tile_seg.p, P->partial.p);
+            RBF_LAUNCHED();
+        }
+        product_tc_sym_gather(P, ys, s);
+        return;
+    }
     const PairList &pl = P->pl;
     if (pl.any_split) P->partial.ensure((size_t)pl.nseg * kChunk, s);
     MvArgs a = base_args(P, pl, zs, ys, P->partial.p);

@@ -554,6 +554,144 @@ __global__ void __launch_bounds__(kRefWarps * 32) k_pl_refine(const float4 *__re
 }
 }  // namespace
 
+// ------------------------------------------------------------------ symmetric sub-list
+namespace {
+
+__global__ void k_tile_of_pos(const int2 *__restrict__ tiles, int32_t *__restrict__ tile_of) {
+    const int2 tl = tiles[blockIdx.x];
+    for (int q = threadIdx.x; q < tl.y; q += blockDim.x) tile_of[tl.x + q] = (int32_t)blockIdx.x;
+}
+
+__device__ __forceinline__ int entry_tile(const int32_t *__restrict__ ent, const int2 *__restrict__ blk,
+                                          const int32_t *__restrict__ tile_of, int64_t e) {
+    return tile_of[blk[ent[e] & 0x7fffffff].x];
+}
+
+// one warp per tile: entries of tile t whose block lies in tile t or a later one
+__global__ void k_sym_count(const int32_t *__restrict__ off, int64_t ntiles, const int32_t *__restrict__ ent,
+                            const int2 *__restrict__ blk, const int32_t *__restrict__ tile_of,
+                            int32_t *__restrict__ cnt) {
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= ntiles) return;
+    int c = 0;
+    for (int64_t e0 = off[t]; e0 < off[t + 1]; e0 += 32) {
+        const int64_t e = e0 + lane;
+        const bool keep = e < off[t + 1] && entry_tile(ent, blk, tile_of, e) >= t;
+        c += __popc(__ballot_sync(0xffffffffu, keep));
+    }
+    if (lane == 0) cnt[t] = c;
+}
+
+// the kept entries in their order; upper ones flagged in bit 16 of ebi.y
+__global__ void k_sym_fill(const int32_t *__restrict__ off, int64_t ntiles, const int32_t *__restrict__ ent,
+                           const int2 *__restrict__ ebi, const int2 *__restrict__ blk,
+                           const int32_t *__restrict__ tile_of, const int32_t *__restrict__ soff,
+                           int32_t *__restrict__ sent, int2 *__restrict__ sebi) {
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= ntiles) return;
+    int64_t w = soff[t];
+    for (int64_t e0 = off[t]; e0 < off[t + 1]; e0 += 32) {
+        const int64_t e = e0 + lane;
+        const int tb = e < off[t + 1] ? entry_tile(ent, blk, tile_of, e) : -1;
+        const bool keep = tb >= t;
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const int64_t d = w + __popc(m & ((1u << lane) - 1u));
+            sent[d] = ent[e];
+            int2 v = ebi[e];
+            if (tb > t) v.y |= 1 << 16;
+            sebi[d] = v;
+        }
+        w += __popc(m);
+    }
+}
+
+// sort keys: the block of an upper entry, or nblk (sorts after every block) otherwise
+__global__ void k_sym_keys(const int32_t *__restrict__ sent, const int2 *__restrict__ sebi, int64_t len,
+                           uint32_t nblk, uint32_t *__restrict__ keys, int32_t *__restrict__ vals) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= len) return;
+    keys[e] = (sebi[e].y >> 16) & 1 ? (uint32_t)(sent[e] & 0x7fffffff) : nblk;
+    vals[e] = (int32_t)e;
+}
+
+}  // namespace
+
+void build_symmetric(rbf_plan *P, cudaStream_t s) {
+    const PairList &pl = P->pl;
+    PairList &sy = P->sym;
+    const int64_t nt = pl.ntiles;
+    P->tile_of.alloc(std::max<int64_t>(P->n, 1), s);
+    if (nt > 0) {
+        k_tile_of_pos<<<(unsigned)nt, kChunk, 0, s>>>(P->tiles.p, P->tile_of.p);
+        RBF_LAUNCHED();
+    }
+    sy.ntiles = nt;
+    sy.off.alloc(nt + 1, s);
+    DevBuf<int32_t> cnt;
+    cnt.alloc(std::max<int64_t>(nt, 1), s);
+    const unsigned wgrid = grid_for(nt * 32);
+    if (nt > 0) {
+        k_sym_count<<<wgrid, kThreads, 0, s>>>(pl.off.p, nt, pl.ent.p, P->blk.p, P->tile_of.p, cnt.p);
+        RBF_LAUNCHED();
+    }
+    scan_exclusive_i32(cnt.p, sy.off.p, nt, s);
+    int32_t len = 0;
+    RBF_CUDA(cudaMemcpyAsync(&len, sy.off.p + nt, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(cudaStreamSynchronize(s));
+    sy.len = len;
+    sy.ent.alloc(std::max<int64_t>(len, 1), s);
+    sy.ebi.alloc(std::max<int64_t>(len, 1), s);
+    if (nt > 0) {
+        k_sym_fill<<<wgrid, kThreads, 0, s>>>(pl.off.p, nt, pl.ent.p, pl.ebi.p, P->blk.p, P->tile_of.p, sy.off.p,
+                                              sy.ent.p, sy.ebi.p);
+        RBF_LAUNCHED();
+    }
+    // segments by the rule of the full list
+    int64_t want = 8LL * P->ctx->num_sms;
+    int64_t seglen = len > 0 ? std::max<int64_t>(64, 2 * ceil_div((int64_t)len, std::max<int64_t>(nt, 1))) : 1;
+    if (nt < want && len > 0) seglen = std::min<int64_t>(seglen, std::max<int64_t>(8, ceil_div((int64_t)len, want)));
+    segment_pairlist(P, sy, seglen, s);
+    // upper entries ordered by block (stable: entry order within a block), with per-block ranges
+    const int64_t nblk = P->nblk;
+    DevBuf<uint32_t> keys;
+    DevBuf<int32_t> vals;
+    keys.alloc(std::max<int64_t>(len, 1), s);
+    vals.alloc(std::max<int64_t>(len, 1), s);
+    if (len > 0) {
+        k_sym_keys<<<grid_for(len), kThreads, 0, s>>>(sy.ent.p, sy.ebi.p, len, (uint32_t)nblk, keys.p, vals.p);
+        RBF_LAUNCHED();
+    }
+    int bits = 1;
+    while ((1LL << bits) <= nblk) ++bits;
+    radix_sort_pairs(keys.p, vals.p, len, bits, s);
+    P->sym_bstart.alloc(nblk + 1, s);
+    P->sym_bend.alloc(nblk + 1, s);
+    P->sym_bstart.zero(s);
+    P->sym_bend.zero(s);
+    if (len > 0) {
+        k_cell_ranges<<<grid_for(len), kThreads, 0, s>>>(keys.p, len, 0, P->sym_bstart.p, P->sym_bend.p);
+        RBF_LAUNCHED();
+    }
+    int32_t upper = 0;     // the upper entries are the ones before the first key nblk
+    if (len > 0) {
+        RBF_CUDA(cudaMemcpyAsync(&upper, P->sym_bstart.p + nblk, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        int32_t end_n = 0;
+        RBF_CUDA(cudaMemcpyAsync(&end_n, P->sym_bend.p + nblk, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        RBF_CUDA(cudaStreamSynchronize(s));
+        if (end_n == 0) upper = len;   // no diagonal entry at all
+    }
+    P->sym_upper = upper;
+    P->sym_src.alloc(std::max<int64_t>(upper, 1), s);
+    if (upper > 0)
+        RBF_CUDA(cudaMemcpyAsync(P->sym_src.p, vals.p, (size_t)upper * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    P->colpart.alloc((size_t)std::max<int64_t>(len, 1) * kBlk, s);
+    RBF_CUDA(cudaStreamSynchronize(s));    // keys and vals are freed on return
+    P->sym_ready = true;
+}
+
 void build_pairlist(rbf_plan *P, const float4 *tlo, const float4 *thi, const float4 *qlo, const float4 *qhi,
                     int64_t ntiles, PairList &pl, cudaStream_t s) {
     CellGridArgs g;
@@ -775,4 +913,13 @@ void plan_build(rbf_plan *P, const float4 *centers, cudaStream_t s, bool binning
             P->pos.p, P->tiles.p, P->pl.off.p, P->nchk, rc2 * (1.f - 1e-5f), rc2 * (1.f + 1e-5f), P->pl.ebi.p);
         RBF_LAUNCHED();
     }
+    // 5: the symmetric form of the tensor-core Gaussian product, for short lists.  Evaluating
+    //    each pair once halves the MMAs and the exponentials but adds a shared-memory
+    //    transpose per (warp, upper block) for the transposed sums.  Measured on B300: with
+    //    39 entries per tile (the 3M-centre sphere at sigma = the spacing) the symmetric
+    //    product takes 2.03 ms against 2.28; with 508 (the C2 torus) 9.92 ms against 9.43,
+    //    where the transpose keeps the shared-memory pipe 91% busy.  So short lists only.
+    if (P->product == RBF_PRODUCT_TC && P->kernel == RBF_KERNEL_GAUSSIAN &&
+        P->pl.len < (int64_t)kSymMaxEntriesPerTile * P->pl.ntiles)
+        build_symmetric(P, s);
 }

@@ -4,6 +4,7 @@
 
 constexpr int kBlk = 32;      // sources per block (one warp stages one block)
 constexpr int kChunk = 128;   // targets per tile (4 per lane of a warp, as 2 packed pairs)
+constexpr int kSymMaxEntriesPerTile = 128;   // the symmetric product is used below this mean list length
 
 // A list of (target tile, source block) work: entries of a tile are contiguous,
 // split into segments (one CTA each) when there are too few tiles to fill the GPU.
@@ -94,6 +95,18 @@ struct rbf_plan {
     PBuf<int2> tiles;            // target tiles: (start, count), runs of <= kChunk per cell
     PBuf<float4> chk_lo, chk_hi;
     PairList pl;
+    // Symmetric form of the product (tensor-core Gaussian plans whose pair list averages
+    // fewer than kSymMaxEntriesPerTile entries per tile): the entries (T, b) of pl
+    // whose block lies in tile T itself ("diagonal": T's rows only) or in a later tile
+    // ("upper", ebi.y bit 16: T's rows and, transposed, the block's rows); entries whose
+    // block lies in an earlier tile are left out - the other side takes them.
+    bool sym_ready = false;
+    PairList sym;
+    PBuf<int32_t> tile_of;       // n: tile holding binned position i
+    int64_t sym_upper = 0;       // upper entries
+    PBuf<int32_t> sym_src;       // sym_upper: upper entry indices ordered by block (stable)
+    PBuf<int32_t> sym_bstart, sym_bend;   // nblk + 1: block b's upper entries [start, end) in sym_src
+    PBuf<float> colpart;         // sym.len x kBlk: per upper entry, the block's transposed partial sums
 
     // work vectors (binned order)
     PBuf<float> zs, ys;
@@ -129,6 +142,9 @@ void permute_to_binned_f64_to_f32(const rbf_plan *P, const double *in, float *ou
 void permute_to_binned_f64(const rbf_plan *P, const double *in, double *out, cudaStream_t s);
 void permute_from_binned_f32(const rbf_plan *P, const float *in, float *out, cudaStream_t s);
 void permute_from_binned_f64(const rbf_plan *P, const double *in, double *out, cudaStream_t s);
+
+// plan.cu: the symmetric sub-list of P->pl (see rbf_plan::sym); called by plan_build.
+void build_symmetric(rbf_plan *P, cudaStream_t s);
 
 // matvec.cu
 void matvec_binned(rbf_plan *P, const float *zs, float *ys, cudaStream_t s);

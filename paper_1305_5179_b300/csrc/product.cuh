@@ -49,6 +49,7 @@ struct MvArgs {
     float scl, R;
     float *out;          // y (binned) or grid f, for tiles with a single segment
     float *partial;      // [seg][kChunk] partial sums of split tiles
+    float *colpart;      // symmetric form: [entry][kBlk] transposed sums of upper entries
     // grid targets: bricks of 2^blog[0] x 2^blog[1] x 2^blog[2] = 128 nodes (bdim[d] bricks along
     // axis d), each cut into four quarters of 2^qlog[0] x 2^qlog[1] x 2^qlog[2] = 32 nodes
     float glo[3], gstep[3];
@@ -255,3 +256,7 @@ __device__ __forceinline__ void product_segment(const MvArgs &a, const int4 sg, 
 
 // product_tc.cu: the same product with the exponents from tcgen05.mma (pl.nseg CTAs).
 void product_tc_launch(const rbf_plan *P, const PairList &pl, const rbfk::MvArgs &a, bool grid, cudaStream_t s);
+// The symmetric form over P->sym (a.seg, a.ent, a.ebi from P->sym, a.colpart = P->colpart),
+// then, after the split tiles' segments are reduced, the gather of the transposed sums.
+void product_tc_sym_launch(const rbf_plan *P, const rbfk::MvArgs &a, cudaStream_t s);
+void product_tc_sym_gather(const rbf_plan *P, float *ys, cudaStream_t s);

@@ -59,9 +59,14 @@ constexpr int kL = 128;     // pair-list entries staged per chunk (4 per produce
 constexpr int kR = 8;       // depth of the cp.async ring of raw source data
 static_assert(kL > kR && kL % 32 == 0, "staging depths");
 
+constexpr int kTr = 36;     // row stride (floats) of a consumer warp's transpose tile
+
 struct TcSmem {
     uint8_t a[kABytes];
     uint8_t b[kStages][kBBytes];
+    float tr[kCons][kBlk][kTr];          // symmetric form: [source][target lane] exponentials
+    float zt[kCons][32];                 // symmetric form: the warp's own target weights
+    float col[kStages][kCons][kBlk];     // symmetric form: each warp's transposed partial sums
     float4 rpos[kProd][kR][kBlk];
     float rz[kProd][kR][kBlk];
     float z[kStages][kBlk];
@@ -101,6 +106,26 @@ __device__ __forceinline__ void put4(uint8_t *base, int row, int chunk, float x,
     *reinterpret_cast<float4 *>(base + core_off(row, chunk)) = make_float4(x, y, z, w);
 }
 
+// the exponentials of targets lane x sources 4g .. 4g + 3 into column `lane` of the tile
+__device__ __forceinline__ void put_t(float *tcol, int g, f2 e0, f2 e1) {
+    float x0, x1, x2, x3;
+    upk(e0, x0, x1);
+    upk(e1, x2, x3);
+    tcol[(4 * g) * kTr] = x0;
+    tcol[(4 * g + 1) * kTr] = x1;
+    tcol[(4 * g + 2) * kTr] = x2;
+    tcol[(4 * g + 3) * kTr] = x3;
+}
+
+// Symmetric form: the transposed sums of the block that used stage s (entry e of the list),
+// the four consumer warps' partials added in a fixed order; nothing for a diagonal entry.
+__device__ __forceinline__ void combine_columns(const MvArgs &a, TcSmem &S, int s, int64_t e, int lane) {
+    if ((S.flag[s] >> 16) & 1) {
+        const float v = ((S.col[s][0][lane] + S.col[s][1][lane]) + S.col[s][2][lane]) + S.col[s][3][lane];
+        a.colpart[e * kBlk + lane] = v;
+    }
+}
+
 __device__ __forceinline__ void raise_error(TcSmem &S, unsigned *err) {
     *(volatile int *)&S.abort = 1;
     if (err) atomicOr(err, 1u);
@@ -108,8 +133,9 @@ __device__ __forceinline__ void raise_error(TcSmem &S, unsigned *err) {
 
 // One segment sg of a pair list; `slot` indexes its row of partial sums when its tile
 // has more than one segment.  Run by a whole CTA of kThreadsTc threads.
-template <bool kGrid>
+template <bool kGrid, bool kSym = false>
 __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, int64_t slot, unsigned *err) {
+    static_assert(!(kGrid && kSym), "grid targets carry no weights: the symmetric form is for products");
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     TcSmem &S = *reinterpret_cast<TcSmem *>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -146,6 +172,7 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
         }
         if (lane == 0)
             for (int d = 0; d < 6; ++d) S.box[warp][d] = b6[d];
+        if (kSym) S.zt[warp][lane] = valid ? a.w[oi] : 0.f;
     }
     tc5::fence_before_sync();
     __syncthreads();
@@ -248,6 +275,11 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
                 raise_error(S, err);
                 break;
             }
+            if (kSym && b >= kStages) {
+                // block b - kStages (this producer's) left its consumers' transposed partials here
+                combine_columns(a, S, s, sg.y + b - kStages, lane);
+                __syncwarp();      // every lane has read the old flag before it is replaced
+            }
             if (lane == 0) S.flag[s] = e.y;
             if (((e.y >> 8) & 0xff) == 0) {   // no quarter of the tile meets this block: no MMA
                 __syncwarp();
@@ -282,6 +314,20 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
             issued = b;
             __syncwarp();
         }
+        if (kSym && !*(volatile int *)&S.abort) {
+            // this producer's last blocks: their stages are not reused, so wait for their
+            // consumers here and combine
+            for (int jj = my_nb > 2 ? my_nb - 2 : 0; jj < my_nb; ++jj) {
+                const int b = pw + kProd * jj;
+                if (b + kStages < nb) continue;
+                const int s = b % kStages;
+                if (!tc5::mbar_wait(&S.empty[s], (uint32_t)(b / kStages) & 1u, &S.abort, kWaitNs)) {
+                    raise_error(S, err);
+                    break;
+                }
+                combine_columns(a, S, s, sg.y + b, lane);
+            }
+        }
         tc5::cp_async_wait_all();
         if (issued >= 0 && lane == 0 && *(volatile int *)&S.abort) {
             // let the MMAs already issued finish before the tensor memory is released
@@ -304,7 +350,9 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
                 break;
             }
             const int code = (S.flag[s] >> (8 + 2 * warp)) & 3;   // this warp's quarter vs the block
+            const bool upper = kSym && ((S.flag[s] >> 16) & 1);
             if (code == 0) {
+                if (upper) S.col[s][warp][lane] = 0.f;       // the quarter meets no source of the block
                 __syncwarp();
                 if (lane == 0) tc5::mbar_arrive(&S.empty[s]);
                 continue;
@@ -313,6 +361,7 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
             float tv[32];
             tc5::tmem_ld_32x32(trow + (uint32_t)(s * kBlk), tv);
             const float4 *zz = reinterpret_cast<const float4 *>(S.z[s]);
+            float *tcol = &S.tr[warp][0][lane];             // column `lane` of the transpose tile
             if (code == 2) {
 #pragma unroll
                 for (int g = 0; g < 8; ++g) {
@@ -321,6 +370,7 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
                     const f2 e1 = ex2_pair(tv[4 * g + 2], tv[4 * g + 3]);
                     acc[2 * (g & 1)] = fma2(e0, pk(Z.x, Z.y), acc[2 * (g & 1)]);
                     acc[2 * (g & 1) + 1] = fma2(e1, pk(Z.z, Z.w), acc[2 * (g & 1) + 1]);
+                    if (upper) put_t(tcol, g, e0, e1);
                 }
             } else {
 #pragma unroll
@@ -328,10 +378,29 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
                     const float4 Z = zz[g];
                     const float t0 = tv[4 * g], t1 = tv[4 * g + 1], t2 = tv[4 * g + 2], t3 = tv[4 * g + 3];
                     const f2 m0 = gt_pair(t0, t1, thr), m1 = gt_pair(t2, t3, thr);
-                    const f2 e0 = ex2_pair(t0, t1), e1 = ex2_pair(t2, t3);
-                    acc[2 * (g & 1)] = fma2(e0, mul2(m0, pk(Z.x, Z.y)), acc[2 * (g & 1)]);
-                    acc[2 * (g & 1) + 1] = fma2(e1, mul2(m1, pk(Z.z, Z.w)), acc[2 * (g & 1) + 1]);
+                    const f2 e0 = mul2(ex2_pair(t0, t1), m0), e1 = mul2(ex2_pair(t2, t3), m1);
+                    acc[2 * (g & 1)] = fma2(e0, pk(Z.x, Z.y), acc[2 * (g & 1)]);
+                    acc[2 * (g & 1) + 1] = fma2(e1, pk(Z.z, Z.w), acc[2 * (g & 1) + 1]);
+                    if (upper) put_t(tcol, g, e0, e1);
                 }
+            }
+            if (upper) {
+                // source `lane` of the block: sum over this warp's 32 targets of a_ij z_i
+                __syncwarp();
+                const float4 *row = reinterpret_cast<const float4 *>(&S.tr[warp][lane][0]);
+                const float4 *zw = reinterpret_cast<const float4 *>(S.zt[warp]);
+                f2 ca = 0ull, cb = 0ull;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float4 R = row[q], Zi = zw[q];
+                    ca = fma2(pk(R.x, R.y), pk(Zi.x, Zi.y), ca);
+                    cb = fma2(pk(R.z, R.w), pk(Zi.z, Zi.w), cb);
+                }
+                float c0, c1, c2, c3;
+                upk(ca, c0, c1);
+                upk(cb, c2, c3);
+                S.col[s][warp][lane] = (c0 + c1) + (c2 + c3);
+                __syncwarp();       // the tile is rewritten by the next block
             }
             tc5::fence_before_sync();
             __syncwarp();
@@ -359,6 +428,27 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
 template <bool kGrid>
 __global__ void __launch_bounds__(kThreadsTc, 4) k_product_tc(MvArgs a, unsigned *err) {
     product_tc_body<kGrid>(a, a.seg[blockIdx.x], blockIdx.x, err);
+}
+
+// the symmetric form over rbf_plan::sym (row sums as above, transposed sums per entry)
+__global__ void __launch_bounds__(kThreadsTc, 4) k_product_tc_sym(MvArgs a, unsigned *err) {
+    product_tc_body<false, true>(a, a.seg[blockIdx.x], blockIdx.x, err);
+}
+
+// y[source] += the transposed sums of its block over the block's upper entries, in the
+// entries' order (one warp per block)
+__global__ void k_sym_gather(const int2 *__restrict__ blk, int64_t nblk, const int32_t *__restrict__ bstart,
+                             const int32_t *__restrict__ bend, const int32_t *__restrict__ src,
+                             const float *__restrict__ colpart, float *__restrict__ y) {
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= nblk) return;
+    const int s0 = bstart[b], s1 = bend[b];
+    if (s1 <= s0) return;
+    float acc = 0.f;
+    for (int q = s0; q < s1; ++q) acc += colpart[(int64_t)src[q] * kBlk + lane];
+    const int2 bl = blk[b];
+    if (lane < bl.y) y[bl.x + lane] += acc;
 }
 
 // Many problems at once: CTA = one (problem, segment) item of a batch.
@@ -400,6 +490,11 @@ void set_smem_attr(int device) {
 void product_tc_prepare(int device) {
     set_smem_attr<false>(device);
     set_smem_attr<true>(device);
+    static bool done_sym[64] = {};
+    if (device >= 0 && device < 64 && !done_sym[device]) {
+        RBF_CUDA(cudaFuncSetAttribute(k_product_tc_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTc));
+        done_sym[device] = true;
+    }
     static bool done[64] = {};
     if (device >= 0 && device < 64 && !done[device]) {
         RBF_CUDA(cudaFuncSetAttribute(k_bproduct_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTc));
@@ -426,5 +521,22 @@ void product_tc_launch(const rbf_plan *P, const PairList &pl, const rbfk::MvArgs
         set_smem_attr<false>(P->ctx->device);
         k_product_tc<false><<<(unsigned)pl.nseg, kThreadsTc, kSmemTc, s>>>(a, err);
     }
+    RBF_LAUNCHED();
+}
+
+// The symmetric product over P->sym (see rbf_plan::sym): the kernel writes each tile's row
+// sums (or its segments' partial sums) and the upper entries' transposed sums; after the
+// segments are reduced, the gather adds the transposed sums to the sources' rows.
+void product_tc_sym_launch(const rbf_plan *P, const rbfk::MvArgs &a, cudaStream_t s) {
+    if (P->sym.nseg <= 0) return;
+    product_tc_prepare(P->ctx->device);
+    k_product_tc_sym<<<(unsigned)P->sym.nseg, kThreadsTc, kSmemTc, s>>>(a, ctx_error_word(P->ctx));
+    RBF_LAUNCHED();
+}
+
+void product_tc_sym_gather(const rbf_plan *P, float *ys, cudaStream_t s) {
+    if (P->nblk <= 0 || P->sym_upper <= 0) return;
+    k_sym_gather<<<(unsigned)ceil_div(P->nblk * 32, 256), 256, 0, s>>>(P->blk.p, P->nblk, P->sym_bstart.p,
+                                                                        P->sym_bend.p, P->sym_src.p, P->colpart.p, ys);
     RBF_LAUNCHED();
 }

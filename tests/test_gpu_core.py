@@ -370,6 +370,37 @@ def test_fgmres_first_iterations_match_oracle(ctx, rbf, sphere_c1):
     assert rel2(A @ x.cpu().numpy(), A @ xo) <= 1e-4
 
 
+def test_symmetric_product_on_a_sparse_sphere(ctx, rbf):
+    """Short pair lists (sigma = the spacing of a golden-spiral sphere: about 40 entries per
+    tile) select the symmetric form of the tensor-core product, in which each in-range pair
+    is evaluated once and its transposed share is added to the source's row.  Checked
+    against the oracle's float64 rows (1e-5), the CUDA-core product (which evaluates every
+    pair from both sides; 3e-6) and itself (bitwise, call to call)."""
+    N = 20_000
+    cl = synth.fibonacci_sphere(N)
+    h = math.sqrt(4 * math.pi / N)
+    C, _ = oracle.build_centers(cl.points, cl.normals, 2.8 * h)
+    Cd, C64 = c4(C)
+    sigma = float(F32(h))
+    plan = rbf.Plan(ctx, Cd, sigma=sigma, k=6.0)
+    info = plan.info()
+    assert info["symmetric"] == 1 and info["pairlist_len"] < 128 * info["nchunks"]
+    z = torch.from_numpy(np.random.default_rng(3).standard_normal(len(C)).astype(np.float32)).cuda()
+    y1 = plan.matvec(z)
+    y2 = plan.matvec(z)
+    assert torch.equal(y1, y2)
+    rows = np.random.default_rng(4).choice(len(C), 3000, replace=False)
+    y64, _ = oracle.kernel_rows(C64, z.double().cpu().numpy(), sigma, 6.0, rows)
+    y = y1.double().cpu().numpy()
+    assert rel2(y[rows], y64) <= 1e-5
+    ys = rbf.Plan(ctx, Cd, sigma=sigma, k=6.0, product="simt").matvec(z).double().cpu().numpy()
+    assert rel2(y, ys) <= 3e-6
+    # the torus patch of the scan configuration has long lists: both sides
+    _, Ct, _ = torus_patch(theta=0.2)
+    Ctd, _ = c4(Ct)
+    assert rbf.Plan(ctx, Ctd, sigma=0.02, k=6.0).info()["symmetric"] == 0
+
+
 def test_c1_fgmres_history_follows_the_oracle_over_150_iterations(ctx, rbf, sphere_c1, capsys):
     """Config 1 (4,500 centres, sigma 0.1, untruncated, no preconditioner): the GPU's
     FGMRES(50) residual estimates after 10 ... 150 iterations (three restart cycles)
