@@ -33,9 +33,9 @@ namespace {
 
 constexpr int kGT = 128;                     // threads: 4 warps, one per 32 accumulator lanes
 constexpr int kBM = 128;                     // rows of A (and of C) per CTA
-constexpr int kBK = 32;                      // K per stage
+constexpr int kBK = 16;                      // K per stage (small stages: 4-5 CTAs per SM hide latency)
 constexpr uint32_t kLbo = 128;               // next 16-byte K chunk of the same 8 rows
-constexpr uint32_t kSbo = (kBK / 4) * 128;   // next group of 8 rows: 8 chunks of 128 bytes
+constexpr uint32_t kSbo = (kBK / 4) * 128;   // next group of 8 rows: kBK / 4 chunks of 128 bytes
 constexpr uint64_t kWaitNs = 1000000000ull;
 
 __host__ __device__ constexpr int tile_bytes(int rows) { return rows / 8 * (int)kSbo; }
@@ -163,20 +163,23 @@ __global__ void __launch_bounds__(kGT) k_gemm_tc(GemmArgs g, const float *__rest
     const int nch = (g.K + kBK - 1) / kBK;
     const int c0 = blockIdx.z * g.kslice, c1 = min(nch, c0 + g.kslice);
     const TB *Bn = B + (int64_t)n0 * g.b_sr;
-    Stager<float, kACont, kBM> sa;
-    Stager<TB, kBCont, kBN> sb;
+    // two register sets: chunk c + 1's loads are in flight while chunk c is converted
+    Stager<float, kACont, kBM> sa0, sa1;
+    Stager<TB, kBCont, kBN> sb0, sb1;
     int last = -1;   // last chunk whose MMAs were committed
-    for (int c = c0; c < c1; ++c) {
+    auto step = [&](Stager<float, kACont, kBM> &ca, Stager<TB, kBCont, kBN> &cb, Stager<float, kACont, kBM> &na,
+                    Stager<TB, kBCont, kBN> &nb, int c) -> bool {
         const int j = c - c0, s = j & 1;
         uint8_t *ahi = smem + s * L::kStage, *alo = ahi + L::kA, *bhi = ahi + 2 * L::kA;
         uint8_t *blo = L::kSplitB ? bhi + L::kB : nullptr;
-        const int k0 = c * kBK;
-        sa.load(A, g.a_sr, g.a_sk, m0, g.M, k0, g.K);
-        sb.load(Bn, g.b_sr, g.b_sk, 0, g.N - n0, k0, g.K);
+        if (c + 1 < c1) {
+            na.load(A, g.a_sr, g.a_sk, m0, g.M, (c + 1) * kBK, g.K);
+            nb.load(Bn, g.b_sr, g.b_sk, 0, g.N - n0, (c + 1) * kBK, g.K);
+        }
         // the MMAs of chunk c - 2 read this stage: wait until they are done
-        if (j >= 2 && !wait_all(&done[s], (uint32_t)((j - 2) >> 1) & 1u, abort_flag, kWaitNs, err)) break;
-        sa.store(ahi, alo);
-        sb.store(bhi, blo);
+        if (j >= 2 && !wait_all(&done[s], (uint32_t)((j - 2) >> 1) & 1u, abort_flag, kWaitNs, err)) return false;
+        ca.store(ahi, alo);
+        cb.store(bhi, blo);
         tc5::fence_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -187,14 +190,23 @@ __global__ void __launch_bounds__(kGT) k_gemm_tc(GemmArgs g, const float *__rest
             const uint64_t dbl = L::kSplitB ? tc5::smem_desc(tc5::smem_u32(blo), kLbo, kSbo) : 0ull;
 #pragma unroll
             for (int i = 0; i < kBK / 8; ++i) {
-                const uint64_t step = (uint64_t)((i * 2 * kLbo) >> 4);   // two 16-byte chunks per K step of 8
-                tc5::mma_tf32(tmem, da + step, db + step, kIdesc, (j > 0 || i > 0) ? 1u : 0u);
-                if (kProducts >= 2) tc5::mma_tf32(tmem, dal + step, db + step, kIdesc, 1u);
-                if (kProducts >= 3) tc5::mma_tf32(tmem, da + step, dbl + step, kIdesc, 1u);
+                const uint64_t st = (uint64_t)((i * 2 * kLbo) >> 4);   // two 16-byte chunks per K step of 8
+                tc5::mma_tf32(tmem, da + st, db + st, kIdesc, (j > 0 || i > 0) ? 1u : 0u);
+                if (kProducts >= 2) tc5::mma_tf32(tmem, dal + st, db + st, kIdesc, 1u);
+                if (kProducts >= 3) tc5::mma_tf32(tmem, da + st, dbl + st, kIdesc, 1u);
             }
             tc5::mma_commit(&done[s]);
         }
         last = j;
+        return true;
+    };
+    if (c0 < c1) {
+        sa0.load(A, g.a_sr, g.a_sk, m0, g.M, c0 * kBK, g.K);
+        sb0.load(Bn, g.b_sr, g.b_sk, 0, g.N - n0, c0 * kBK, g.K);
+    }
+    for (int c = c0; c < c1; c += 2) {
+        if (!step(sa0, sb0, sa1, sb1, c)) break;
+        if (c + 1 < c1 && !step(sa1, sb1, sa0, sb0, c + 1)) break;
     }
     // the accumulator is complete when the last committed chunk's MMAs are (after an
     // abort, wait a shorter bounded time so that no MMA is in flight at the release)
@@ -271,7 +283,13 @@ void launch(const GemmArgs &g0, const float *A, const TB *B, unsigned *err, cuda
     constexpr int smem = GemmSmem<kBN, kProducts>::kBytes;
     static_assert(smem <= 227 * 1024, "shared memory");
     auto k = k_gemm_tc<kBN, kProducts, TB, kACont, kBCont>;
-    RBF_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    static bool attr_set[64] = {};      // once per device and kernel instance
+    int dev = 0;
+    RBF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        RBF_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
     if (g0.M <= 0) return;
     GemmArgs g = g0;
     const int mt = (g.M + kBM - 1) / kBM, nt = (g.N + kBN - 1) / kBN, nch = (g.K + kBK - 1) / kBK;
