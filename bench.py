@@ -76,12 +76,12 @@ WORKLOADS = {
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_product_tc launch on the
-# 3,000,000-centre torus, from one ncu capture of the product on the torus sector, scaled to the
-# full operator; valid only while the kernel sources hash to the values it was taken with.
-PRODUCT_TRAFFIC = {"torus1m": (156.81e6 + 8.98e6, {
-    "paper_1305_5179_b300/csrc/product_tc.cu": "9328d403021bb0d483177592c0f0177f86d64a8eb11dec7b8a16950a78928c77",
+# 3,000,000-centre torus (one-pass metrics on the full-size launch); valid only while the kernel
+# sources hash to the values it was taken with.
+PRODUCT_TRAFFIC = {"torus1m": (156.52e6 + 10.07e6, {
+    "paper_1305_5179_b300/csrc/product_tc.cu": "af30da94f9bbf22875cb47290b291147a88bfb0fd08b61863b416154a996fe24",
     "paper_1305_5179_b300/csrc/tcgen05.cuh": "b0f1821451b34e230cdc5000e9e34c3b6ce5dd95aef3f1df5a956d533ea2386e",
-    "paper_1305_5179_b300/csrc/product.cuh": "7da831b5eec7623181f7ab2ce78e05d90a3d41ff301a2883871a3679935d138c"})}
+    "paper_1305_5179_b300/csrc/product.cuh": "e793bc700199cc2a36a625bb5a949b6237eb09c9ec0bc3cc739be67cf19dc008"})}
 
 # DRAM bytes of one k_spmv_csr launch per byte of its algorithmic traffic, from one ncu capture on
 # the 0.05-radian sector (23,871 centres, 514 MB of CSR):
