@@ -67,6 +67,12 @@ WORKLOADS = {
                         "plain, RAS and learned FGMRES(50)",
                    N=1_000_000, delta=0.01, k=6.0, tol=1e-6, max_it=300, m=50, lam=1e-2, samples=16384,
                    epochs=20),
+    "sphere_products": dict(desc="products of the truncated operator on the 200,000-point golden-spiral sphere "
+                                 "(600,000 centres, sigma = the mean spacing, delta = 0.01 sqrt(10^6 / N), k = 6): "
+                                 "short pair lists, so the symmetric tensor-core product", N=200_000, k=6.0, reps=20),
+    "mlp_layers": dict(desc="the learned preconditioner's network on the tensor cores: inference over 46,875 blocks "
+                            "(the 3,000,000-centre sphere's 64-centre subdomains) and a training step of 512",
+                       rows=46_875, batch=512, reps=10),
     "sphere1500": dict(desc="unit sphere N=1,500 -> 4,500 centres, untruncated", N=1500, delta=0.05, sigma=0.1,
                        k=0.0, grid=64, core=96, block=128, shift=1e-4, iters=50, m=50, precond="none"),
     "batch512": dict(desc="512 ellipsoids/tori, log-uniform 500-20,000 points each, delta 0.02, "
@@ -686,6 +692,89 @@ def run_tol(args, wl):
     return 0
 
 
+def run_sphere_products(args, wl):
+    """Products y = A~ z on a golden-spiral sphere at sigma = the spacing (the symmetric form):
+    algorithmic pair evaluations per second, CUDA events around `reps` products."""
+    import torch
+    import paper_1305_5179_b300 as rbf
+    import synth
+
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    ctx = rbf.Context(local)
+    N = wl["N"]
+    cl = synth.fibonacci_sphere(N)
+    C, _, _ = rbf.build_centers(ctx, torch.from_numpy(cl.points).cuda(), torch.from_numpy(cl.normals).cuda(),
+                                delta=0.01 * math.sqrt(1e6 / N))
+    plan = rbf.Plan(ctx, C, sigma=math.sqrt(4 * math.pi / N), k=wl["k"])
+    z = torch.randn(plan.n, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    for _ in range(max(3, args.warmup)):
+        plan.matvec(z)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = rbf.launch_count()
+    e0.record()
+    for _ in range(wl["reps"]):
+        plan.matvec(z)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / wl["reps"]
+    pairs = plan.count_pairs()
+    info = plan.info()
+    if rank == 0:
+        print(json.dumps({"metric": "RBF pair-evals/s in matvec", "value": pairs / (ms * 1e-3), "unit": UNIT,
+                          "n_gpus": 1, "steps": wl["reps"], "warmup": max(3, args.warmup), "ms_per_step": ms,
+                          "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": wl["desc"], "centres": plan.n, "pairs_per_matvec": pairs,
+                                     "entries_per_tile": info["pairlist_len"] / max(1, info["nchunks"]),
+                                     "symmetric": info["symmetric"]},
+                          "gpu_launches": rbf.launch_count() - l0}))
+    return 0
+
+
+def run_mlp_layers(args, wl):
+    """The network's tensor-core contractions: a BF16-weight inference pass over `rows` blocks
+    and a float32 loss-and-gradient step of `batch` samples, CUDA events."""
+    import torch
+    import paper_1305_5179_b300 as rbf
+    import synth
+
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    ctx = rbf.Context(local)
+    net = rbf.MLP(ctx, synth.mlp_init(seed=1))
+    g = torch.Generator("cuda").manual_seed(0)
+    X = torch.randn(wl["rows"], 256, device="cuda", generator=g)
+    Xb = torch.randn(wl["batch"], 256, device="cuda", generator=g)
+    T = torch.randn(wl["batch"], 64, device="cuda", generator=g)
+    for _ in range(max(3, args.warmup)):
+        net.forward(X, bf16=True)
+        net.loss_grad(Xb, T)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(wl["reps"]):
+        net.forward(X, bf16=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_fwd = e0.elapsed_time(e1) / wl["reps"]
+    t0 = time.perf_counter()
+    for _ in range(wl["reps"]):
+        net.loss_grad(Xb, T)
+    ms_step = 1e3 * (time.perf_counter() - t0) / wl["reps"]
+    macs = wl["rows"] * (256 * 256 + 256 * 256 + 256 * 64)
+    if rank == 0:
+        print(json.dumps({"metric": "MLP inference MAC/s (tensor cores, tf32 head and tail of the activations x "
+                                    "BF16 weights)", "value": macs / (ms_fwd * 1e-3), "unit": "MAC/s",
+                          "n_gpus": 1, "steps": wl["reps"], "warmup": max(3, args.warmup), "ms_per_step": ms_fwd,
+                          "higher_is_better": True, "dtype": "tf32 x2 (activations), bf16 (weights), f32 accumulate",
+                          "data": "synthetic", "config": {"workload": wl["desc"]},
+                          "training_step_ms_host": ms_step}))
+    return 0
+
+
 def run_density(args, wl):
     """Row f1: the density measures that choose sigma (rbf_density_measures) on the C2
     cloud: N nearest-neighbour queries plus M probe queries per step."""
@@ -1002,6 +1091,13 @@ def main():
         return 0
     if args.workload == "batch512":
         return run_batch(args, wl)
+    if args.workload in ("sphere_products", "mlp_layers"):
+        if args.impl == "reference":
+            if int(os.environ.get("RANK", "0")) == 0:
+                print(json.dumps({"impl": "reference", "workload": args.workload,
+                                  "unavailable": "no oracle leg for this workload; run --workload torus1m"}))
+            return 0
+        return run_sphere_products(args, wl) if args.workload == "sphere_products" else run_mlp_layers(args, wl)
     if args.workload == "density":
         return run_density_reference(args, wl) if args.impl == "reference" else run_density(args, wl)
     if args.workload == "isosurface":
