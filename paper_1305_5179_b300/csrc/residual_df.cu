@@ -428,7 +428,9 @@ void tile_of_launch(const int2 *tiles, int64_t ntiles, int32_t *tile_of, cudaStr
 
 void residual_binned_df(rbf_plan *P, const float *bs, const double *xs, double *rs, cudaStream_t s) {
     upload_table(P->ctx->device, s);
-    const PairList &pl = P->pl;
+    // A plan with the symmetric sub-list walks it: it holds exactly the entries this kernel does
+    // not skip (block in the same or a later tile), in the same order within each tile.
+    const PairList &pl = P->sym_ready ? P->sym : P->pl;
     DfConst kc;
     split(1.4426950408889634 * P->inv2s2_64, kc.Ch, kc.Cl);
     split(0.6931471805599453, kc.Lh, kc.Ll);
@@ -440,18 +442,22 @@ void residual_binned_df(rbf_plan *P, const float *bs, const double *xs, double *
     }
     DevBuf<double> part;
     if (pl.any_split) part.alloc((size_t)pl.nseg * kChunk, s);
-    DevBuf<int32_t> tile_of;
+    DevBuf<int32_t> tile_of_own;
     DevBuf<unsigned long long> fix;
-    tile_of.alloc(P->n, s);
     fix.alloc(2 * (size_t)P->n, s);
     fix.zero(s);
-    if (pl.ntiles > 0) {
-        k_tile_of<<<(unsigned)pl.ntiles, kChunk, 0, s>>>(P->tiles.p, tile_of.p);
-        RBF_LAUNCHED();
+    const int32_t *tile_of = P->tile_of.p;
+    if (!P->sym_ready) {
+        tile_of_own.alloc(P->n, s);
+        tile_of = tile_of_own.p;
+        if (pl.ntiles > 0) {
+            k_tile_of<<<(unsigned)pl.ntiles, kChunk, 0, s>>>(P->tiles.p, tile_of_own.p);
+            RBF_LAUNCHED();
+        }
     }
     if (pl.nseg > 0) {
         k_resid_df_sym<<<(unsigned)pl.nseg, kT, 0, s>>>(P->pos.p, P->tiles.p, xs, P->blk.p, pl.ent.p, pl.ebi.p,
-                                                        pl.seg.p, tile_of.p, kc, bs, rs, part.p, fix.p,
+                                                        pl.seg.p, tile_of, kc, bs, rs, part.p, fix.p,
                                                         fix_share_limit(pl.ntiles), ctx_error_word(P->ctx));
         RBF_LAUNCHED();
     }
