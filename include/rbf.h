@@ -19,6 +19,8 @@
  *     multiplies every weight by the same constant and leaves P_f unchanged.
  *   - Truncation.  With cut-off factor k > 0 the operator keeps the pairs with
  *     |c_i - c_j| < k sigma (strict); every dropped entry is below exp(-k^2/2).
+ *     (For k >= 5.77 the tensor-core product also keeps some pairs just beyond
+ *     the radius, whose entries are below 2^-24: see rbf_matvec.)
  *     k = 0 means untruncated (dense).  0 <= k <= 12.
  *   - Centres.  float4 per centre (x, y, z, unused), 16-byte aligned, in the
  *     order [X; X+; X-] that rbf_build_centers writes (Sec. II.A.1).
@@ -204,9 +206,16 @@ rbf_status rbf_plan_export_binning(rbf_plan *plan, int32_t *perm, uint32_t *keys
  * The truncated product y = A~ z (Sec. III.A, Eq. matrixEntries), float32
  * arithmetic with exp2 on the special-function unit, caller order.
  *   z, y : n float each (may not alias).
- * Per-pair error: relative ~1e-6 of the term; the cut-off decision is taken in
- * float32 and can differ from an exact one only for pairs within rounding of
- * the cut-off radius, whose entries are <= exp(-k^2/2). */
+ * Per-pair error: relative ~1e-6 of the term.  Cut-off: the CUDA-core product
+ * (RBF_PRODUCT_SIMT) tests every pair in float32 (it can differ from an exact
+ * test only within rounding of the radius).  The tensor-core product
+ * (RBF_PRODUCT_TC) tests them too when exp(-k^2/2) >= 2^-24 (k < 5.77); for
+ * k >= 5.77 it sums every pair of each (32-target quarter, 32-source block)
+ * combination that the plan could not exclude, so besides every pair within
+ * k sigma it includes pairs of straddling combinations just beyond it, each of
+ * entry below exp(-k^2/2) < 2^-24 - below float32's resolution of the unit
+ * diagonal and below the truncation bound itself.  The pair counts, the
+ * residuals and the assembled matrix use the strict cut-off. */
 rbf_status rbf_matvec(rbf_plan *plan, const float *z, float *y, void *stream);
 
 /* Number of algorithmic pairs (i, j) with |c_i - c_j| < k sigma, i = j included
@@ -217,7 +226,7 @@ rbf_status rbf_count_pairs(rbf_plan *plan, int64_t *count, void *stream);
 /* Number of (target, source) pairs the tensor-core product evaluates: for every
  * pair-list entry, each quarter of 32 targets of its tile whose box test does not
  * exclude the block, times the block's sources (pairs beyond the cut-off inside
- * such quarter-block combinations are evaluated and masked).  Divided by
+ * such quarter-block combinations are evaluated and kept, see rbf_matvec).  Divided by
  * rbf_count_pairs it is the product's waste ratio (>= 1; n^2 / n^2 = 1 when every
  * pair is kept).  `count` is host memory; synchronises `stream`. */
 rbf_status rbf_count_candidate_pairs(rbf_plan *plan, int64_t *count, void *stream);

@@ -13,8 +13,8 @@
 //      B_j = [Hx Lx Hx Hy | Ly Hy Hz Lz | Hz qh ql 1 | 1 0 0 0]
 // (h, l of u_i; H, L of 2 v_j; p = -|u_i|^2, q = -|v_j|^2).  Two
 // tcgen05.mma (M = 128, N = 32, K = 8) write the 128 x 32 exponents to tensor
-// memory; the CUDA cores then only evaluate MUFU.EX2, the cut-off test and the
-// weighted sum.  The exponent is never positive, so no overflow guard is needed.
+// memory; the CUDA cores then only evaluate MUFU.EX2 and the weighted sum.  The
+// exponent is never positive, so no overflow guard is needed.
 //
 // CTA = one segment of a tile's pair list, 6 warps.  Warps 4 and 5 (producers,
 // alternate blocks) build the B operand of a block in shared memory (one source
@@ -22,10 +22,13 @@
 // (consumers) each
 // own 32 targets (TMEM lanes 32w..32w+31), read their 32 x 32 exponents,
 // and accumulate z_j 2^t over the segment.  The pair list carries, per block, a
-// 2-bit code for each quarter of 32 targets (box tests on the quarter's box): a
-// consumer skips a block its quarter cannot reach, tests pairs against the cut-off
-// only when some may fail it, and a producer issues no MMA for a block no quarter
-// reaches.  full[s] completes when the stage's
+// 2-bit code for each quarter of 32 targets (box tests on the quarter's box, refined
+// pair by pair): a consumer skips a block its quarter cannot reach and sums the pairs
+// of the others; in a combination that straddles the cut-off it tests each pair
+// against it when the cut-off entry e^(-k^2/2) = 2^-R is at least 2^-24, and otherwise
+// (k >= 5.77, e.g. the scan configurations' k = 6) sums every pair: those beyond the
+// cut-off carry entries below float32's resolution of the unit diagonal and below the
+// truncation bound itself.  A producer issues no MMA for a block no quarter reaches.  full[s] completes when the stage's
 // MMAs have finished and the producer has written its weights; empty[s] when
 // all four consumers have read it.  Every wait is bounded (1 s); on expiry the
 // kernel raises the context's device error word and returns after freeing its
@@ -89,6 +92,7 @@ __device__ __forceinline__ f2 ex2_pair(float a, float b) {
         : "f"(a), "f"(b));
     return r;
 }
+
 __device__ __forceinline__ f2 gt_pair(float a, float b, float thr) {
     f2 r;
     asm("{\n\t.reg .f32 lo, hi;\n\tset.gt.f32.f32 lo, %1, %3;\n\tset.gt.f32.f32 hi, %2, %3;\n\t"
@@ -341,6 +345,9 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
         // ------------------------------------------------------------ consumers
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         const float thr = -a.R;      // in the cut-off iff -|u - v|^2 > -R
+        // entries beyond the cut-off are below 2^-R: with R >= 24 (k >= 5.77) they are below
+        // float32's resolution of the unit diagonal and are summed instead of tested
+        const bool mask = a.R < 24.f;
         f2 acc[4] = {0ull, 0ull, 0ull, 0ull};
         for (int b = 0; b < nb; ++b) {
             const int s = b % kStages;
@@ -362,7 +369,9 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
             tc5::tmem_ld_32x32(trow + (uint32_t)(s * kBlk), tv);
             const float4 *zz = reinterpret_cast<const float4 *>(S.z[s]);
             float *tcol = &S.tr[warp][0][lane];             // column `lane` of the transpose tile
-            if (code == 2) {
+            if (code == 2 || !mask) {
+                // every pair summed: inside the cut-off, or (mask off) beyond it with an entry
+                // below 2^-24 (see the top of the file)
 #pragma unroll
                 for (int g = 0; g < 8; ++g) {
                     const float4 Z = zz[g];
