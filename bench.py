@@ -1021,8 +1021,8 @@ def run_batch(args, wl):
         return Cs, torch.cat(bs), plans, rbf.Batch(ctx, plans)
 
     Cs, b, plans, batch = build()
-    best, scores = batch.autotune(b, candidates=(32, 64, 96, 128), m=20)
-    kw = dict(m=wl["m"], max_it=wl["iters"], precond="schwarz", core=3 * best // 4, block=best, shift=wl["shift"],
+    best, scores = batch.autotune(b, candidates=(32, 64, 96, 128), m=20, shift=wl["shift"])
+    kw = dict(m=wl["m"], max_it=wl["iters"], precond="schwarz", core=best, block=best, shift=wl["shift"],
               escalate=True)
     pairs = sum(p.count_pairs() for p in plans)
     for _ in range(args.warmup):

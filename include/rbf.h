@@ -550,10 +550,12 @@ rbf_status rbf_batch_matvec(rbf_batch *batch, const float *z, float *y, void *st
 rbf_status rbf_batch_solve(rbf_batch *batch, const float *b, const rbf_solve_params *p, double *x,
                            rbf_report *reports, rbf_batch_stats *stats, void *stream);
 
-/* Choose the Schwarz subdomain size: for each candidate block size (core = 3/4
- * of it) run a short solve (min(m, 20) iterations) of b and score it by decades
- * of worst-case residual reduction per millisecond.  *best receives the winner;
- * scores (host, ncand, may be NULL) the scores. */
+/* Choose the Schwarz subdomain size: for each candidate block size (block
+ * Jacobi: core = block, the shift of p) run a short solve (min(m, 20)
+ * iterations) of b and score it by decades of worst-case residual reduction per
+ * millisecond.  *best receives the winner; scores (host, ncand, may be NULL)
+ * the scores.  The batch keeps a Schwarz set-up between solves while core,
+ * block, shift, restricted and escalate are unchanged. */
 rbf_status rbf_batch_autotune(rbf_batch *batch, const float *b, const rbf_solve_params *p, const int *candidates,
                               int ncand, int *best, double *scores, void *stream);
 

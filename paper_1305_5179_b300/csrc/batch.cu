@@ -53,7 +53,8 @@ struct rbf_batch {
     PBuf<unsigned long long> fix;          // residual: fixed-point row accumulators (2 words each)
     int persistent_ctas = 0;
     bool tc = false;              // every plan takes the tensor-core product
-    int schwarz_block = 0;        // block size of the current Schwarz set-up (0 = none)
+    bool sz_valid = false;        // the plans hold a Schwarz set-up made with sz_p
+    rbf_schwarz_params sz_p{};
     // solve state
     int m_alloc = 0;
     PBuf<float> bs, Z, w32;
@@ -677,13 +678,18 @@ rbf_status batch_solve(rbf_batch *Bt, const float *b, const rbf_solve_params &p,
     try {
         RBF_CUDA(cudaEventRecord(e0, s));
         int failed = 0;
-        if (pc && Bt->schwarz_block != p.schwarz.block) {
+        const rbf_schwarz_params &q = p.schwarz;
+        const bool same = Bt->sz_valid && Bt->sz_p.core == q.core && Bt->sz_p.block == q.block &&
+                          Bt->sz_p.shift == q.shift && Bt->sz_p.restricted == q.restricted &&
+                          Bt->sz_p.escalate == q.escalate;
+        if (pc && !same) {
             for (auto *P : Bt->plans) {
                 int64_t f = 0;
                 schwarz_setup(P, p.schwarz, &f, s);
                 failed += (int)f;
             }
-            Bt->schwarz_block = p.schwarz.block;
+            Bt->sz_p = q;
+            Bt->sz_valid = true;
             batch_refresh_views(Bt, s);
         }
         RBF_CHECK(!pc || Bt->nsub_items > 0, RBF_ERR_INVALID, "Schwarz preconditioner not set up");
@@ -786,8 +792,8 @@ rbf_status batch_solve(rbf_batch *Bt, const float *b, const rbf_solve_params &p,
 
 int batch_autotune(rbf_batch *Bt, const float *b, const rbf_solve_params &p, const int *cands, int ncand,
                    double *scores, cudaStream_t s) {
-    // short fixed solves of each candidate subdomain size (core = 3/4 block), scored by
-    // decades of residual reduction per millisecond
+    // short fixed solves of each candidate subdomain size (block Jacobi: core = block, the
+    // caller's shift), scored by decades of residual reduction per millisecond
     DevBuf<double> xdev;
     xdev.alloc(Bt->N, s);
     int best = -1;
@@ -796,10 +802,10 @@ int batch_autotune(rbf_batch *Bt, const float *b, const rbf_solve_params &p, con
         rbf_solve_params q = p;
         q.precond = RBF_PRECOND_SCHWARZ;
         q.schwarz.block = cands[c];
-        q.schwarz.core = std::max(1, 3 * cands[c] / 4);
+        q.schwarz.core = cands[c];
         q.m = std::min(p.m > 0 ? p.m : 20, 20);
         q.max_it = q.m;
-        Bt->schwarz_block = 0;   // force set-up
+        Bt->sz_valid = false;   // force set-up
         rbf_batch_stats st{};
         batch_solve(Bt, b, q, xdev.p, nullptr, &st, s);          // set-up + capture
         batch_solve(Bt, b, q, xdev.p, nullptr, &st, s);          // timed replay
@@ -812,7 +818,7 @@ int batch_autotune(rbf_batch *Bt, const float *b, const rbf_solve_params &p, con
             best = cands[c];
         }
     }
-    Bt->schwarz_block = 0;
+    Bt->sz_valid = false;
     return best;
 }
 
