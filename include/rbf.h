@@ -333,7 +333,11 @@ typedef struct {
     int residual_mode;      /* RBF_RESIDUAL_DF (0) or RBF_RESIDUAL_F64 (1), see rbf_residual */
     rbf_mlp *mlp;           /* RBF_PRECOND_MLP: the trained network */
     float mlp_lambda;       /* RBF_PRECOND_MLP: the shift the network was trained for */
-    int mlp_initial_guess;  /* RBF_PRECOND_MLP: start from x0 = network(b) instead of 0 */
+    int mlp_initial_guess;  /* RBF_PRECOND_MLP: start from x0 = a network(b) instead of 0, with
+                               a = <b, A~ g> / <A~ g, A~ g> for g = network(b) (one more product):
+                               the scaling that minimises the starting residual, so that a poor
+                               guess is shrunk (or dropped, a = 0) instead of starting the solve
+                               above |b| */
     int assembled;          /* non-zero: the float32 products use the plan's assembled matrix
                                (rbf_plan_assemble; RBF_ERR_INVALID without one); the float64
                                true residuals stay matrix-free */
@@ -355,6 +359,10 @@ typedef struct {
     double ms_matvec;           /* summed CUDA-event time of the float32 products */
     double ms_residual;         /* summed CUDA-event time of the float64 residual products */
     double ms_precond;          /* summed CUDA-event time of the preconditioner applications */
+    double guess_scale;         /* mlp_initial_guess: the factor a applied to the network's guess g
+                                   (a minimises |b - a A~ g|; 0 when the guess was not used) */
+    double guess_residual;      /* mlp_initial_guess: |b - a A~ g| / |b| with the float32 product
+                                   (at most 1: the guess never starts above x0 = 0) */
 } rbf_report;
 
 /* Solve A~ x = b on a plan.  b: n float (caller order); x: n double (out,

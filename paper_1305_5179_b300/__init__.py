@@ -104,7 +104,7 @@ class Report(ctypes.Structure):
                 ("residual_true", ctypes.c_double), ("ms_setup", ctypes.c_double), ("ms_solve", ctypes.c_double),
                 ("matvec_pairs", ctypes.c_int64), ("matvec_launches", ctypes.c_int),
                 ("residual_launches", ctypes.c_int), ("ms_matvec", ctypes.c_double), ("ms_residual", ctypes.c_double),
-                ("ms_precond", ctypes.c_double)]
+                ("ms_precond", ctypes.c_double), ("guess_scale", ctypes.c_double), ("guess_residual", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -155,6 +155,11 @@ __global__ void k_f32_to_f64(const float *__restrict__ a, double *__restrict__ b
     if (i < n) b[i] = (double)a[i];
 }
 
+__global__ void k_f32_scaled_to_f64(const float *__restrict__ a, double alpha, double *__restrict__ b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = alpha * (double)a[i];
+}
+
 __global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (float)a[i];
@@ -292,15 +297,37 @@ rbf_status fgmres_solve(rbf_plan *P, const float *b_caller, const rbf_solve_para
     const double bnorm = std::sqrt(bnorm2);
     int64_t mlp_fallbacks = 0;
     bool x_nonzero = false;
+    Intervals t_mv, t_res, t_pc;
     if (p.precond == RBF_PRECOND_MLP && p.mlp_initial_guess && bnorm > 0) {
-        // x0 = network applied to b; then r0 = b - A~ x0 in float64
+        // g = network applied to b, u = A~ g (float32 product); x0 = a g with the a that
+        // minimises |b - a u|, a = <b, u> / <u, u>, so that |r0| <= |b| whatever the network
+        // returns (a = 0 drops the guess)
         mlp_fallbacks += mlp_apply(p.mlp, P, p.mlp_lambda, 64, r.p, w32.p, s);
-        k_f32_to_f64<<<g1(n), kThreads, 0, s>>>(w32.p, x.p, n);
+        t_mv.begin(s);
+        op(w32.p, Z.p);                                   // Z's first column as scratch
+        t_mv.end(s);
+        k_f32_to_f64<<<g1(n), kThreads, 0, s>>>(Z.p, w64.p, n);
         RBF_LAUNCHED();
-        x_nonzero = true;
+        k_mdot<double><<<G, kThreads, 0, s>>>(r.p, n, 1, w64.p, n, part.p);   // r holds b here
+        RBF_LAUNCHED();
+        k_mdot_final<<<1, kThreads, 0, s>>>(part.p, G, scal.p, 0);
+        RBF_LAUNCHED();
+        norm2_dev(w64.p, n, G, part.p, scal.p + 1, s);
+        double bu_uu[2] = {0, 0};
+        RBF_CUDA(cudaMemcpyAsync(bu_uu, scal.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        RBF_CUDA(cudaStreamSynchronize(s));
+        ctx_check_device_error(P->ctx);
+        const double bu = bu_uu[0], uu = bu_uu[1];
+        const double alpha = (uu > 0 && std::isfinite(uu) && std::isfinite(bu)) ? bu / uu : 0.0;
+        R.guess_scale = alpha;
+        R.guess_residual = alpha != 0.0 ? std::sqrt(std::max(0.0, bnorm2 - bu * alpha)) / bnorm : 1.0;
+        if (alpha != 0.0) {
+            k_f32_scaled_to_f64<<<g1(n), kThreads, 0, s>>>(w32.p, alpha, x.p, n);
+            RBF_LAUNCHED();
+            x_nonzero = true;
+        }
     }
 
-    Intervals t_mv, t_res, t_pc;
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hcol(m + 2), yh(m),
         hbuf((size_t)m * 3 * (m + 1));
     int it = 0, cycles = 0;
