@@ -137,7 +137,10 @@ __device__ __forceinline__ void raise_error(TcSmem &S, unsigned *err) {
 
 // One segment sg of a pair list; `slot` indexes its row of partial sums when its tile
 // has more than one segment.  Run by a whole CTA of kThreadsTc threads.
-template <bool kGrid, bool kSym = false>
+// kScalar: the summed combinations accumulate in eight scalar sums (one FMA per pair)
+// instead of four packed pairs; measured faster for the single-plan product and slower
+// for the batched one (one more live register set where that kernel already spills).
+template <bool kGrid, bool kSym = false, bool kScalar = false>
 __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, int64_t slot, unsigned *err) {
     static_assert(!(kGrid && kSym), "grid targets carry no weights: the symmetric form is for products");
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -349,6 +352,7 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
         // float32's resolution of the unit diagonal and are summed instead of tested
         const bool mask = a.R < 24.f;
         f2 acc[4] = {0ull, 0ull, 0ull, 0ull};
+        float sac[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // kScalar sums
         for (int b = 0; b < nb; ++b) {
             const int s = b % kStages;
             const uint32_t k = (uint32_t)(b / kStages);
@@ -369,7 +373,16 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
             tc5::tmem_ld_32x32(trow + (uint32_t)(s * kBlk), tv);
             const float4 *zz = reinterpret_cast<const float4 *>(S.z[s]);
             float *tcol = &S.tr[warp][0][lane];             // column `lane` of the transpose tile
-            if (code == 2 || !mask) {
+            if (kScalar && !kSym && (code == 2 || !mask)) {
+#pragma unroll
+                for (int g = 0; g < 8; ++g) {
+                    const float4 Z = zz[g];
+                    sac[(4 * g) & 7] = fmaf(ex2_approx(tv[4 * g]), Z.x, sac[(4 * g) & 7]);
+                    sac[(4 * g + 1) & 7] = fmaf(ex2_approx(tv[4 * g + 1]), Z.y, sac[(4 * g + 1) & 7]);
+                    sac[(4 * g + 2) & 7] = fmaf(ex2_approx(tv[4 * g + 2]), Z.z, sac[(4 * g + 2) & 7]);
+                    sac[(4 * g + 3) & 7] = fmaf(ex2_approx(tv[4 * g + 3]), Z.w, sac[(4 * g + 3) & 7]);
+                }
+            } else if (code == 2 || !mask) {
                 // every pair summed: inside the cut-off, or (mask off) beyond it with an entry
                 // below 2^-24 (see the top of the file)
 #pragma unroll
@@ -418,7 +431,8 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
         float v[8];
 #pragma unroll
         for (int i = 0; i < 4; ++i) upk(acc[i], v[2 * i], v[2 * i + 1]);
-        const float y = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+        const float y = (((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]))) +
+                        (((sac[0] + sac[1]) + (sac[2] + sac[3])) + ((sac[4] + sac[5]) + (sac[6] + sac[7])));
         if (sg.w) {
             if (valid) a.out[oi] = y;
         } else {
@@ -436,7 +450,7 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
 
 template <bool kGrid>
 __global__ void __launch_bounds__(kThreadsTc, 4) k_product_tc(MvArgs a, unsigned *err) {
-    product_tc_body<kGrid>(a, a.seg[blockIdx.x], blockIdx.x, err);
+    product_tc_body<kGrid, false, true>(a, a.seg[blockIdx.x], blockIdx.x, err);
 }
 
 // the symmetric form over rbf_plan::sym (row sums as above, transposed sums per entry)
