@@ -353,6 +353,7 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
         const bool mask = a.R < 24.f;
         f2 acc[4] = {0ull, 0ull, 0ull, 0ull};
         float sac[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // kScalar sums
+        float gtot = 0.f;   // grid targets: the running total of the per-block sums
         for (int b = 0; b < nb; ++b) {
             const int s = b % kStages;
             const uint32_t k = (uint32_t)(b / kStages);
@@ -381,6 +382,15 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
                     sac[(4 * g + 1) & 7] = fmaf(ex2_approx(tv[4 * g + 1]), Z.y, sac[(4 * g + 1) & 7]);
                     sac[(4 * g + 2) & 7] = fmaf(ex2_approx(tv[4 * g + 2]), Z.z, sac[(4 * g + 2) & 7]);
                     sac[(4 * g + 3) & 7] = fmaf(ex2_approx(tv[4 * g + 3]), Z.w, sac[(4 * g + 3) & 7]);
+                }
+                if (kGrid) {
+                    // A grid node far from the data sums thousands of terms whose weights
+                    // cancel: each block's 32 terms are summed on their own and added to the
+                    // node's total, so that no float32 sum runs over more than a block's
+                    // terms or the node's blocks.
+                    gtot += ((sac[0] + sac[1]) + (sac[2] + sac[3])) + ((sac[4] + sac[5]) + (sac[6] + sac[7]));
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) sac[q] = 0.f;
                 }
             } else if (code == 2 || !mask) {
                 // every pair summed: inside the cut-off, or (mask off) beyond it with an entry
@@ -432,7 +442,7 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
 #pragma unroll
         for (int i = 0; i < 4; ++i) upk(acc[i], v[2 * i], v[2 * i + 1]);
         const float y = (((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]))) +
-                        (((sac[0] + sac[1]) + (sac[2] + sac[3])) + ((sac[4] + sac[5]) + (sac[6] + sac[7])));
+                        ((((sac[0] + sac[1]) + (sac[2] + sac[3])) + ((sac[4] + sac[5]) + (sac[6] + sac[7]))) + gtot);
         if (sg.w) {
             if (valid) a.out[oi] = y;
         } else {
