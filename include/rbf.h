@@ -520,9 +520,13 @@ rbf_status rbf_mlp_train(rbf_mlp *mlp, const float *X, const float *T, int64_t n
  * (problem, segment) work item, longest first: the tensor-core kernel when every
  * plan takes RBF_PRODUCT_TC, else a persistent CUDA-core kernel whose CTAs take
  * items from an atomic counter; the Arnoldi reductions are segmented per problem; the Givens
- * rotations and the triangular solve run on the device.  The iteration count
- * is fixed (max_it, restarted every m <= 64), as in the paper's timing protocol
- * (Table II); each problem reports its own float64-class true residual.
+ * rotations and the triangular solve run on the device.  The captured solve has
+ * max_it steps (restarted every m <= 64, each restart with a float64-class true
+ * residual); with p->fixed_iterations every problem takes all of them, as in the
+ * paper's timing protocol (Table II); otherwise a problem stops at p->tol (its
+ * residual estimate within a cycle, its true residual at a restart) and the
+ * kernels skip its work from then on.  Each problem reports its own true
+ * residual and its iteration count.
  * ------------------------------------------------------------------------ */
 typedef struct rbf_batch rbf_batch;
 
@@ -552,7 +556,8 @@ int64_t rbf_batch_size(const rbf_batch *batch);
 rbf_status rbf_batch_matvec(rbf_batch *batch, const float *z, float *y, void *stream);
 
 /* Solve every problem: b (float) and x (double, out) are concatenations as above;
- * p->fixed_iterations is implied; p->m <= 64; p->precond NONE or SCHWARZ (the
+ * p->fixed_iterations: every problem takes max_it steps, else each stops at
+ * p->tol (1e-6 if <= 0); p->m <= 64; p->precond NONE or SCHWARZ (the
  * Schwarz set-up runs on every plan when its block size changes).  reports: host
  * array of nplans (may be NULL); stats: host (may be NULL). */
 rbf_status rbf_batch_solve(rbf_batch *batch, const float *b, const rbf_solve_params *p, double *x,

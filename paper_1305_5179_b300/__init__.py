@@ -623,7 +623,8 @@ class Batch:
         return y
 
     def solve(self, b, stream=None, **kw):
-        """Fixed-iteration solve of every problem; returns (x float64, reports, stats)."""
+        """Solve every problem: with fixed_iterations=True each takes max_it steps, else
+        each stops at tol.  Returns (x float64, reports, stats)."""
         import torch
         _req(b, torch.float32, "b", self.n)
         x = torch.empty(self.n, dtype=torch.float64, device=self.device)

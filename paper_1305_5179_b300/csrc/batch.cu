@@ -58,12 +58,13 @@ struct rbf_batch {
     // solve state
     int m_alloc = 0;
     PBuf<float> bs, Z, w32;
-    PBuf<double> V, w64, x, r, red, hA, hB, hN, hs, H, g, cs, sn, y, est, bn2, rn2;
+    PBuf<double> V, w64, x, r, red, hA, hB, hN, hs, H, g, cs, sn, y, est, bn2, rn2, dtol;
+    PBuf<int> act, kp, itp;       // per problem: still iterating; steps of this cycle; steps in all
     // captured solve, on a private stream ordered after and before the caller's
     cudaStream_t own = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    int g_m = -1, g_it = -1, g_pc = -1;
+    int g_m = -1, g_it = -1, g_pc = -1, g_act = -1;
     long long g_kernels = 0;      // kernel nodes of the captured solve
     ~rbf_batch() {
         if (own) cudaStreamSynchronize(own);
@@ -82,7 +83,8 @@ constexpr int kRange = 8192;
 // ------------------------------------------------------------------ product
 __global__ void __launch_bounds__(kWarps * 32, RBF_MV_MINBLOCKS)
     k_bmatvec(const PlanView *__restrict__ views, const int2 *__restrict__ items, int nitems,
-              unsigned int *__restrict__ counter, const float *__restrict__ z, float *__restrict__ y) {
+              unsigned int *__restrict__ counter, const float *__restrict__ z, float *__restrict__ y,
+              const int *__restrict__ act) {
     __shared__ Stage s_st[kWarps];
     __shared__ float s_red[kWarps][kChunk];
     __shared__ int s_item;
@@ -93,6 +95,7 @@ __global__ void __launch_bounds__(kWarps * 32, RBF_MV_MINBLOCKS)
         const int it = s_item;
         if (it >= nitems) break;
         const int2 ci = items[it];
+        if (act && !act[ci.x]) continue;   // the problem has met its tolerance
         const PlanView &v = views[ci.x];
         MvArgs a{};
         a.pos = v.pos;
@@ -113,8 +116,9 @@ __global__ void __launch_bounds__(kWarps * 32, RBF_MV_MINBLOCKS)
 }
 
 __global__ void k_breduce_split(const PlanView *__restrict__ views, const int2 *__restrict__ splits,
-                                float *__restrict__ y) {
+                                float *__restrict__ y, const int *__restrict__ act) {
     const int2 it = splits[blockIdx.x];
+    if (act && !act[it.x]) return;
     const PlanView &v = views[it.x];
     const int s0 = v.tile_seg[it.y], s1 = v.tile_seg[it.y + 1];
     const int2 tl = v.tiles[it.y];
@@ -127,11 +131,12 @@ __global__ void k_breduce_split(const PlanView *__restrict__ views, const int2 *
 
 // ------------------------------------------------------------------ Schwarz
 __global__ void k_bschwarz_apply(const PlanView *__restrict__ views, const int2 *__restrict__ items, int64_t nitems,
-                                 const double *__restrict__ vin, float *__restrict__ z) {
+                                 const double *__restrict__ vin, float *__restrict__ z, const int *__restrict__ act) {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= nitems) return;
     const int2 it = items[w];
+    if (!act[it.x]) return;   // a whole warp's item: the warp leaves together
     const PlanView &v = views[it.x];
     const int B = v.B, core = v.core;
     const int64_t n = v.n;
@@ -180,9 +185,11 @@ __device__ double cta_sum(double v, double *sh) {
 template <typename Tw>
 __global__ void __launch_bounds__(kThreads) k_bmdot(const double *__restrict__ V, int64_t ldv, int nv,
                                                     const Tw *__restrict__ w, const int4 *__restrict__ chunks,
-                                                    int64_t nchunks, double *__restrict__ red) {
+                                                    int64_t nchunks, double *__restrict__ red,
+                                                    const int *__restrict__ act) {
     __shared__ double sh[kThreads / 32];
     const int4 c = chunks[blockIdx.x];
+    if (act && !act[c.x]) return;   // problem done: its sums are not read
     for (int k = 0; k < nv; ++k) {
         const double *vk = V + k * ldv;
         double s = 0.0;
@@ -194,9 +201,10 @@ __global__ void __launch_bounds__(kThreads) k_bmdot(const double *__restrict__ V
 
 // out[p * stride + k] = sum over problem p's chunks of red[k * nchunks + c]; grid (nb, nv)
 __global__ void k_bmdot_final(const double *__restrict__ red, int64_t nchunks, const int32_t *__restrict__ chunk_off,
-                              double *__restrict__ out, int stride) {
+                              double *__restrict__ out, int stride, const int *__restrict__ act) {
     __shared__ double sh[kThreads / 32];
     const int p = blockIdx.x, k = blockIdx.y;
+    if (act && !act[p]) return;
     double s = 0.0;
     for (int c = chunk_off[p] + threadIdx.x; c < chunk_off[p + 1]; c += kThreads) s += red[(int64_t)k * nchunks + c];
     double t = cta_sum(s, sh);
@@ -208,10 +216,12 @@ template <typename Tw>
 __global__ void __launch_bounds__(kThreads) k_bmaxpy(const double *__restrict__ V, int64_t ldv, int nv,
                                                      const double *__restrict__ h, int stride,
                                                      const Tw *__restrict__ win, double *__restrict__ wout,
-                                                     const int4 *__restrict__ chunks, double *__restrict__ red) {
+                                                     const int4 *__restrict__ chunks, double *__restrict__ red,
+                                                     const int *__restrict__ act) {
     __shared__ double sh[kThreads / 32];
     __shared__ double hs[72];
     const int4 c = chunks[blockIdx.x];
+    if (!act[c.x]) return;
     for (int k = threadIdx.x; k < nv; k += kThreads) hs[k] = h[(int64_t)c.x * stride + k];
     __syncthreads();
     double sq = 0.0;
@@ -230,9 +240,10 @@ __global__ void __launch_bounds__(kThreads) k_bmaxpy(const double *__restrict__ 
 
 // dst = src / scale(problem) (0 where the scale is 0)
 __global__ void k_bscale(const double *__restrict__ src, const double *__restrict__ scale,
-                         double *__restrict__ dst, const int4 *__restrict__ chunks) {
+                         double *__restrict__ dst, const int4 *__restrict__ chunks, const int *__restrict__ act) {
     __shared__ double s_inv;    // one float64 division per CTA
     const int4 c = chunks[blockIdx.x];
+    if (!act[c.x]) return;
     if (threadIdx.x == 0) {
         const double sv = scale[c.x];
         s_inv = sv > 0.0 ? 1.0 / sv : 0.0;
@@ -242,10 +253,13 @@ __global__ void k_bscale(const double *__restrict__ src, const double *__restric
     for (int i = threadIdx.x; i < c.z; i += blockDim.x) dst[c.y + i] = src[c.y + i] * inv;
 }
 
-__global__ void k_bupdate_x(double *__restrict__ x, const float *__restrict__ Z, int64_t ldz, int k,
-                            const double *__restrict__ y, int ystride, const int4 *__restrict__ chunks) {
+__global__ void k_bupdate_x(double *__restrict__ x, const float *__restrict__ Z, int64_t ldz,
+                            const int *__restrict__ kp, const double *__restrict__ y, int ystride,
+                            const int4 *__restrict__ chunks) {
     __shared__ double ys[72];
     const int4 c = chunks[blockIdx.x];
+    const int k = kp[c.x];   // the steps this problem took in the cycle (0: none)
+    if (k == 0) return;
     for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = y[(int64_t)c.x * ystride + j];
     __syncthreads();
     for (int i = threadIdx.x; i < c.z; i += blockDim.x) {
@@ -266,18 +280,25 @@ __global__ void k_bto64(const float *__restrict__ a, double *__restrict__ b, int
     if (i < n) b[i] = (double)a[i];
 }
 
+__global__ void k_bset(double *__restrict__ a, double v) { *a = v; }
+
 __global__ void k_bzero(double *__restrict__ a, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] = 0.0;
 }
 
-// per problem: beta = sqrt(norm^2); restart the Givens state
+// per problem: beta = sqrt(norm^2); restart the Givens state; the problem iterates in this
+// cycle unless its residual already meets the tolerance (*tol < 0: every problem iterates)
 __global__ void k_bstart(const double *__restrict__ nrm2, double *__restrict__ beta, double *__restrict__ g,
-                         double *__restrict__ H, int m, int nb) {
+                         double *__restrict__ H, int m, int nb, const double *__restrict__ bn2,
+                         const double *__restrict__ tol, int *__restrict__ act, int *__restrict__ kp) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= nb) return;
     const double b = sqrt(nrm2[p]);
     beta[p] = b;
+    const double t = *tol;
+    act[p] = (t < 0.0 || b > t * sqrt(bn2[p])) && b > 0.0 ? 1 : 0;
+    kp[p] = 0;
     for (int i = 0; i <= m; ++i) g[(int64_t)p * (m + 1) + i] = 0.0;
     g[(int64_t)p * (m + 1)] = b;
     for (int i = 0; i < (m + 1) * m; ++i) H[(int64_t)p * (m + 1) * m + i] = 0.0;
@@ -287,9 +308,10 @@ __global__ void k_bstart(const double *__restrict__ nrm2, double *__restrict__ b
 __global__ void k_bgivens(const double *__restrict__ hA, const double *__restrict__ hB, const double *__restrict__ hN,
                           int stride, int j, int m, double *__restrict__ H, double *__restrict__ cs,
                           double *__restrict__ sn, double *__restrict__ g, double *__restrict__ hscale,
-                          const double *__restrict__ bn2, double *__restrict__ est, int nb) {
+                          const double *__restrict__ bn2, double *__restrict__ est, int nb,
+                          const double *__restrict__ tol, int *__restrict__ act, int *__restrict__ kp) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= nb) return;
+    if (p >= nb || !act[p]) return;
     double *Hp = H + (int64_t)p * (m + 1) * m;
     double *cp = cs + (int64_t)p * m, *sp = sn + (int64_t)p * m, *gp = g + (int64_t)p * (m + 1);
     for (int i = 0; i <= j; ++i) Hp[i * m + j] = hA[(int64_t)p * stride + i] + hB[(int64_t)p * stride + i];
@@ -311,13 +333,19 @@ __global__ void k_bgivens(const double *__restrict__ hA, const double *__restric
     gp[j] = cp[j] * gp[j];
     const double bn = sqrt(bn2[p]);
     est[p] = bn > 0.0 ? fabs(gp[j + 1]) / bn : 0.0;
+    kp[p] = j + 1;
+    // the estimate met the tolerance (or the Krylov space holds the solution): this problem
+    // takes no more steps in the cycle
+    if ((*tol >= 0.0 && est[p] <= *tol) || hn == 0.0) act[p] = 0;
 }
 
 // per problem: y = R^-1 g (k x k upper triangle of the rotated H)
-__global__ void k_bbacksolve(const double *__restrict__ H, const double *__restrict__ g, int k, int m,
-                             double *__restrict__ y, int nb) {
+__global__ void k_bbacksolve(const double *__restrict__ H, const double *__restrict__ g, const int *__restrict__ kp,
+                             int m, double *__restrict__ y, int nb, int *__restrict__ itp) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= nb) return;
+    const int k = kp[p];
+    itp[p] += k;
     const double *Hp = H + (int64_t)p * (m + 1) * m;
     const double *gp = g + (int64_t)p * (m + 1);
     double *yp = y + (int64_t)p * m;
@@ -553,6 +581,10 @@ static void batch_alloc(rbf_batch *Bt, int m, cudaStream_t s) {
     Bt->est.alloc(nb, s);
     Bt->bn2.alloc(nb, s);
     Bt->rn2.alloc(nb, s);
+    Bt->dtol.alloc(1, s);
+    Bt->act.alloc(nb, s);
+    Bt->kp.alloc(nb, s);
+    Bt->itp.alloc(nb, s);
     Bt->m_alloc = m;
     if (Bt->gexec) {
         cudaGraphExecDestroy(Bt->gexec);
@@ -560,33 +592,38 @@ static void batch_alloc(rbf_batch *Bt, int m, cudaStream_t s) {
     }
 }
 
-void batch_matvec_binned(rbf_batch *Bt, const float *z, float *y, cudaStream_t s) {
+// problems whose act flag is 0 are skipped (their y rows are left as they were)
+void batch_matvec_binned(rbf_batch *Bt, const float *z, float *y, cudaStream_t s, const int *act) {
     if (Bt->tc) {
         product_tc_batched_launch(Bt->views.p, Bt->seg_items.p, Bt->nseg_items, z, y, ctx_error_word(Bt->ctx),
-                                  Bt->ctx->device, s);
+                                  Bt->ctx->device, s, act);
     } else {
         RBF_CUDA(cudaMemsetAsync(Bt->counter.p, 0, sizeof(unsigned int), s));
         const int grid = (int)std::min<int64_t>(Bt->persistent_ctas, std::max<int64_t>(Bt->nseg_items, 1));
         k_bmatvec<<<grid, kWarps * 32, 0, s>>>(Bt->views.p, Bt->seg_items.p, (int)Bt->nseg_items, Bt->counter.p, z,
-                                               y);
+                                               y, act);
         RBF_LAUNCHED();
     }
     if (Bt->nsplit > 0) {
-        k_breduce_split<<<(unsigned)Bt->nsplit, kChunk, 0, s>>>(Bt->views.p, Bt->split_tiles.p, y);
+        k_breduce_split<<<(unsigned)Bt->nsplit, kChunk, 0, s>>>(Bt->views.p, Bt->split_tiles.p, y, act);
         RBF_LAUNCHED();
     }
 }
 
 // segmented norms^2 of a float64 vector -> out[problem]
 static void batch_norm2(rbf_batch *Bt, const double *v, double *out, cudaStream_t s) {
-    k_bmdot<double><<<(unsigned)Bt->nchunks, kThreads, 0, s>>>(v, 0, 1, v, Bt->chunks.p, Bt->nchunks, Bt->red.p);
+    k_bmdot<double><<<(unsigned)Bt->nchunks, kThreads, 0, s>>>(v, 0, 1, v, Bt->chunks.p, Bt->nchunks, Bt->red.p,
+                                                               nullptr);
     RBF_LAUNCHED();
-    k_bmdot_final<<<dim3(Bt->nb, 1), kThreads, 0, s>>>(Bt->red.p, Bt->nchunks, Bt->chunk_off.p, out, 1);
+    k_bmdot_final<<<dim3(Bt->nb, 1), kThreads, 0, s>>>(Bt->red.p, Bt->nchunks, Bt->chunk_off.p, out, 1, nullptr);
     RBF_LAUNCHED();
 }
 
-// The whole fixed-iteration solve on the stream (no host synchronisation):
-// input Bt->bs (binned), output Bt->x, Bt->rn2, Bt->bn2, Bt->est.
+// The whole solve on the stream (no host synchronisation): input Bt->bs (binned) and the
+// tolerance *Bt->dtol (< 0: every problem takes every step), output Bt->x, Bt->rn2,
+// Bt->bn2, Bt->est, Bt->itp.  The captured sequence has max_it steps; a problem that meets
+// the tolerance (its Givens estimate within a cycle, its true residual at a restart) takes
+// no further steps: the kernels skip its items, chunks and subdomains.
 static void batch_solve_body(rbf_batch *Bt, int m, int max_it, bool precond, cudaStream_t s) {
     const int64_t N = Bt->N;
     const int nb = Bt->nb;
@@ -595,7 +632,9 @@ static void batch_solve_body(rbf_batch *Bt, int m, int max_it, bool precond, cud
     RBF_LAUNCHED();
     k_bzero<<<g1(N), kThreads, 0, s>>>(Bt->x.p, N);
     RBF_LAUNCHED();
+    RBF_CUDA(cudaMemsetAsync(Bt->itp.p, 0, nb * sizeof(int), s));
     batch_norm2(Bt, Bt->r.p, Bt->bn2.p, s);
+    const int *act = Bt->act.p;
     int it = 0;
     bool first = true;
     while (it < max_it) {
@@ -606,9 +645,10 @@ static void batch_solve_body(rbf_batch *Bt, int m, int max_it, bool precond, cud
         }
         first = false;
         batch_norm2(Bt, Bt->r.p, Bt->hN.p, s);
-        k_bstart<<<nbg, 128, 0, s>>>(Bt->hN.p, Bt->hs.p, Bt->g.p, Bt->H.p, m, nb);
+        k_bstart<<<nbg, 128, 0, s>>>(Bt->hN.p, Bt->hs.p, Bt->g.p, Bt->H.p, m, nb, Bt->bn2.p, Bt->dtol.p, Bt->act.p,
+                                     Bt->kp.p);
         RBF_LAUNCHED();
-        k_bscale<<<(unsigned)Bt->nchunks, kThreads, 0, s>>>(Bt->r.p, Bt->hs.p, Bt->V.p, Bt->chunks.p);
+        k_bscale<<<(unsigned)Bt->nchunks, kThreads, 0, s>>>(Bt->r.p, Bt->hs.p, Bt->V.p, Bt->chunks.p, act);
         RBF_LAUNCHED();
         const int steps = std::min(m, max_it - it);
         for (int j = 0; j < steps; ++j) {
@@ -617,42 +657,47 @@ static void batch_solve_body(rbf_batch *Bt, int m, int max_it, bool precond, cud
             if (precond) {
                 RBF_CUDA(cudaMemsetAsync(Zj, 0, N * sizeof(float), s));   // additive subdomains accumulate
                 k_bschwarz_apply<<<(unsigned)ceil_div(Bt->nsub_items * 32, 256), 256, 0, s>>>(
-                    Bt->views.p, Bt->sub_items.p, Bt->nsub_items, Vj, Zj);
+                    Bt->views.p, Bt->sub_items.p, Bt->nsub_items, Vj, Zj, act);
                 RBF_LAUNCHED();
             } else {
                 k_bcast<<<g1(N), kThreads, 0, s>>>(Vj, Zj, N);
                 RBF_LAUNCHED();
             }
-            batch_matvec_binned(Bt, Zj, Bt->w32.p, s);
+            batch_matvec_binned(Bt, Zj, Bt->w32.p, s, act);
             const int nv = j + 1, st = m + 1;
             k_bmdot<float><<<(unsigned)Bt->nchunks, kThreads, 0, s>>>(Bt->V.p, N, nv, Bt->w32.p, Bt->chunks.p,
-                                                                      Bt->nchunks, Bt->red.p);
+                                                                      Bt->nchunks, Bt->red.p, act);
             RBF_LAUNCHED();
-            k_bmdot_final<<<dim3(nb, nv), kThreads, 0, s>>>(Bt->red.p, Bt->nchunks, Bt->chunk_off.p, Bt->hA.p, st);
+            k_bmdot_final<<<dim3(nb, nv), kThreads, 0, s>>>(Bt->red.p, Bt->nchunks, Bt->chunk_off.p, Bt->hA.p, st,
+                                                            act);
             RBF_LAUNCHED();
             k_bmaxpy<float><<<(unsigned)Bt->nchunks, kThreads, 0, s>>>(Bt->V.p, N, nv, Bt->hA.p, st, Bt->w32.p,
-                                                                       Bt->w64.p, Bt->chunks.p, nullptr);
+                                                                       Bt->w64.p, Bt->chunks.p, nullptr, act);
             RBF_LAUNCHED();
             k_bmdot<double><<<(unsigned)Bt->nchunks, kThreads, 0, s>>>(Bt->V.p, N, nv, Bt->w64.p, Bt->chunks.p,
-                                                                       Bt->nchunks, Bt->red.p);
+                                                                       Bt->nchunks, Bt->red.p, act);
             RBF_LAUNCHED();
-            k_bmdot_final<<<dim3(nb, nv), kThreads, 0, s>>>(Bt->red.p, Bt->nchunks, Bt->chunk_off.p, Bt->hB.p, st);
+            k_bmdot_final<<<dim3(nb, nv), kThreads, 0, s>>>(Bt->red.p, Bt->nchunks, Bt->chunk_off.p, Bt->hB.p, st,
+                                                            act);
             RBF_LAUNCHED();
             k_bmaxpy<double><<<(unsigned)Bt->nchunks, kThreads, 0, s>>>(Bt->V.p, N, nv, Bt->hB.p, st, Bt->w64.p,
-                                                                        Bt->w64.p, Bt->chunks.p, Bt->red.p);
+                                                                        Bt->w64.p, Bt->chunks.p, Bt->red.p, act);
             RBF_LAUNCHED();
-            k_bmdot_final<<<dim3(nb, 1), kThreads, 0, s>>>(Bt->red.p, Bt->nchunks, Bt->chunk_off.p, Bt->hN.p, 1);
+            k_bmdot_final<<<dim3(nb, 1), kThreads, 0, s>>>(Bt->red.p, Bt->nchunks, Bt->chunk_off.p, Bt->hN.p, 1,
+                                                           act);
             RBF_LAUNCHED();
             k_bgivens<<<nbg, 128, 0, s>>>(Bt->hA.p, Bt->hB.p, Bt->hN.p, st, j, m, Bt->H.p, Bt->cs.p, Bt->sn.p,
-                                          Bt->g.p, Bt->hs.p, Bt->bn2.p, Bt->est.p, nb);
+                                          Bt->g.p, Bt->hs.p, Bt->bn2.p, Bt->est.p, nb, Bt->dtol.p, Bt->act.p,
+                                          Bt->kp.p);
             RBF_LAUNCHED();
             k_bscale<<<(unsigned)Bt->nchunks, kThreads, 0, s>>>(Bt->w64.p, Bt->hs.p, Bt->V.p + (size_t)(j + 1) * N,
-                                                                 Bt->chunks.p);
+                                                                 Bt->chunks.p, act);
             RBF_LAUNCHED();
         }
-        k_bbacksolve<<<nbg, 128, 0, s>>>(Bt->H.p, Bt->g.p, steps, m, Bt->y.p, nb);
+        k_bbacksolve<<<nbg, 128, 0, s>>>(Bt->H.p, Bt->g.p, Bt->kp.p, m, Bt->y.p, nb, Bt->itp.p);
         RBF_LAUNCHED();
-        k_bupdate_x<<<(unsigned)Bt->nchunks, kThreads, 0, s>>>(Bt->x.p, Bt->Z.p, N, steps, Bt->y.p, m, Bt->chunks.p);
+        k_bupdate_x<<<(unsigned)Bt->nchunks, kThreads, 0, s>>>(Bt->x.p, Bt->Z.p, N, Bt->kp.p, Bt->y.p, m,
+                                                                Bt->chunks.p);
         RBF_LAUNCHED();
         it += steps;
     }
@@ -694,6 +739,10 @@ rbf_status batch_solve(rbf_batch *Bt, const float *b, const rbf_solve_params &p,
         }
         RBF_CHECK(!pc || Bt->nsub_items > 0, RBF_ERR_INVALID, "Schwarz preconditioner not set up");
         batch_alloc(Bt, m, s);
+        // the tolerance the captured solve reads (a graph replay needs no new capture for it)
+        const double tol = p.fixed_iterations ? -1.0 : (p.tol > 0 ? p.tol : 1e-6);
+        k_bset<<<1, 1, 0, s>>>(Bt->dtol.p, tol);
+        RBF_LAUNCHED();
         RBF_CUDA(cudaEventRecord(e1, s));
         k_bgather_in<<<(unsigned)Bt->nchunks, kThreads, 0, s>>>(Bt->views.p, Bt->chunks.p, b, Bt->bs.p);
         RBF_LAUNCHED();
@@ -742,6 +791,8 @@ rbf_status batch_solve(rbf_batch *Bt, const float *b, const rbf_solve_params &p,
         RBF_LAUNCHED();
         RBF_CUDA(cudaEventRecord(e2, s));
         std::vector<double> rn(Bt->nb), bn(Bt->nb), es(Bt->nb);
+        std::vector<int> itp(Bt->nb);
+        RBF_CUDA(cudaMemcpyAsync(itp.data(), Bt->itp.p, Bt->nb * sizeof(int), cudaMemcpyDeviceToHost, s));
         RBF_CUDA(cudaMemcpyAsync(rn.data(), Bt->rn2.p, Bt->nb * sizeof(double), cudaMemcpyDeviceToHost, s));
         RBF_CUDA(cudaMemcpyAsync(bn.data(), Bt->bn2.p, Bt->nb * sizeof(double), cudaMemcpyDeviceToHost, s));
         RBF_CUDA(cudaMemcpyAsync(es.data(), Bt->est.p, Bt->nb * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -763,14 +814,14 @@ rbf_status batch_solve(rbf_batch *Bt, const float *b, const rbf_solve_params &p,
             nconv += rel <= (p.tol > 0 ? p.tol : 1e-6);
             if (reps) {
                 rbf_report R{};
-                R.iterations = max_it;
+                R.iterations = itp[b2];
                 R.restarts = (int)ceil_div(max_it, m);
                 R.residual_true = rel;
                 R.residual_estimate = es[b2];
                 R.converged = rel <= (p.tol > 0 ? p.tol : 1e-6);
                 R.precond_failed_blocks = 0;
                 R.ms_solve = msb;
-                R.matvec_launches = max_it;
+                R.matvec_launches = itp[b2];
                 reps[b2] = R;
             }
         }
@@ -805,6 +856,7 @@ int batch_autotune(rbf_batch *Bt, const float *b, const rbf_solve_params &p, con
         q.schwarz.core = cands[c];
         q.m = std::min(p.m > 0 ? p.m : 20, 20);
         q.max_it = q.m;
+        q.fixed_iterations = 1;   // every candidate takes the same steps
         Bt->sz_valid = false;   // force set-up
         rbf_batch_stats st{};
         batch_solve(Bt, b, q, xdev.p, nullptr, &st, s);          // set-up + capture

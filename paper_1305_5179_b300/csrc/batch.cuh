@@ -29,9 +29,10 @@ struct PlanView {
 };
 
 // Tensor-core product of every problem of a batch (product_tc.cu): one CTA per
-// (problem, segment) item; split tiles' partial sums go to each view's `partial`.
+// (problem, segment) item; split tiles' partial sums go to each view's `partial`.  act
+// (device, one flag per problem, or null): items of problems whose flag is 0 are skipped.
 void product_tc_batched_launch(const PlanView *views, const int2 *items, int64_t nitems, const float *z, float *y,
-                               unsigned *err, int device, cudaStream_t s);
+                               unsigned *err, int device, cudaStream_t s, const int *act = nullptr);
 // Sets the product kernels' shared-memory attribute on `device` (call before any capture).
 void product_tc_prepare(int device);
 

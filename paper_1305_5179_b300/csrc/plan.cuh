@@ -186,7 +186,8 @@ int64_t count_grid_candidates(rbf_plan *P, const rbf_grid &g, cudaStream_t s);
 
 // batch.cu
 rbf_batch *batch_create(rbf_ctx *ctx, rbf_plan *const *plans, int nplans, cudaStream_t s);
-void batch_matvec_binned(rbf_batch *Bt, const float *z, float *y, cudaStream_t s);
+// act (device, one flag per problem, or null): problems whose flag is 0 are skipped
+void batch_matvec_binned(rbf_batch *Bt, const float *z, float *y, cudaStream_t s, const int *act = nullptr);
 rbf_status batch_solve(rbf_batch *Bt, const float *b, const rbf_solve_params &p, double *x, rbf_report *reps,
                        rbf_batch_stats *stats, cudaStream_t s);
 int batch_autotune(rbf_batch *Bt, const float *b, const rbf_solve_params &p, const int *cands, int ncand,

@@ -488,8 +488,9 @@ __global__ void k_sym_gather(const int2 *__restrict__ blk, int64_t nblk, const i
 __global__ void __launch_bounds__(kThreadsTc, 4) k_bproduct_tc(const PlanView *__restrict__ views,
                                                               const int2 *__restrict__ items,
                                                               const float *__restrict__ z, float *__restrict__ y,
-                                                              unsigned *err) {
+                                                              unsigned *err, const int *__restrict__ act) {
     const int2 ci = items[blockIdx.x];
+    if (act && !act[ci.x]) return;   // the problem has met its tolerance (uniform over the CTA)
     const PlanView &v = views[ci.x];
     MvArgs a{};
     a.pos = v.pos;
@@ -536,10 +537,10 @@ void product_tc_prepare(int device) {
 }
 
 void product_tc_batched_launch(const PlanView *views, const int2 *items, int64_t nitems, const float *z, float *y,
-                               unsigned *err, int device, cudaStream_t s) {
+                               unsigned *err, int device, cudaStream_t s, const int *act) {
     if (nitems <= 0) return;
     product_tc_prepare(device);
-    k_bproduct_tc<<<(unsigned)nitems, kThreadsTc, kSmemTc, s>>>(views, items, z, y, err);
+    k_bproduct_tc<<<(unsigned)nitems, kThreadsTc, kSmemTc, s>>>(views, items, z, y, err, act);
     RBF_LAUNCHED();
 }
 

@@ -88,8 +88,9 @@ def test_batched_cuda_core_path(rbf, ctx, batch, clouds, products):
 
 def test_batched_solve_matches_single_solves(batch, clouds):
     b = np.concatenate([c[1] for c in clouds])
-    x, reps, st = batch.solve(torch.from_numpy(b).cuda(), m=15, max_it=30)
+    x, reps, st = batch.solve(torch.from_numpy(b).cuda(), m=15, max_it=30, fixed_iterations=True)
     assert st["persistent_ctas"] > 0 and st["work_items"] > 0
+    assert all(r["iterations"] == 30 for r in reps)
     xs = x.cpu().numpy()
     o = 0
     for (C, bc, s), plan, rep in zip(clouds, batch.plans, reps):
@@ -146,3 +147,37 @@ def test_batched_schwarz_setup_follows_its_parameters(batch, clouds):
     x3, _, _ = batch.solve(b, shift=1e-3, **kw)
     assert not torch.equal(x1, x2)
     assert torch.equal(x1, x3)
+
+
+def test_batched_solve_to_tolerance(batch, clouds, capsys):
+    """Without fixed_iterations each problem stops at the tolerance: its estimate within a
+    cycle or its true residual at a restart.  The tolerance is set between the clouds'
+    residuals after a fixed solve, so that some stop early and some run to max_it; every
+    problem reported converged meets it in the oracle's float64 operator, its iteration
+    count matches the single-problem FGMRES of the same cloud, and the problems that do
+    not converge take every step."""
+    b = torch.from_numpy(np.concatenate([c[1] for c in clouds])).cuda()
+    kw = dict(m=15, precond="schwarz", core=32, block=32, shift=1e-3, escalate=True)
+    _, reps_f, _ = batch.solve(b, max_it=120, fixed_iterations=True, **kw)
+    res_f = sorted(r["residual_true"] for r in reps_f)
+    tol = float(np.sqrt(res_f[1] * res_f[-2]))          # between the second best and second worst
+    x, reps, st = batch.solve(b, max_it=120, tol=tol, **kw)
+    xs = x.cpu().numpy()
+    o = 0
+    its = []
+    for (C, bc, s), plan, rep in zip(clouds, batch.plans, reps):
+        n = len(C)
+        r64 = oracle.residual_rows(C[:, :3].astype(np.float64), bc.astype(np.float64), xs[o:o + n], s, 6.0)
+        true = np.linalg.norm(r64) / np.linalg.norm(bc.astype(np.float64))
+        assert rep["residual_true"] == pytest.approx(true, rel=1e-6, abs=1e-12)
+        if rep["converged"]:
+            assert true <= tol and rep["iterations"] <= 120
+            _, rp = plan.solve(torch.from_numpy(bc).cuda(), max_it=120, tol=tol, **kw)
+            assert rp["converged"] and abs(rp["iterations"] - rep["iterations"]) <= 2, (rp["iterations"], rep)
+        else:
+            assert rep["iterations"] == 120 and true > tol
+        its.append(rep["iterations"])
+        o += n
+    with capsys.disabled():
+        print(f"\n  batch to tolerance {tol:.2e}: iterations per cloud {its}, {st['converged']} of {len(its)} converged")
+    assert 0 < st["converged"] < len(its) and min(its) < 120
