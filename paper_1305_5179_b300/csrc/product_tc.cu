@@ -353,7 +353,7 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
         const bool mask = a.R < 24.f;
         f2 acc[4] = {0ull, 0ull, 0ull, 0ull};
         float sac[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // kScalar sums
-        float gtot = 0.f;   // grid targets: the running total of the per-block sums
+        float gtot = 0.f, gcomp = 0.f;   // grid targets: compensated total of the per-block sums
         for (int b = 0; b < nb; ++b) {
             const int s = b % kStages;
             const uint32_t k = (uint32_t)(b / kStages);
@@ -386,9 +386,13 @@ __device__ __forceinline__ void product_tc_body(const MvArgs &a, const int4 sg, 
                 if (kGrid) {
                     // A grid node far from the data sums thousands of terms whose weights
                     // cancel: each block's 32 terms are summed on their own and added to the
-                    // node's total, so that no float32 sum runs over more than a block's
-                    // terms or the node's blocks.
-                    gtot += ((sac[0] + sac[1]) + (sac[2] + sac[3])) + ((sac[4] + sac[5]) + (sac[6] + sac[7]));
+                    // node's total with a compensated (Kahan) addition, so that the rounding
+                    // of the long sum is that of one addition.
+                    const float bs = ((sac[0] + sac[1]) + (sac[2] + sac[3])) + ((sac[4] + sac[5]) + (sac[6] + sac[7]));
+                    const float yk = bs - gcomp;
+                    const float tk = gtot + yk;
+                    gcomp = (tk - gtot) - yk;
+                    gtot = tk;
 #pragma unroll
                     for (int q = 0; q < 8; ++q) sac[q] = 0.f;
                 }
