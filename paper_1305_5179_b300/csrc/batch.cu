@@ -130,8 +130,10 @@ __global__ void k_breduce_split(const PlanView *__restrict__ views, const int2 *
 }
 
 // ------------------------------------------------------------------ Schwarz
-__global__ void k_bschwarz_apply(const PlanView *__restrict__ views, const int2 *__restrict__ items, int64_t nitems,
-                                 const double *__restrict__ vin, float *__restrict__ z, const int *__restrict__ act) {
+template <bool kOne>   // kOne: every subdomain has at most 32 centres (one factor tile)
+__global__ void __launch_bounds__(256) k_bschwarz_apply(const PlanView *__restrict__ views, const int2 *__restrict__ items,
+                                                        int64_t nitems, const double *__restrict__ vin,
+                                                        float *__restrict__ z, const int *__restrict__ act) {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= nitems) return;
@@ -154,7 +156,8 @@ __global__ void k_bschwarz_apply(const PlanView *__restrict__ views, const int2 
         int k = lane + 32 * q;
         yv[q] = k < B ? (float)vv[d0 + k] : 0.f;
     }
-    ras::solve_block(L, B, yv, lane);
+    if (kOne) ras::solve_block32(L, B, yv[0], lane);
+    else ras::solve_block(L, B, yv, lane);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         int k = lane + 32 * q;
@@ -656,8 +659,12 @@ static void batch_solve_body(rbf_batch *Bt, int m, int max_it, bool precond, cud
             float *Zj = Bt->Z.p + (size_t)j * N;
             if (precond) {
                 RBF_CUDA(cudaMemsetAsync(Zj, 0, N * sizeof(float), s));   // additive subdomains accumulate
-                k_bschwarz_apply<<<(unsigned)ceil_div(Bt->nsub_items * 32, 256), 256, 0, s>>>(
-                    Bt->views.p, Bt->sub_items.p, Bt->nsub_items, Vj, Zj, act);
+                if (Bt->sz_p.block <= 32)
+                    k_bschwarz_apply<true><<<(unsigned)ceil_div(Bt->nsub_items * 32, 256), 256, 0, s>>>(
+                        Bt->views.p, Bt->sub_items.p, Bt->nsub_items, Vj, Zj, act);
+                else
+                    k_bschwarz_apply<false><<<(unsigned)ceil_div(Bt->nsub_items * 32, 256), 256, 0, s>>>(
+                        Bt->views.p, Bt->sub_items.p, Bt->nsub_items, Vj, Zj, act);
                 RBF_LAUNCHED();
             } else {
                 k_bcast<<<g1(N), kThreads, 0, s>>>(Vj, Zj, N);

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_schwarz_setup(const float4 *_
     }
 }
 
-template <typename Tin>
+template <typename Tin, bool kOne>   // kOne: B <= 32 (one factor tile)
 __global__ void k_schwarz_apply(const Tin *__restrict__ v, int64_t n, int core, int B, int64_t nblocks,
                                 const float *__restrict__ Lall, int restricted, float *__restrict__ z) {
     int64_t blk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -190,7 +190,8 @@ __global__ void k_schwarz_apply(const Tin *__restrict__ v, int64_t n, int core, 
         int k = lane + 32 * q;
         y[q] = k < B ? (float)v[d0 + k] : 0.f;
     }
-    ras::solve_block(L, B, y, lane);
+    if (kOne) ras::solve_block32(L, B, y[0], lane);
+    else ras::solve_block(L, B, y, lane);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         int k = lane + 32 * q;
@@ -245,9 +246,19 @@ void schwarz_apply_binned(rbf_plan *P, const double *vd, const float *vf, float 
     RBF_CHECK(S.ready, RBF_ERR_INVALID, "schwarz preconditioner not set up");
     if (!S.restricted) RBF_CUDA(cudaMemsetAsync(z, 0, P->n * sizeof(float), s));
     unsigned grid = (unsigned)ceil_div(S.nblocks * 32, 256);
-    if (vd)
-        k_schwarz_apply<double><<<grid, 256, 0, s>>>(vd, P->n, S.core, S.block, S.nblocks, S.L.p, S.restricted, z);
-    else
-        k_schwarz_apply<float><<<grid, 256, 0, s>>>(vf, P->n, S.core, S.block, S.nblocks, S.L.p, S.restricted, z);
+    if (S.block <= 32) {
+        if (vd)
+            k_schwarz_apply<double, true><<<grid, 256, 0, s>>>(vd, P->n, S.core, S.block, S.nblocks, S.L.p,
+                                                                S.restricted, z);
+        else
+            k_schwarz_apply<float, true><<<grid, 256, 0, s>>>(vf, P->n, S.core, S.block, S.nblocks, S.L.p,
+                                                               S.restricted, z);
+    } else if (vd) {
+        k_schwarz_apply<double, false><<<grid, 256, 0, s>>>(vd, P->n, S.core, S.block, S.nblocks, S.L.p,
+                                                             S.restricted, z);
+    } else {
+        k_schwarz_apply<float, false><<<grid, 256, 0, s>>>(vf, P->n, S.core, S.block, S.nblocks, S.L.p,
+                                                            S.restricted, z);
+    }
     RBF_LAUNCHED();
 }

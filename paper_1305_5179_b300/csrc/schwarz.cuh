@@ -28,6 +28,41 @@ __device__ __forceinline__ void stage(const float *__restrict__ L, int B, int r0
     __syncwarp();
 }
 
+// B <= 32: the factor is one tile, staged once (all 32 row loads in flight) and used by
+// both sweeps; the same operations in the same order as the general form below, with the
+// loops fully unrolled (the apply kernels run it as a separate instantiation, so that its
+// registers do not lower the general form's occupancy).
+__device__ __forceinline__ void solve_block32(const float *__restrict__ L, int B, float &y, int lane,
+                                              float (*sm)[33]) {
+    float r[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) r[i] = (i < B && lane < B) ? L[(int64_t)i * B + lane] : 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) sm[i][lane] = r[i];
+    __syncwarp();
+    const float inv = lane < B ? 1.f / sm[lane][lane] : 0.f;   // this lane's pivot
+    float s = lane < B ? y : 0.f;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {                       // forward: L w = v
+        const float wc = __shfl_sync(0xffffffffu, s * inv, c);
+        if (lane == c) s = wc;
+        else if (lane > c) s = fmaf(-sm[lane][c], wc, s);
+    }
+#pragma unroll
+    for (int c = 31; c >= 0; --c) {                      // backward: L^T x = w
+        const float xc = __shfl_sync(0xffffffffu, s * inv, c);
+        if (lane == c) s = xc;
+        else if (lane < c) s = fmaf(-sm[c][lane], xc, s);
+    }
+    y = s;
+    __syncwarp();
+}
+
+__device__ __forceinline__ void solve_block32(const float *__restrict__ L, int B, float &y, int lane) {
+    __shared__ float s_tile1[kWarpsPerCta][32][33];
+    solve_block32(L, B, y, lane, s_tile1[threadIdx.x >> 5]);
+}
+
 __device__ __forceinline__ void solve_block(const float *__restrict__ L, int B, float (&y)[kTiles], int lane) {
     __shared__ float s_tile[kWarpsPerCta][32][33];
     float(*sm)[33] = s_tile[threadIdx.x >> 5];
