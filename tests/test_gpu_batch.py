@@ -181,3 +181,33 @@ def test_batched_solve_to_tolerance(batch, clouds, capsys):
     with capsys.disabled():
         print(f"\n  batch to tolerance {tol:.2e}: iterations per cloud {its}, {st['converged']} of {len(its)} converged")
     assert 0 < st["converged"] < len(its) and min(its) < 120
+
+
+def test_batched_solve_to_tolerance_cuda_core_product(rbf, ctx, batch, clouds):
+    """The same tolerance solve on a batch of CUDA-core plans (the persistent product, which
+    skips the items of problems that have stopped): the same clouds converge, in the same
+    number of steps within 2, and each meets the tolerance in the oracle's operator."""
+    b = torch.from_numpy(np.concatenate([c[1] for c in clouds])).cuda()
+    kw = dict(m=15, precond="schwarz", core=32, block=32, shift=1e-3, escalate=True)
+    _, reps_f, _ = batch.solve(b, max_it=120, fixed_iterations=True, **kw)
+    res_f = sorted(r["residual_true"] for r in reps_f)
+    tol = float(np.sqrt(res_f[1] * res_f[-2]))
+    _, reps_tc, _ = batch.solve(b, max_it=120, tol=tol, **kw)
+    plans = [rbf.Plan(ctx, torch.from_numpy(C).cuda(), sigma=s, k=6.0, product="simt") for C, _, s in clouds]
+    other = rbf.Batch(ctx, plans)
+    x, reps, st = other.solve(b, max_it=120, tol=tol, **kw)
+    xs = x.cpu().numpy()
+    o = 0
+    differ = 0
+    for (C, bc, s), rt, rep in zip(clouds, reps_tc, reps):
+        n = len(C)
+        differ += bool(rep["converged"]) != bool(rt["converged"])      # a cloud right at the tolerance
+        if rep["converged"] and rt["converged"]:
+            assert abs(rep["iterations"] - rt["iterations"]) <= 2, (rep["iterations"], rt["iterations"])
+        if not rep["converged"]:
+            assert rep["iterations"] == 120
+        if rep["converged"]:
+            r64 = oracle.residual_rows(C[:, :3].astype(np.float64), bc.astype(np.float64), xs[o:o + n], s, 6.0)
+            assert np.linalg.norm(r64) / np.linalg.norm(bc.astype(np.float64)) <= tol
+        o += n
+    assert differ <= 1 and 0 < st["converged"]
