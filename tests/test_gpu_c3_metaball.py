@@ -92,7 +92,9 @@ LAM5 = 1.0     # shift of the block solves the network learns (relative to the u
 
 def _c5_train(rbf, ctx, plans, per_plan, seed):
     """200,000 exact float64 shifted block solves (lambda LAM5) drawn from the training
-    plans, and the network trained on them (20 epochs of 512)."""
+    plans, and the network trained on them (40 epochs of 512 at step size 3e-4: with 20
+    epochs at 1e-3 the iterations to 1e-4 on C3 varied from 135 to 234 with the order of
+    the same samples; at 3e-4 both orders gave 146-150)."""
     Xs, Ys = [], []
     rng = np.random.default_rng(seed)
     for plan in plans:
@@ -108,7 +110,7 @@ def _c5_train(rbf, ctx, plans, per_plan, seed):
     X, Y = X[perm].contiguous(), Y[perm].contiguous()
     net = rbf.MLP(ctx, synth.mlp_init(seed=1))
     l0, _ = net.loss_grad(X[:8192].contiguous(), Y[:8192].contiguous(), grad=False)
-    hist = net.train(X, Y, epochs=20, batch=512, lr=1e-3)
+    hist = net.train(X, Y, epochs=40, batch=512, lr=3e-4)
     l1, _ = net.loss_grad(X[:8192].contiguous(), Y[:8192].contiguous(), grad=False)
     return net, X.shape[0], (l0, hist[0], hist[-1], l1)
 
@@ -163,7 +165,7 @@ def test_c5_learned_preconditioner_on_c2_and_c3(c3, capsys):
                    rep["ms_setup"] + rep["ms_solve"])
     with capsys.disabled():
         print("\n  C5 (true residual after 50 iterations, ms, fallback blocks):", out,
-              f"training loss (before, epoch 1, epoch 20, after) {[round(float(h), 4) for h in hist]} on {ns} solves")
+              f"training loss (before, epoch 1, epoch 40, after) {[round(float(h), 4) for h in hist]} on {ns} solves")
         print("  C5 on C3 to 1e-4 (converged, iterations, residual, ms; plain after the network's iterations):", tol)
     for name in ("C2", "C3"):
         assert all(np.isfinite(v[0]) for v in out[name].values()) and out[name]["learned"][2] == 0
@@ -173,3 +175,4 @@ def test_c5_learned_preconditioner_on_c2_and_c3(c3, capsys):
     assert g3["learned"] > 1.5 and g3["ras64"] > 1.5                   # C3: both gain
     assert tol["learned"][0] and tol["ras64"][0]
     assert not tol["none"][0]          # the plain solve is still above 1e-4 after the network's iterations
+    assert tol["learned"][1] < 200      # measured: 146 (plain FGMRES: 272)
