@@ -13,8 +13,11 @@
 //  * the preconditioner is each plan's restricted additive Schwarz data, applied
 //    by one warp per (problem, subdomain);
 //  * the float64-class true residual uses the batched double-float kernel.
-// The iteration count is fixed (the paper's timing protocol of Table II); every
-// problem reports its own true residual.  The subdomain size can be chosen by
+// The captured solve has a fixed number of steps.  With fixed_iterations every problem
+// takes all of them (the paper's timing protocol of Table II); otherwise a problem stops
+// at the tolerance (its estimate within a cycle, its true residual at a restart) and a
+// per-problem flag makes every kernel skip its work from then on.  Every problem reports
+// its own true residual and step count.  The subdomain size can be chosen by
 // rbf_batch_autotune, which times short solves of the candidate sizes.
 #include <algorithm>
 #include <chrono>
